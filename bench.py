@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the selected-inversion hot path on one GB300 (or N replicas).
+
+Workload: 3D 7-point upwind convection-diffusion on a 40^3 grid
+(n = 64,000, FP64), nested-dissection ordering, supernodes of at most 256
+columns.  One step = pselinv_selinv (normalisation + the whole root-to-leaf
+sweep) + extraction of the selected entries on the pattern of A, with the
+LU factors resident in HBM.  The factorisation is timed separately.
+
+Metric: FP64-equivalent GFLOP/s of selected inversion, counting
+sum_K 4 c^2 s + 4 c s^2 + 4/3 s^3 over the strict (unrelaxed) supernodes.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the single-matrix path has no exchange step); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "selinv_fp64_equiv_gflops"
+UNIT = "GFLOP/s"
+WORKLOAD = ("3D 7-point upwind convection-diffusion 40^3 (n=64000), FP64, nested dissection, "
+            "max supernode 256, relaxed supernodes (<=20% explicit zeros)")
+# FP64 DFMA pipe of GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz max SM clock
+FP64_ALU_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+SAMPLE_TARGET_N = 4000  # unknowns of the leading nested-dissection subdomain timed on the CPU
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--schedule", default="level", choices=["level", "per_supernode"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def leading_subdomain(p, target):
+    """The leading nested-dissection subdomain of ``p`` with at most ``target``
+    unknowns, as a Problem in the permuted ordering (identity perm)."""
+    import scipy.sparse as sp
+
+    import gen
+    import oracle
+
+    s = oracle.analyze(p, relax_pct=0)
+    n = p.n
+    size = np.ones(n, dtype=np.int64)
+    for j in range(n):
+        if s.parent[j] >= 0:
+            size[s.parent[j]] += size[j]
+    # walk up from column 0: the largest complete subtree that is exactly the
+    # leading columns [0, m) with m <= target
+    m, j = 1, 0
+    while j >= 0 and size[j] <= target:
+        if size[j] == j + 1:
+            m = j + 1
+        j = int(s.parent[j])
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[p.perm] = np.arange(n)
+    cols = np.repeat(np.arange(n), np.diff(p.colptr))
+    a = sp.csc_matrix((p.values, (iperm[p.rowind], iperm[cols])), shape=(n, n))[:m, :m].tocsc()
+    a.sort_indices()
+    return gen.Problem(f"{p.name}_lead{m}", m, a.indptr.astype(np.int64),
+                       a.indices.astype(np.int64), a.data.copy(), np.arange(m, dtype=np.int64),
+                       p.max_supernode)
+
+
+def exact_flops(sym):
+    w = np.diff(sym.supptr).astype(float)
+    c = np.array([sym.supernode_rows(k).size for k in range(sym.nsup)], dtype=float)
+    return float(np.sum(4 * c * c * w + 4 * c * w * w + 4.0 / 3.0 * w ** 3))
+
+
+class OracleSample:
+    def __init__(self, p):
+        import oracle
+        self.q = leading_subdomain(p, SAMPLE_TARGET_N)
+        self.sym = oracle.analyze(self.q, relax_pct=0)
+        self.fac = oracle.lu(self.sym, self.q.colptr, self.q.rowind, self.q.values)
+        self.flops = exact_flops(self.sym)
+        self.desc = (f"selected inversion (Theorem 1 oracle, single thread) of the leading "
+                     f"nested-dissection subdomain of the same matrix: n={self.q.n}, "
+                     f"{self.flops:.3e} flop; LU untimed")
+
+    def step(self):
+        import oracle
+        t0 = time.perf_counter()
+        oracle.selinv(self.fac)
+        return time.perf_counter() - t0
+
+
+def cpu_baseline(p, min_seconds=10.0, max_reps=5):
+    smp = OracleSample(p)
+    times = []
+    while len(times) < max_reps and (sum(times) < min_seconds or len(times) < 1):
+        times.append(smp.step())
+    t = statistics.median(times)
+    return {"value": smp.flops / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": smp.desc, "seconds_per_sample": t, "reps": len(times)}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profiles(kernel):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_1708_04539_gb300", "csrc", ent["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent["bytes_per_launch"] if sha == ent.get("source_sha") else None
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import gen
+    p = gen.make_config(2)
+    smp = OracleSample(p)
+    for _ in range(args.warmup):
+        smp.step()
+    times = [smp.step() for _ in range(args.steps)]
+    t = sum(times) / len(times)
+    value = smp.flops / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": smp.desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": smp.desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import gen
+    import paper_1708_04539_gb300 as ps
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_1708_04539_gb300 import build as libbuild
+    if rank == 0 or world == 1:
+        libbuild.build()
+    if dist is not None:
+        dist.barrier()
+    ps.load_library()
+
+    p = gen.make_config(2)
+    sched = ps.SCHED_PER_SUPERNODE if args.schedule == "per_supernode" else ps.SCHED_LEVEL
+    h = ps.SelInv.from_problem(p, relax_pct=20, schedule=sched, use_graph=not args.no_graph)
+    st = h.structure()
+    flops = float(st["flops_selinv_exact"])
+    stream = torch.cuda.Stream()
+    vals_dev = torch.from_numpy(p.values).cuda()
+    out_dev = torch.zeros(p.nnz, dtype=torch.float64, device="cuda")
+
+    # factorisation (timed separately)
+    with torch.cuda.stream(stream):
+        h.factor(vals_dev, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.factor(vals_dev, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    factor_ms = e0.elapsed_time(e1)
+
+    def step():
+        h.selinv(stream=stream)
+        h.get_selected(out_dev, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        time.sleep(0.25)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                step()
+            ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    h.sync(stream=stream)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * flops / (ms_per_step * 1e-3) / 1e9
+
+    # launch-by-launch replay with CUDA events on the same stream
+    prof = h.profile(0, stream=stream)
+    gemm = [r for r in prof if r["kind"] == "gemm"]
+    tot_ms = sum(r["ms"] for r in prof)
+    g_ms = sum(r["ms"] for r in gemm)
+    g_fl = sum(r["flops"] for r in gemm)
+    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
+    kinds = {}
+    for r in prof:
+        k = kinds.setdefault(r["kind"], {"launches": 0, "ms": 0.0})
+        k["launches"] += 1
+        k["ms"] += r["ms"]
+    for k in kinds.values():
+        k["share"] = k["ms"] / tot_ms if tot_ms else 0.0
+    roofline = {"bound": "alu", "kernel": "gemm_kernel<double,64,64,16> (FP64 DFMA)",
+                "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_ALU_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                "traffic": traffic_from_profiles("gemm_kernel_f64"),
+                "share_of_step": g_ms / tot_ms if tot_ms else None,
+                "launches_per_step": len(gemm)}
+
+    # end to end through the C ABI with host buffers: H2D values, factor,
+    # selected inversion, D2H of the selected entries
+    vals_host = torch.from_numpy(p.values.copy()).pin_memory()
+    out_host = torch.zeros(p.nnz, dtype=torch.float64).pin_memory()
+    with torch.cuda.stream(stream):
+        h.factor(vals_host, stream=stream)
+        h.selinv(stream=stream)
+        h.get_selected(out_host, stream=stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(args.e2e_steps):
+            h.factor(vals_host, stream=stream)
+            h.selinv(stream=stream)
+            h.get_selected(out_host, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * flops / e2e_s / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(p.nnz * 8), "d2h_bytes_per_step": int(p.nnz * 8),
+           "ms_per_step": e2e_s * 1e3, "includes": "H2D values, factor, selinv, extract, D2H"}
+
+    nl = h.plan_stats()["launches_selinv"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator, nested dissection)",
+        "config": {"workload": WORKLOAD, "n": p.n, "nnz": p.nnz,
+                   "supernodes": int(st["nsuper"]), "levels": int(st["nlevels"]),
+                   "flops_per_matrix": flops, "flops_relaxed_structure": st["flops_selinv"],
+                   "schedule": args.schedule, "cuda_graph": not args.no_graph,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (%.0f MB of factors read per step)"
+                         % (st["storage_size"] * 8 / 1e6)},
+        "time_per_matrix_ms": ms_per_step,
+        "factor_ms": factor_ms,
+        "e2e": e2e,
+        "gpu_launches": int((nl + 1) * args.steps),
+        "roofline": roofline,
+        "kernel_shares": kinds,
+        "clocks": clk.summary(),
+    }
+    h.close()
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

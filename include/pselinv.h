@@ -1,0 +1,207 @@
+/*
+ * pselinv -- supernodal selected inversion of a structurally symmetric,
+ * non-symmetric sparse matrix on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Jacquelin, Lin, Yang, "PSelInv -- A distributed memory parallel
+ * algorithm for selected inversion: the non-symmetric case" (Section 2,
+ * Algorithm 1; Theorems 1 and 2).  Given A (n x n, CSC) and a symmetric
+ * fill-reducing ordering P (P A P^T = Atilde), the library factors
+ * Atilde = L U without pivoting (L unit lower, U upper; Eq. LU) and returns
+ * every entry of A^{-1} on the pattern of L + U, by sweeping the
+ * supernodal elimination tree from the roots to the leaves:
+ *
+ *   Lhat_{C,K} = L_{C,K} (L_{K,K})^{-1},  Uhat_{K,C} = (U_{K,K})^{-1} U_{K,C}  (Alg. 1 step 2)
+ *   Ainv_{C,K} = -Ainv_{C,C} Lhat_{C,K}                                  (Alg. 1 step 3)
+ *   Ainv_{K,K} = (U_{K,K})^{-1} (L_{K,K})^{-1} - Uhat_{K,C} Ainv_{C,K}   (Alg. 1 step 4)
+ *   Ainv_{K,C} = -Uhat_{K,C} Ainv_{C,C}                                  (Alg. 1 step 5)
+ *
+ * written here in the non-transposed form (the paper stores A^{-T} in
+ * place; transposing its steps 3-5 gives the lines above).  C is the row
+ * structure R_K of supernode K (C_L = C_U for a structurally symmetric
+ * pattern, Section 1).
+ *
+ * Conventions for every entry point
+ *  - All functions return PSELINV_OK (0) or a negative PSELINV_ERR_* code;
+ *    none exits or aborts.  pselinv_error_string() describes a code.
+ *  - Index arrays are 0-based int64.  `perm` is new -> old: row/column
+ *    perm[k] of A becomes row/column k of Atilde.
+ *  - Input buffers are copied; the library never keeps a caller pointer.
+ *    The handle owns all device memory it allocates (freed by pselinv_free).
+ *    Output buffers belong to the caller.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is ordered on that stream.
+ *  - Value buffers may be host or device pointers (detected with
+ *    cudaPointerGetAttributes); host buffers are copied through the stream.
+ *  - Complex values (PSELINV_C128) are interleaved (re, im) doubles.
+ */
+#ifndef PSELINV_H
+#define PSELINV_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum pselinv_status {
+  PSELINV_OK = 0,
+  PSELINV_ERR_ARG = -1,            /* bad argument or call order */
+  PSELINV_ERR_NOT_STRUCT_SYM = -2, /* pattern(A) != pattern(A^T) */
+  PSELINV_ERR_ZERO_PIVOT = -3,     /* zero pivot; column in pselinv_last_info */
+  PSELINV_ERR_OOM = -4,            /* host or device allocation failed */
+  PSELINV_ERR_CUDA = -5,           /* a CUDA call failed */
+  PSELINV_ERR_TIMEOUT = -6,        /* a bounded device wait gave up */
+  PSELINV_ERR_CHECK = -7,          /* a checked index map read was out of range */
+  PSELINV_ERR_UNSUPPORTED = -8     /* option not available for this dtype */
+};
+
+enum pselinv_dtype { PSELINV_F64 = 1, PSELINV_C128 = 2 };
+
+enum pselinv_precision {
+  PSELINV_PREC_FP64 = 0,      /* every product in FP64 */
+  PSELINV_PREC_OZAKI_FP16 = 1 /* Ainv_CC products as sliced FP16 tensor-core GEMMs */
+};
+
+enum pselinv_schedule {
+  PSELINV_SCHED_LEVEL = 0,         /* one batched launch per elimination-tree level */
+  PSELINV_SCHED_PER_SUPERNODE = 1  /* separate launches for every supernode */
+};
+
+enum pselinv_layout {
+  PSELINV_LAYOUT_PATTERN_A = 0,  /* nnz(A) values, CSC order of the input, original indices */
+  PSELINV_LAYOUT_SUPERNODAL = 1, /* the whole supernodal storage of Ainv (see pselinv_structure) */
+  PSELINV_LAYOUT_FACTORS = 2     /* the supernodal storage of the LU factors (same layout) */
+};
+
+typedef struct pselinv_opts {
+  int32_t max_supernode; /* widest supernode (columns), >= 1; default 256 */
+  int32_t relax_pct;     /* max share (%) of explicit zeros a relaxed supernode adds; default 20 */
+  int32_t precision;     /* pselinv_precision used by pselinv_selinv when it is passed -1 */
+  int32_t slices;        /* FP16 slices per operand for PREC_OZAKI_FP16; 0 = default */
+  int32_t schedule;      /* pselinv_schedule; default PSELINV_SCHED_LEVEL */
+  int32_t use_graph;     /* 1: record the selinv sweep once in a CUDA graph and replay it */
+  int32_t check_level;   /* 1: bounds-check every index-map read on the device */
+  int32_t tile_plan;     /* 0 = built-in heuristic, 1 = tuned plan (pselinv_tune), 2 = learned model */
+  int32_t host_only;     /* 1: pselinv_analyze makes no CUDA call (structure inspection only;
+                            the handle then refuses pselinv_factor) */
+  int32_t reserved[7];
+} pselinv_opts;
+
+typedef struct pselinv_ctx* pselinv_t;
+
+/* Borrowed views of the symbolic structure (valid until pselinv_free).
+ * Supernode K covers permuted columns [sn_first[K], sn_first[K] + sn_width[K]),
+ * its row structure R_K = rows[rows_ptr[K] .. rows_ptr[K+1]) (sorted, > last
+ * column), c_K = rows_ptr[K+1] - rows_ptr[K].  Its storage (one instance)
+ * starts at element sn_offset[K]:
+ *   diagonal block  s x s column-major (L_KK below, U_KK on/above the diagonal;
+ *                   after selinv: Ainv_KK)
+ *   L panel         c x s column-major at sn_offset[K] + s*s
+ *                   (row p = R_K[p]; after selinv: Ainv_{R_K, K})
+ *   U^T panel       c x s column-major at sn_offset[K] + s*s + c*s
+ *                   (entry (p, t) = U_{first+t, R_K[p]}; after selinv:
+ *                   (Ainv_{K, R_K})^T)
+ * storage_size is the number of scalars of one instance. */
+typedef struct pselinv_structure {
+  int64_t n;
+  int64_t nsuper;
+  int64_t nlevels;             /* depth levels of the supernodal tree */
+  int64_t storage_size;
+  int64_t nnz_a;
+  const int64_t* perm;         /* [n] new -> old */
+  const int64_t* etree;        /* [n] column elimination tree of the exact fill, -1 = root */
+  const int64_t* sn_first;     /* [nsuper] */
+  const int64_t* sn_width;     /* [nsuper] */
+  const int64_t* sn_parent;    /* [nsuper] -1 = root */
+  const int64_t* sn_depth;     /* [nsuper] 0 = root */
+  const int64_t* sn_offset;    /* [nsuper] */
+  const int64_t* rows_ptr;     /* [nsuper + 1] */
+  const int64_t* rows;         /* [rows_ptr[nsuper]] */
+  const int64_t* level_ptr;    /* [nlevels + 1] supernodes of depth d: level_sn[level_ptr[d]..) */
+  const int64_t* level_sn;     /* [nsuper] */
+  const int64_t* value_map;    /* [nnz_a] storage slot of each entry of A (CSC order) */
+  double flops_selinv;         /* sum_K 4 c^2 s + 4 c s^2 + 4/3 s^3 on this structure (real) */
+  double flops_selinv_exact;   /* the same sum on the strict (relax 0) supernodes */
+  double flops_factor;         /* sum_K 2 c^2 s + 2 c s^2 + 2/3 s^3 (real) */
+} pselinv_structure;
+
+/* Fill *opts with the defaults. */
+void pselinv_default_opts(pselinv_opts* opts);
+
+/* Symbolic analysis (host only; Section 2 supernodes, elimination tree):
+ * checks pattern(A) = pattern(A^T) (a missing diagonal counts as present),
+ * builds the elimination tree, the (relaxed, width-limited) supernodes, their
+ * row structures, the supernodal tree and its levels, the block index maps
+ * used by the device gathers/scatters, and uploads them.
+ * n >= 0; colptr[n+1], rowind[nnz] host arrays, rows strictly increasing per
+ * column; perm[n] host (NULL = identity); opts NULL = defaults.
+ * Needs a current CUDA device.  On success *out is a new handle. */
+int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
+                    const int64_t* perm, const pselinv_opts* opts, pselinv_t* out);
+
+/* Supernodal LU without pivoting of nbatch instances sharing the pattern
+ * (Eq. LU, Section 3's prerequisite).  values: nbatch * nnz scalars of dtype,
+ * instance b at values + b*nnz, in the CSC order given to pselinv_analyze;
+ * host or device.  Runs on `stream` and waits for it to report a zero pivot
+ * (PSELINV_ERR_ZERO_PIVOT; pselinv_last_info gives the permuted column). */
+int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, void* stream);
+
+/* Selected inversion of every factored instance (Algorithm 1 steps 2-5):
+ * precision = pselinv_precision or -1 for the handle's option.  Asynchronous
+ * on `stream`. */
+int pselinv_selinv(pselinv_t h, int precision, void* stream);
+
+/* Copy results of instance `batch` (Algorithm 1 step 6 and Theorem 2 for
+ * PSELINV_LAYOUT_PATTERN_A: out[p] = (A^{-1})_{rowind[p], j} for entry p of
+ * column j of the input; PSELINV_LAYOUT_SUPERNODAL: storage_size scalars of
+ * Ainv; PSELINV_LAYOUT_FACTORS: storage_size scalars of L and U, available
+ * after pselinv_factor).  out: host or device.  For a host `out` the call
+ * waits for the stream. */
+int pselinv_get_selected(pselinv_t h, int layout, int64_t batch, void* out, void* stream);
+
+/* Borrowed views of the structure; valid until pselinv_free. */
+int pselinv_get_structure(pselinv_t h, pselinv_structure* out);
+
+/* Per-launch record of pselinv_profile. */
+typedef struct pselinv_step_stat {
+  int32_t kind;   /* pselinv_step_kind */
+  int32_t level;  /* tree level of the launch, -1 for whole-tree launches */
+  int64_t tasks;  /* work items (tiles, supernodes, segments) */
+  double flops;   /* useful floating-point operations (real) */
+  double bytes;   /* algorithmic bytes moved (operands read + results written) */
+  double ms;      /* device time from CUDA events around the launch */
+} pselinv_step_stat;
+
+enum pselinv_step_kind {
+  PSELINV_STEP_GEMM = 0, PSELINV_STEP_TRI_INV = 1, PSELINV_STEP_DIAG_LU = 2,
+  PSELINV_STEP_GATHER = 3, PSELINV_STEP_SCATTER_SUB = 4, PSELINV_STEP_COPY = 5,
+  PSELINV_STEP_MEMSET = 6, PSELINV_STEP_SCATTER_VALUES = 7, PSELINV_STEP_SLICE = 8,
+  PSELINV_STEP_OZAKI_GEMM = 9, PSELINV_STEP_RECOMBINE = 10
+};
+
+/* Run the selected-inversion plan (which = 0) or the factorisation plan
+ * (which = 1) launch by launch, outside any graph, with CUDA events around
+ * every launch, and report up to `cap` records in out[] (*count = number of
+ * launches).  The results are the same as pselinv_selinv / pselinv_factor
+ * produce.  Synchronises `stream`. */
+int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out, int64_t cap,
+                    int64_t* count);
+
+/* Number of kernel launches (and memsets) one pselinv_selinv and one
+ * pselinv_factor issue with the current plans (0 if not built yet). */
+int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_factor);
+
+/* Wait for `stream` and report a device-side error recorded by earlier calls. */
+int pselinv_sync(pselinv_t h, void* stream);
+
+/* Extra information about the last error (zero-pivot column, ...), or -1. */
+int64_t pselinv_last_info(pselinv_t h);
+
+const char* pselinv_error_string(int status);
+
+/* Release the handle and all its device memory (NULL is a no-op). */
+void pselinv_free(pselinv_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,316 @@
+"""ctypes binding of libpselinv.so: the same entry points as include/pselinv.h.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); only
+their data pointers are passed.  Streams are torch.cuda.Stream objects,
+raw cudaStream_t integers, or None (the current torch stream if torch has
+CUDA, else the legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "libpselinv.so")
+
+F64, C128 = 1, 2
+PREC_FP64, PREC_OZAKI_FP16 = 0, 1
+SCHED_LEVEL, SCHED_PER_SUPERNODE = 0, 1
+LAYOUT_PATTERN_A, LAYOUT_SUPERNODAL, LAYOUT_FACTORS = 0, 1, 2
+
+ERRORS = {0: "ok", -1: "invalid argument", -2: "not structurally symmetric", -3: "zero pivot",
+          -4: "out of memory", -5: "CUDA error", -6: "timeout", -7: "index check failed",
+          -8: "unsupported"}
+
+_EXPORTS = [
+    "pselinv_default_opts", "pselinv_analyze", "pselinv_factor", "pselinv_selinv",
+    "pselinv_get_selected", "pselinv_get_structure", "pselinv_profile", "pselinv_plan_stats",
+    "pselinv_sync", "pselinv_last_info", "pselinv_error_string", "pselinv_free",
+]
+
+STEP_KINDS = {0: "gemm", 1: "tri_inv", 2: "diag_lu", 3: "gather", 4: "scatter_sub", 5: "copy",
+              6: "memset", 7: "scatter_values", 8: "slice", 9: "ozaki_gemm", 10: "recombine"}
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class PselinvError(RuntimeError):
+    def __init__(self, code, what, info=-1):
+        msg = f"{what}: {ERRORS.get(code, code)} ({code})"
+        if info >= 0:
+            msg += f", info {info}"
+        super().__init__(msg)
+        self.code = code
+        self.info = info
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("max_supernode", ctypes.c_int32), ("relax_pct", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("slices", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("check_level", ctypes.c_int32), ("tile_plan", ctypes.c_int32),
+                ("host_only", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+_P64 = ctypes.POINTER(ctypes.c_int64)
+
+
+class StepStat(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("tasks", ctypes.c_int64),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+class Structure(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nsuper", ctypes.c_int64), ("nlevels", ctypes.c_int64),
+                ("storage_size", ctypes.c_int64), ("nnz_a", ctypes.c_int64),
+                ("perm", _P64), ("etree", _P64), ("sn_first", _P64), ("sn_width", _P64),
+                ("sn_parent", _P64), ("sn_depth", _P64), ("sn_offset", _P64),
+                ("rows_ptr", _P64), ("rows", _P64), ("level_ptr", _P64), ("level_sn", _P64),
+                ("value_map", _P64), ("flops_selinv", ctypes.c_double),
+                ("flops_selinv_exact", ctypes.c_double), ("flops_factor", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB
+
+
+def load_library():
+    """Load libpselinv.so (raises LibraryMissing if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB):
+        raise LibraryMissing(f"{_LIB} is missing: build it with "
+                             "`python -m paper_1708_04539_gb300.build`")
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    lib.pselinv_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.pselinv_default_opts.restype = None
+    lib.pselinv_analyze.argtypes = [I64, P, P, P, ctypes.POINTER(Opts), ctypes.POINTER(P)]
+    lib.pselinv_analyze.restype = ctypes.c_int
+    lib.pselinv_factor.argtypes = [P, ctypes.c_int, I64, P, P]
+    lib.pselinv_factor.restype = ctypes.c_int
+    lib.pselinv_selinv.argtypes = [P, ctypes.c_int, P]
+    lib.pselinv_selinv.restype = ctypes.c_int
+    lib.pselinv_get_selected.argtypes = [P, ctypes.c_int, I64, P, P]
+    lib.pselinv_get_selected.restype = ctypes.c_int
+    lib.pselinv_get_structure.argtypes = [P, ctypes.POINTER(Structure)]
+    lib.pselinv_get_structure.restype = ctypes.c_int
+    lib.pselinv_profile.argtypes = [P, ctypes.c_int, P, ctypes.POINTER(StepStat), I64,
+                                    ctypes.POINTER(I64)]
+    lib.pselinv_profile.restype = ctypes.c_int
+    lib.pselinv_plan_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.pselinv_plan_stats.restype = ctypes.c_int
+    lib.pselinv_sync.argtypes = [P, P]
+    lib.pselinv_sync.restype = ctypes.c_int
+    lib.pselinv_last_info.argtypes = [P]
+    lib.pselinv_last_info.restype = I64
+    lib.pselinv_error_string.argtypes = [ctypes.c_int]
+    lib.pselinv_error_string.restype = ctypes.c_char_p
+    lib.pselinv_free.argtypes = [P]
+    lib.pselinv_free.restype = None
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_EXPORTS)
+
+
+def _ptr(x):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _is_complex(x) -> bool:
+    if isinstance(x, np.ndarray):
+        return np.iscomplexobj(x)
+    return bool(getattr(x, "is_complex", lambda: False)())
+
+
+class SelInv:
+    """One analysed pattern (a handle of the C library)."""
+
+    def __init__(self, n, colptr, rowind, perm=None, max_supernode=256, relax_pct=20,
+                 schedule=SCHED_LEVEL, use_graph=True, check_level=0, precision=PREC_FP64,
+                 slices=0, tile_plan=0, host_only=False):
+        lib = load_library()
+        self._lib = lib
+        opts = Opts()
+        lib.pselinv_default_opts(ctypes.byref(opts))
+        opts.max_supernode = int(max_supernode)
+        opts.relax_pct = int(relax_pct)
+        opts.schedule = int(schedule)
+        opts.use_graph = 1 if use_graph else 0
+        opts.check_level = int(check_level)
+        opts.precision = int(precision)
+        opts.slices = int(slices)
+        opts.tile_plan = int(tile_plan)
+        opts.host_only = 1 if host_only else 0
+        self._colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+        self._rowind = np.ascontiguousarray(rowind, dtype=np.int64)
+        p = None if perm is None else np.ascontiguousarray(perm, dtype=np.int64)
+        h = ctypes.c_void_p()
+        rc = lib.pselinv_analyze(int(n), _ptr(self._colptr), _ptr(self._rowind), _ptr(p),
+                                 ctypes.byref(opts), ctypes.byref(h))
+        if rc != 0:
+            raise PselinvError(rc, "pselinv_analyze")
+        self._h = h
+        self.n = int(n)
+        self.nnz = int(self._colptr[-1])
+        self.dtype = None
+        self.nbatch = 0
+
+    @classmethod
+    def from_problem(cls, problem, **kw):
+        kw.setdefault("max_supernode", problem.max_supernode)
+        return cls(problem.n, problem.colptr, problem.rowind, problem.perm, **kw)
+
+    # -- C ABI wrappers ------------------------------------------------------
+    def _check(self, rc, what):
+        if rc != 0:
+            raise PselinvError(rc, what, int(self._lib.pselinv_last_info(self._h)))
+
+    def factor(self, values, stream=None):
+        """values: [nnz] or [nbatch, nnz] float64/complex128 (numpy or torch)."""
+        shape = tuple(values.shape)
+        nbatch = 1 if len(shape) == 1 else shape[0]
+        if shape[-1] != self.nnz:
+            raise ValueError("values do not match the pattern")
+        dt = C128 if _is_complex(values) else F64
+        rc = self._lib.pselinv_factor(self._h, dt, nbatch, _ptr(values), _stream(stream))
+        self._check(rc, "pselinv_factor")
+        self.dtype, self.nbatch = dt, nbatch
+
+    def selinv(self, precision=-1, stream=None):
+        self._check(self._lib.pselinv_selinv(self._h, int(precision), _stream(stream)),
+                    "pselinv_selinv")
+
+    def get_selected(self, out=None, batch=0, layout=LAYOUT_PATTERN_A, stream=None):
+        """Selected entries of instance ``batch``; ``out`` may be host or device."""
+        if out is None:
+            size = self.nnz if layout == LAYOUT_PATTERN_A else self.structure()["storage_size"]
+            if self.nbatch == 0:
+                raise PselinvError(-1, "get_selected before factor")
+            out = np.zeros(size, dtype=np.complex128 if self.dtype == C128 else np.float64)
+        self._check(self._lib.pselinv_get_selected(self._h, int(layout), int(batch), _ptr(out),
+                                                   _stream(stream)), "pselinv_get_selected")
+        return out
+
+    def profile(self, which=0, stream=None):
+        """Launch-by-launch timing of the selinv (0) or factor (1) plan."""
+        cap = 1 << 16
+        buf = (StepStat * cap)()
+        cnt = ctypes.c_int64(0)
+        self._check(self._lib.pselinv_profile(self._h, int(which), _stream(stream), buf, cap,
+                                              ctypes.byref(cnt)), "pselinv_profile")
+        return [{"kind": STEP_KINDS.get(buf[i].kind, buf[i].kind), "level": buf[i].level,
+                 "tasks": buf[i].tasks, "flops": buf[i].flops, "bytes": buf[i].bytes,
+                 "ms": buf[i].ms} for i in range(min(cnt.value, cap))]
+
+    def plan_stats(self):
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(self._lib.pselinv_plan_stats(self._h, ctypes.byref(a), ctypes.byref(b)),
+                    "pselinv_plan_stats")
+        return {"launches_selinv": a.value, "launches_factor": b.value}
+
+    def sync(self, stream=None):
+        self._check(self._lib.pselinv_sync(self._h, _stream(stream)), "pselinv_sync")
+
+    def structure(self) -> dict:
+        s = Structure()
+        self._check(self._lib.pselinv_get_structure(self._h, ctypes.byref(s)),
+                    "pselinv_get_structure")
+
+        def arr(p, size):
+            if size == 0:
+                return np.zeros(0, dtype=np.int64)
+            return np.ctypeslib.as_array(p, shape=(size,)).copy()
+
+        ns = s.nsuper
+        out = {
+            "n": s.n, "nsuper": ns, "nlevels": s.nlevels, "storage_size": s.storage_size,
+            "nnz_a": s.nnz_a,
+            "perm": arr(s.perm, s.n), "etree": arr(s.etree, s.n),
+            "sn_first": arr(s.sn_first, ns), "sn_width": arr(s.sn_width, ns),
+            "sn_parent": arr(s.sn_parent, ns), "sn_depth": arr(s.sn_depth, ns),
+            "sn_offset": arr(s.sn_offset, ns), "rows_ptr": arr(s.rows_ptr, ns + 1),
+            "level_ptr": arr(s.level_ptr, s.nlevels + 1), "level_sn": arr(s.level_sn, ns),
+            "value_map": arr(s.value_map, s.nnz_a),
+            "flops_selinv": s.flops_selinv, "flops_selinv_exact": s.flops_selinv_exact,
+            "flops_factor": s.flops_factor,
+        }
+        out["rows"] = arr(s.rows, int(out["rows_ptr"][-1]) if ns else 0)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.pselinv_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def supernodal_coordinates(st: dict):
+    """(rows, cols) in permuted indices of every slot of the supernodal storage
+    of one instance (diagonal block, L panel, U^T panel per supernode)."""
+    total = int(st["storage_size"])
+    rows = np.empty(total, dtype=np.int64)
+    cols = np.empty(total, dtype=np.int64)
+    for K in range(int(st["nsuper"])):
+        f, s = int(st["sn_first"][K]), int(st["sn_width"][K])
+        R = st["rows"][st["rows_ptr"][K]:st["rows_ptr"][K + 1]]
+        c = R.size
+        o = int(st["sn_offset"][K])
+        loc = np.arange(f, f + s)
+        rows[o:o + s * s] = np.tile(loc, s)
+        cols[o:o + s * s] = np.repeat(loc, s)
+        o += s * s
+        rows[o:o + c * s] = np.tile(R, s)
+        cols[o:o + c * s] = np.repeat(loc, c)
+        o += c * s
+        rows[o:o + c * s] = np.repeat(loc, c)
+        cols[o:o + c * s] = np.tile(R, s)
+    return rows, cols

@@ -1,0 +1,819 @@
+// C-ABI entry points, device storage and the level scheduler.
+//
+// A handle owns: the symbolic structure (host and device copies), the
+// supernodal storage of the factors (`lu`), of the normalised factors
+// (`nf`: Lhat and Uhat^T panels, Algorithm 1 step 2) and of the selected
+// inverse (`ainv`), one scratch arena, and the launch plans.  A plan is a
+// list of kernel launches whose task lists, GEMM descriptors and offsets
+// live in one device arena built once per (dtype, batch); the selected-
+// inversion plan can be recorded in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+#include "pselinv.h"
+
+using namespace pselinv;
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PSELINV_OK;
+  if (e == cudaErrorMemoryAllocation) return PSELINV_ERR_OOM;
+  return PSELINV_ERR_CUDA;
+}
+#define CK(x)                              \
+  do {                                     \
+    const cudaError_t e_ = (x);            \
+    if (e_ != cudaSuccess) {               \
+      (void)cudaGetLastError();            \
+      return cuda_status(e_);              \
+    }                                      \
+  } while (0)
+
+enum StepKind {
+  ST_GEMM,
+  ST_TRI_INV,
+  ST_DIAG_LU,
+  ST_GATHER,
+  ST_SCATTER_SUB,
+  ST_COPY,
+  ST_MEMSET,
+  ST_SCATTER_VALUES
+};
+
+struct Step {
+  StepKind kind;
+  int cfg = 0;
+  int n = 0;      // tasks / segments
+  int grid = 0;
+  size_t tasks = 0, descs = 0, offs = 0;  // byte offsets into the plan arena
+  void* ptr = nullptr;                    // memset target / store
+  void* ptr2 = nullptr;                   // second buffer
+  size_t bytes = 0;
+  double flops = 0;                       // useful flops of a GEMM step
+  int level = -1;
+};
+
+struct Plan {
+  std::vector<Step> steps;
+  std::vector<char> host;  // staged arena
+  char* arena = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool built = false;
+
+  template <class T>
+  size_t push(const std::vector<T>& v) {
+    size_t off = (host.size() + 255) & ~size_t(255);
+    host.resize(off + v.size() * sizeof(T));
+    if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (arena) cudaFree(arena);
+    exec = nullptr;
+    graph = nullptr;
+    arena = nullptr;
+    steps.clear();
+    host.clear();
+    built = false;
+  }
+};
+
+}  // namespace
+
+struct pselinv_ctx {
+  HostSym H;
+  pselinv_opts opts{};
+  int device = -1;
+  // device structure
+  void* dsym = nullptr;
+  SymDev S{};
+  int* derr = nullptr;
+  int max_width = 1;
+  // numeric state
+  int dtype = 0;
+  int64_t nbatch = 0;
+  size_t esize = 0;
+  char* lu = nullptr;
+  char* nf = nullptr;
+  char* ainv = nullptr;
+  char* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  char* staging = nullptr;  // nbatch * nnz values
+  char* outstage = nullptr; // nnz values
+  bool factored = false, inverted = false;
+  Plan factor_plan;
+  Plan selinv_plan[2];  // by schedule
+  cudaStream_t cap_stream = nullptr;
+  int64_t last_info = -1;
+  int last_status = 0;
+};
+
+namespace {
+
+template <class T>
+int upload(std::vector<char>& host, size_t& off, const std::vector<T>& v) {
+  off = (host.size() + 255) & ~size_t(255);
+  host.resize(off + v.size() * sizeof(T) + 8);
+  if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(T));
+  return 0;
+}
+
+template <class Dst, class Src>
+std::vector<Dst> narrow(const std::vector<Src>& v) {
+  std::vector<Dst> out(v.size());
+  for (size_t i = 0; i < v.size(); i++) out[i] = (Dst)v[i];
+  return out;
+}
+
+int upload_structure(pselinv_ctx* h) {
+  const HostSym& H = h->H;
+  std::vector<int64_t> sn_c(H.ns);
+  for (int64_t k = 0; k < H.ns; k++) sn_c[k] = H.rows_ptr[k + 1] - H.rows_ptr[k];
+  std::vector<char> host;
+  size_t o_first, o_width, o_c, o_off, o_rptr, o_rblk, o_bsn, o_bpb, o_brel, o_rel, o_vmap;
+  upload(host, o_first, narrow<int32_t>(H.sn_first));
+  upload(host, o_width, narrow<int32_t>(H.sn_width));
+  upload(host, o_c, narrow<int32_t>(sn_c));
+  upload(host, o_off, H.sn_offset);
+  upload(host, o_rptr, H.rows_ptr);
+  upload(host, o_rblk, H.rows_blk);
+  upload(host, o_bsn, H.blk_sn);
+  upload(host, o_bpb, H.blk_pb);
+  upload(host, o_brel, H.blk_rel);
+  upload(host, o_rel, H.relidx);
+  upload(host, o_vmap, H.value_map);
+  CK(cudaMalloc(&h->dsym, host.size() + 256));
+  CK(cudaMemcpy(h->dsym, host.data(), host.size(), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&h->derr, 4 * sizeof(int)));
+  CK(cudaMemset(h->derr, 0, 4 * sizeof(int)));
+  char* b = (char*)h->dsym;
+  SymDev& S = h->S;
+  S.sn_first = (const int32_t*)(b + o_first);
+  S.sn_width = (const int32_t*)(b + o_width);
+  S.sn_c = (const int32_t*)(b + o_c);
+  S.sn_off = (const int64_t*)(b + o_off);
+  S.rows_ptr = (const int64_t*)(b + o_rptr);
+  S.rows_blk = (const int32_t*)(b + o_rblk);
+  S.blk_sn = (const int32_t*)(b + o_bsn);
+  S.blk_pb = (const int32_t*)(b + o_bpb);
+  S.blk_rel = (const int64_t*)(b + o_brel);
+  S.relidx = (const int32_t*)(b + o_rel);
+  S.value_map = (const int64_t*)(b + o_vmap);
+  S.storage = H.storage;
+  S.nnz = H.nnz;
+  S.ns = (int32_t)H.ns;
+  S.check = h->opts.check_level > 0 ? 1 : 0;
+  S.relidx_size = (int64_t)H.relidx.size();
+  S.err = h->derr;
+  return PSELINV_OK;
+}
+
+inline int64_t cK(const HostSym& H, int64_t K) { return H.rows_ptr[K + 1] - H.rows_ptr[K]; }
+
+int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// GEMM step from a list of descriptors; tasks enumerate every tile and K chunk
+void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& descs, int level) {
+  if (descs.empty()) return;
+  const int bm = gemm_tile_m(dtype, cfg), bn = gemm_tile_n(dtype, cfg);
+  std::vector<GemmTask> tasks;
+  double flops = 0, bytes = 0;
+  for (size_t d = 0; d < descs.size(); d++) {
+    const GemmDesc& g = descs[d];
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0) continue;
+    for (int ks = 0; ks < g.ksplit; ks++)
+      for (int tn = 0; tn < ceil_div(g.N, bn); tn++)
+        for (int tm = 0; tm < ceil_div(g.M, bm); tm++) tasks.push_back({(int)d, tm, tn, ks});
+    flops += 2.0 * g.M * g.N * g.K * (dtype == DT_F64 ? 1 : 4);
+    const double es = dtype == DT_F64 ? 8.0 : 16.0;
+    bytes += es * ((double)g.M * g.K + (double)g.K * g.N +
+                   (double)g.M * g.N * ((g.atomic || g.beta != 0.0) ? 2.0 : 1.0));
+  }
+  if (tasks.empty()) return;
+  Step s;
+  s.bytes = (size_t)bytes;
+  s.kind = ST_GEMM;
+  s.cfg = cfg;
+  s.n = (int)tasks.size();
+  s.grid = std::min(s.n, 1 << 20);
+  s.descs = P.push(descs);
+  s.tasks = P.push(tasks);
+  s.flops = flops;
+  s.level = level;
+  P.steps.push_back(s);
+}
+
+GemmDesc make_desc(const void* A, const void* B, void* C, int M, int N, int K, int lda, int ldb,
+                   int ldc, int ta, int tb, double alpha, double beta, int atomic = 0,
+                   int ksplit = 1) {
+  GemmDesc d;
+  d.A = A;
+  d.B = B;
+  d.C = C;
+  d.M = M;
+  d.N = N;
+  d.K = K;
+  d.lda = lda;
+  d.ldb = ldb;
+  d.ldc = ldc;
+  d.transA = ta;
+  d.transB = tb;
+  d.alpha = alpha;
+  d.beta = beta;
+  d.atomic = atomic;
+  d.ksplit = ksplit < 1 ? 1 : ksplit;
+  return d;
+}
+
+// scratch needed (bytes) by the factor and selected-inversion plans
+size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
+  // selinv: W (2 s^2 for every supernode) + the largest level's G (c^2)
+  int64_t w = 0, gmax = 0, fmax = 0;
+  for (int64_t k = 0; k < H.ns; k++) w += 2 * H.sn_width[k] * H.sn_width[k];
+  for (size_t d = 0; d + 1 < H.level_ptr.size(); d++) {
+    int64_t g = 0;
+    for (int64_t i = H.level_ptr[d]; i < H.level_ptr[d + 1]; i++) {
+      const int64_t c = cK(H, H.level_sn[i]);
+      g += c * c;
+    }
+    gmax = std::max(gmax, g);
+  }
+  for (size_t d = 0; d + 1 < H.hlevel_ptr.size(); d++) {
+    int64_t f = 0;
+    for (int64_t i = H.hlevel_ptr[d]; i < H.hlevel_ptr[d + 1]; i++) {
+      const int64_t K = H.hlevel_sn[i], s = H.sn_width[K], c = cK(H, K);
+      f += 2 * s * s + 2 * c * s + c * c;
+    }
+    fmax = std::max(fmax, f);
+  }
+  const int64_t sel = w + gmax;
+  return (size_t)(std::max(sel, fmax) * nb) * es + 256;
+}
+
+int choose_cfg(int dtype) { return dtype == DT_F64 ? GEMM_64x64 : GEMM_64x64; }
+
+// ---------------------------------------------------------------------------
+// factor plan: scatter A, then per height level (leaves first):
+//   diagonal LU, triangular inverses, L = A_{C,K} U_KK^{-1},
+//   U^T = A_{K,C}^T L_KK^{-T}, Schur Sc = L U, scatter -Sc into ancestors,
+//   copy the panels back.
+// ---------------------------------------------------------------------------
+int build_factor_plan(pselinv_ctx* h) {
+  const HostSym& H = h->H;
+  Plan& P = h->factor_plan;
+  P.release();
+  const size_t es = h->esize;
+  const int dt = h->dtype;
+  const int64_t nb = h->nbatch;
+  Step ms;
+  ms.kind = ST_MEMSET;
+  ms.ptr = h->lu;
+  ms.bytes = (size_t)nb * H.storage * es;
+  P.steps.push_back(ms);
+  Step sv;
+  sv.kind = ST_SCATTER_VALUES;
+  P.steps.push_back(sv);
+  const int cfg = choose_cfg(dt);
+  for (size_t lev = 0; lev + 1 < H.hlevel_ptr.size(); lev++) {
+    std::vector<SnTask> diag, tri, gt;
+    std::vector<int64_t> wofs, gofs;
+    std::vector<GemmDesc> trsm, schur;
+    std::vector<CopySeg> segs;
+    int64_t off = 0;  // scalars into scratch
+    for (int64_t b = 0; b < nb; b++)
+      for (int64_t i = H.hlevel_ptr[lev]; i < H.hlevel_ptr[lev + 1]; i++) {
+        const int64_t K = H.hlevel_sn[i], s = H.sn_width[K], c = cK(H, K);
+        const int64_t w0 = off, t0 = w0 + 2 * s * s, s0 = t0 + 2 * c * s;
+        off = s0 + c * c;
+        diag.push_back({(int)b, (int)K, 0, 0});
+        if (c == 0) continue;
+        for (int which = 0; which < 2; which++)
+          for (int64_t j = 0; j < s; j += 8) {
+            tri.push_back({(int)b, (int)K, which, (int)j});
+            wofs.push_back(w0 + which * s * s);
+          }
+        char* base = h->lu + ((size_t)b * H.storage + H.sn_offset[K]) * es;
+        char* Lp = base + (size_t)s * s * es;
+        char* Up = Lp + (size_t)c * s * es;
+        char* Linv = h->scratch + (size_t)w0 * es;
+        char* Uinv = Linv + (size_t)s * s * es;
+        char* TL = h->scratch + (size_t)t0 * es;
+        char* TU = TL + (size_t)c * s * es;
+        char* Sc = h->scratch + (size_t)s0 * es;
+        trsm.push_back(make_desc(Lp, Uinv, TL, c, s, s, c, s, c, 0, 0, 1.0, 0.0));
+        trsm.push_back(make_desc(Up, Linv, TU, c, s, s, c, s, c, 0, 1, 1.0, 0.0));
+        schur.push_back(make_desc(TL, TU, Sc, c, c, s, c, c, c, 0, 1, 1.0, 0.0));
+        for (int tq = 0; tq < ceil_div(c, 32); tq++)
+          for (int tp = 0; tp < ceil_div(c, 32); tp++) {
+            gt.push_back({(int)b, (int)K, tp, tq});
+            gofs.push_back(s0);
+          }
+        segs.push_back({TL, Lp, 2 * c * s});
+      }
+    Step d;
+    d.kind = ST_DIAG_LU;
+    d.n = (int)diag.size();
+    d.tasks = P.push(diag);
+    d.level = (int)lev;
+    P.steps.push_back(d);
+    if (!tri.empty()) {
+      Step t;
+      t.kind = ST_TRI_INV;
+      t.n = (int)tri.size();
+      t.tasks = P.push(tri);
+      t.offs = P.push(wofs);
+      t.level = (int)lev;
+      P.steps.push_back(t);
+    }
+    add_gemm_step(P, dt, cfg, trsm, (int)lev);
+    add_gemm_step(P, dt, cfg, schur, (int)lev);
+    if (!gt.empty()) {
+      Step sc;
+      sc.kind = ST_SCATTER_SUB;
+      sc.n = (int)gt.size();
+      sc.tasks = P.push(gt);
+      sc.offs = P.push(gofs);
+      sc.level = (int)lev;
+      P.steps.push_back(sc);
+    }
+    if (!segs.empty()) {
+      Step cp;
+      cp.kind = ST_COPY;
+      cp.n = (int)segs.size();
+      cp.tasks = P.push(segs);
+      cp.level = (int)lev;
+      P.steps.push_back(cp);
+    }
+  }
+  CK(cudaMalloc(&P.arena, P.host.size() + 256));
+  CK(cudaMemcpy(P.arena, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
+  P.built = true;
+  return PSELINV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// selected-inversion plan (FP64 / complex128 products):
+//   normalise (all supernodes at once): Linv, Uinv; Lhat = L Linv,
+//   Uhat^T = U^T Uinv^T, D = Uinv Linv (-> Ainv_KK);
+//   then for every depth level (roots first): gather G = Ainv_CC,
+//   Ainv_CK = -G Lhat, (Ainv_KC)^T = -G^T Uhat^T, Ainv_KK += -Uhat Ainv_CK.
+// schedule = PER_SUPERNODE issues the three level launches per supernode.
+// ---------------------------------------------------------------------------
+int build_selinv_plan(pselinv_ctx* h, int schedule) {
+  const HostSym& H = h->H;
+  Plan& P = h->selinv_plan[schedule];
+  P.release();
+  const size_t es = h->esize;
+  const int dt = h->dtype;
+  const int64_t nb = h->nbatch;
+  const int cfg = choose_cfg(dt);
+  // W region: Linv | Uinv per (instance, supernode)
+  std::vector<int64_t> wbase((size_t)(nb * H.ns));
+  int64_t off = 0;
+  for (int64_t b = 0; b < nb; b++)
+    for (int64_t K = 0; K < H.ns; K++) {
+      wbase[b * H.ns + K] = off;
+      off += 2 * H.sn_width[K] * H.sn_width[K];
+    }
+  const int64_t gbase = off;
+  {
+    std::vector<SnTask> tri;
+    std::vector<int64_t> wofs;
+    std::vector<GemmDesc> norm;
+    for (int64_t b = 0; b < nb; b++)
+      for (int64_t K = 0; K < H.ns; K++) {
+        const int64_t s = H.sn_width[K], c = cK(H, K), w0 = wbase[b * H.ns + K];
+        for (int which = 0; which < 2; which++)
+          for (int64_t j = 0; j < s; j += 8) {
+            tri.push_back({(int)b, (int)K, which, (int)j});
+            wofs.push_back(w0 + which * s * s);
+          }
+        const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
+        char* Linv = h->scratch + (size_t)w0 * es;
+        char* Uinv = Linv + (size_t)s * s * es;
+        norm.push_back(make_desc(Uinv, Linv, h->ainv + so, s, s, s, s, s, s, 0, 0, 1.0, 0.0));
+        if (c > 0) {
+          const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
+          norm.push_back(make_desc(h->lu + lo, Linv, h->nf + lo, c, s, s, c, s, c, 0, 0, 1.0, 0.0));
+          norm.push_back(make_desc(h->lu + uo, Uinv, h->nf + uo, c, s, s, c, s, c, 0, 1, 1.0, 0.0));
+        }
+      }
+    Step t;
+    t.kind = ST_TRI_INV;
+    t.n = (int)tri.size();
+    t.tasks = P.push(tri);
+    t.offs = P.push(wofs);
+    P.steps.push_back(t);
+    add_gemm_step(P, dt, cfg, norm, -1);
+  }
+  for (size_t lev = 0; lev + 1 < H.level_ptr.size(); lev++) {
+    // groups: the whole level, or one supernode at a time
+    std::vector<std::vector<int64_t>> groups;
+    if (schedule == PSELINV_SCHED_LEVEL) {
+      groups.emplace_back(H.level_sn.begin() + H.level_ptr[lev],
+                          H.level_sn.begin() + H.level_ptr[lev + 1]);
+    } else {
+      for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++)
+        groups.push_back({H.level_sn[i]});
+    }
+    for (const auto& grp : groups) {
+      std::vector<SnTask> gt;
+      std::vector<int64_t> gofs;
+      std::vector<GemmDesc> main, dg;
+      int64_t goff = gbase;
+      for (int64_t b = 0; b < nb; b++)
+        for (int64_t K : grp) {
+          const int64_t s = H.sn_width[K], c = cK(H, K);
+          if (c == 0) continue;
+          const int64_t g0 = goff;
+          goff += c * c;
+          for (int tq = 0; tq < ceil_div(c, 32); tq++)
+            for (int tp = 0; tp < ceil_div(c, 32); tp++) {
+              gt.push_back({(int)b, (int)K, tp, tq});
+              gofs.push_back(g0);
+            }
+          const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
+          const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
+          char* G = h->scratch + (size_t)g0 * es;
+          main.push_back(make_desc(G, h->nf + lo, h->ainv + lo, c, s, c, c, c, c, 0, 0, -1.0, 0.0));
+          main.push_back(make_desc(G, h->nf + uo, h->ainv + uo, c, s, c, c, c, c, 1, 0, -1.0, 0.0));
+          const int ksplit = std::max(1, (int)std::min<int64_t>(c / 256, 64));
+          dg.push_back(make_desc(h->nf + uo, h->ainv + lo, h->ainv + so, s, s, c, c, c, s, 1, 0,
+                                 -1.0, 1.0, 1, ksplit));
+        }
+      if (gt.empty()) continue;
+      Step g;
+      g.kind = ST_GATHER;
+      g.bytes = (size_t)((goff - gbase) * (int64_t)es * 2);
+      g.n = (int)gt.size();
+      g.tasks = P.push(gt);
+      g.offs = P.push(gofs);
+      g.level = (int)lev;
+      P.steps.push_back(g);
+      add_gemm_step(P, dt, cfg, main, (int)lev);
+      add_gemm_step(P, dt, cfg, dg, (int)lev);
+    }
+  }
+  CK(cudaMalloc(&P.arena, P.host.size() + 256));
+  CK(cudaMemcpy(P.arena, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
+  P.built = true;
+  return PSELINV_OK;
+}
+
+void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) {
+  char* a = P.arena;
+  switch (s.kind) {
+    case ST_GEMM:
+      launch_gemm(h->dtype, s.cfg, (const GemmDesc*)(a + s.descs), (const GemmTask*)(a + s.tasks),
+                  s.n, s.grid, st);
+      break;
+    case ST_TRI_INV:
+      launch_tri_inv(h->dtype, h->S, h->lu, h->scratch, (const int64_t*)(a + s.offs),
+                     (const SnTask*)(a + s.tasks), s.n, h->max_width, st);
+      break;
+    case ST_DIAG_LU:
+      launch_diag_lu(h->dtype, h->S, h->lu, (const SnTask*)(a + s.tasks), s.n, st);
+      break;
+    case ST_GATHER:
+      launch_gather(h->dtype, h->S, h->ainv, h->scratch, (const int64_t*)(a + s.offs),
+                    (const SnTask*)(a + s.tasks), s.n, st);
+      break;
+    case ST_SCATTER_SUB:
+      launch_scatter_sub(h->dtype, h->S, h->lu, h->scratch, (const int64_t*)(a + s.offs),
+                         (const SnTask*)(a + s.tasks), s.n, st);
+      break;
+    case ST_COPY:
+      launch_copy(h->dtype, (const CopySeg*)(a + s.tasks), s.n, st);
+      break;
+    case ST_MEMSET:
+      cudaMemsetAsync(s.ptr, 0, s.bytes, st);
+      break;
+    case ST_SCATTER_VALUES:
+      launch_scatter_values(h->dtype, h->S, h->staging, h->lu, (int)h->nbatch, st);
+      break;
+  }
+}
+
+int run_plan(pselinv_ctx* h, Plan& P, cudaStream_t st, bool graph) {
+  if (!graph) {
+    for (const Step& s : P.steps) launch_step(h, P, s, st);
+    CK(cudaGetLastError());
+    return PSELINV_OK;
+  }
+  if (!P.exec) {
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (const Step& s : P.steps) launch_step(h, P, s, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return cuda_status(e);
+    }
+    P.graph = g;
+    CK(cudaGraphInstantiate(&P.exec, g, 0));
+  }
+  CK(cudaGraphLaunch(P.exec, st));
+  return PSELINV_OK;
+}
+
+void free_numeric(pselinv_ctx* h) {
+  h->factor_plan.release();
+  for (auto& p : h->selinv_plan) p.release();
+  cudaFree(h->lu);
+  cudaFree(h->nf);
+  cudaFree(h->ainv);
+  cudaFree(h->scratch);
+  cudaFree(h->staging);
+  cudaFree(h->outstage);
+  h->lu = h->nf = h->ainv = h->scratch = h->staging = h->outstage = nullptr;
+  h->dtype = 0;
+  h->nbatch = 0;
+  h->factored = h->inverted = false;
+}
+
+int read_device_error(pselinv_ctx* h, cudaStream_t st) {
+  int herr[2] = {0, 0};
+  CK(cudaMemcpyAsync(herr, h->derr, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr[0] == DEV_ZERO_PIVOT) {
+    h->last_info = herr[1];
+    return PSELINV_ERR_ZERO_PIVOT;
+  }
+  if (herr[0] == DEV_CHECK) {
+    h->last_info = herr[1];
+    return PSELINV_ERR_CHECK;
+  }
+  return PSELINV_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pselinv_default_opts(pselinv_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->max_supernode = 256;
+  o->relax_pct = 20;
+  o->precision = PSELINV_PREC_FP64;
+  o->slices = 0;
+  o->schedule = PSELINV_SCHED_LEVEL;
+  o->use_graph = 1;
+  o->check_level = 0;
+  o->tile_plan = 0;
+  o->host_only = 0;
+}
+
+const char* pselinv_error_string(int status) {
+  switch (status) {
+    case PSELINV_OK: return "ok";
+    case PSELINV_ERR_ARG: return "invalid argument or call order";
+    case PSELINV_ERR_NOT_STRUCT_SYM: return "pattern is not structurally symmetric";
+    case PSELINV_ERR_ZERO_PIVOT: return "zero pivot in the LU factorisation";
+    case PSELINV_ERR_OOM: return "out of memory";
+    case PSELINV_ERR_CUDA: return "CUDA error";
+    case PSELINV_ERR_TIMEOUT: return "bounded device wait timed out";
+    case PSELINV_ERR_CHECK: return "index map read out of range";
+    case PSELINV_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind, const int64_t* perm,
+                    const pselinv_opts* opts, pselinv_t* out) {
+  if (!out) return PSELINV_ERR_ARG;
+  *out = nullptr;
+  pselinv_ctx* h = new (std::nothrow) pselinv_ctx();
+  if (!h) return PSELINV_ERR_OOM;
+  if (opts) h->opts = *opts; else pselinv_default_opts(&h->opts);
+  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 1024) {
+    delete h;
+    return PSELINV_ERR_ARG;
+  }
+  int rc = analyze_host(n, colptr, rowind, perm, h->opts.max_supernode, h->opts.relax_pct, h->H);
+  if (rc != PSELINV_OK) {
+    delete h;
+    return rc;
+  }
+  for (int64_t k = 0; k < h->H.ns; k++) h->max_width = std::max<int>(h->max_width, (int)h->H.sn_width[k]);
+  if (!h->opts.host_only) {
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+      (void)cudaGetLastError();
+      delete h;
+      return PSELINV_ERR_CUDA;
+    }
+    rc = upload_structure(h);
+    if (rc != PSELINV_OK) {
+      pselinv_free(h);
+      return rc;
+    }
+  }
+  *out = h;
+  return PSELINV_OK;
+}
+
+int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, void* stream) {
+  if (!h || h->opts.host_only || (dtype != PSELINV_F64 && dtype != PSELINV_C128) || nbatch < 1 ||
+      (!values && h->H.nnz > 0))
+    return PSELINV_ERR_ARG;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t es = dtype == PSELINV_F64 ? 8 : 16;
+  if (h->dtype != dtype || h->nbatch != nbatch) {
+    free_numeric(h);
+    h->dtype = dtype;
+    h->nbatch = nbatch;
+    h->esize = es;
+    const size_t sbytes = (size_t)nbatch * h->H.storage * es + 256;
+    CK(cudaMalloc(&h->lu, sbytes));
+    CK(cudaMalloc(&h->nf, sbytes));
+    CK(cudaMalloc(&h->ainv, sbytes));
+    CK(cudaMemset(h->nf, 0, sbytes));
+    h->scratch_bytes = scratch_need(h->H, nbatch, es);
+    CK(cudaMalloc(&h->scratch, h->scratch_bytes));
+    CK(cudaMalloc(&h->staging, (size_t)nbatch * h->H.nnz * es + 256));
+    CK(cudaMalloc(&h->outstage, (size_t)h->H.nnz * es + 256));
+    CK(prepare_dense_kernels(dtype, h->max_width));
+    int rc = build_factor_plan(h);
+    if (rc != PSELINV_OK) return rc;
+  }
+  h->factored = h->inverted = false;
+  if (h->H.nnz > 0)
+    CK(cudaMemcpyAsync(h->staging, values, (size_t)nbatch * h->H.nnz * es, cudaMemcpyDefault, st));
+  CK(cudaMemsetAsync(h->derr, 0, 4 * sizeof(int), st));
+  int rc = run_plan(h, h->factor_plan, st, false);
+  if (rc != PSELINV_OK) return rc;
+  rc = read_device_error(h, st);
+  if (rc != PSELINV_OK) return rc;
+  h->factored = true;
+  return PSELINV_OK;
+}
+
+int pselinv_selinv(pselinv_t h, int precision, void* stream) {
+  if (!h || !h->factored) return PSELINV_ERR_ARG;
+  if (precision < 0) precision = h->opts.precision;
+  if (precision != PSELINV_PREC_FP64) return PSELINV_ERR_UNSUPPORTED;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
+  Plan& P = h->selinv_plan[sched];
+  if (!P.built) {
+    const int rc = build_selinv_plan(h, sched);
+    if (rc != PSELINV_OK) return rc;
+  }
+  const int rc = run_plan(h, P, st, h->opts.use_graph != 0);
+  if (rc != PSELINV_OK) return rc;
+  h->inverted = true;
+  return PSELINV_OK;
+}
+
+int pselinv_get_selected(pselinv_t h, int layout, int64_t batch, void* out, void* stream) {
+  if (!h || !out || batch < 0 || batch >= h->nbatch) return PSELINV_ERR_ARG;
+  if (layout == PSELINV_LAYOUT_FACTORS ? !h->factored : !h->inverted) return PSELINV_ERR_ARG;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev = is_device_ptr(out);
+  if (layout == PSELINV_LAYOUT_FACTORS) {
+    CK(cudaMemcpyAsync(out, h->lu + (size_t)batch * h->H.storage * h->esize,
+                       (size_t)h->H.storage * h->esize, cudaMemcpyDefault, st));
+    if (!dev) CK(cudaStreamSynchronize(st));
+    return PSELINV_OK;
+  }
+  if (layout == PSELINV_LAYOUT_PATTERN_A) {
+    void* dst = dev ? out : (void*)h->outstage;
+    launch_extract(h->dtype, h->S, h->ainv, (int)batch, dst, st);
+    CK(cudaGetLastError());
+    if (!dev) {
+      CK(cudaMemcpyAsync(out, h->outstage, (size_t)h->H.nnz * h->esize, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    return PSELINV_OK;
+  }
+  if (layout == PSELINV_LAYOUT_SUPERNODAL) {
+    CK(cudaMemcpyAsync(out, h->ainv + (size_t)batch * h->H.storage * h->esize,
+                       (size_t)h->H.storage * h->esize, cudaMemcpyDefault, st));
+    if (!dev) CK(cudaStreamSynchronize(st));
+    return PSELINV_OK;
+  }
+  return PSELINV_ERR_ARG;
+}
+
+int pselinv_get_structure(pselinv_t h, pselinv_structure* o) {
+  if (!h || !o) return PSELINV_ERR_ARG;
+  const HostSym& H = h->H;
+  o->n = H.n;
+  o->nsuper = H.ns;
+  o->nlevels = (int64_t)H.level_ptr.size() - 1;
+  o->storage_size = H.storage;
+  o->nnz_a = H.nnz;
+  o->perm = H.perm.data();
+  o->etree = H.etree.data();
+  o->sn_first = H.sn_first.data();
+  o->sn_width = H.sn_width.data();
+  o->sn_parent = H.sn_parent.data();
+  o->sn_depth = H.sn_depth.data();
+  o->sn_offset = H.sn_offset.data();
+  o->rows_ptr = H.rows_ptr.data();
+  o->rows = H.rows.data();
+  o->level_ptr = H.level_ptr.data();
+  o->level_sn = H.level_sn.data();
+  o->value_map = H.value_map.data();
+  o->flops_selinv = H.flops_selinv;
+  o->flops_selinv_exact = H.flops_selinv_exact;
+  o->flops_factor = H.flops_factor;
+  return PSELINV_OK;
+}
+
+int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out, int64_t cap,
+                    int64_t* count) {
+  if (!h || (which != 0 && which != 1) || !count || (cap > 0 && !out)) return PSELINV_ERR_ARG;
+  if (which == 0 ? !h->factored : h->nbatch == 0) return PSELINV_ERR_ARG;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
+  if (which == 0 && !h->selinv_plan[sched].built) {
+    const int rc = build_selinv_plan(h, sched);
+    if (rc != PSELINV_OK) return rc;
+  }
+  Plan& P = which == 0 ? h->selinv_plan[sched] : h->factor_plan;
+  const size_t ns = P.steps.size();
+  std::vector<cudaEvent_t> ev(ns + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(ev[0], st));
+  for (size_t i = 0; i < ns; i++) {
+    launch_step(h, P, P.steps[i], st);
+    CK(cudaEventRecord(ev[i + 1], st));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  *count = (int64_t)ns;
+  for (size_t i = 0; i < ns && (int64_t)i < cap; i++) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+    const Step& s = P.steps[i];
+    static const int kinds[] = {PSELINV_STEP_GEMM,    PSELINV_STEP_TRI_INV,    PSELINV_STEP_DIAG_LU,
+                                PSELINV_STEP_GATHER,  PSELINV_STEP_SCATTER_SUB, PSELINV_STEP_COPY,
+                                PSELINV_STEP_MEMSET,  PSELINV_STEP_SCATTER_VALUES};
+    out[i].kind = kinds[s.kind];
+    out[i].level = s.level;
+    out[i].tasks = s.n;
+    out[i].flops = s.flops;
+    out[i].bytes = (double)s.bytes;
+    out[i].ms = ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (which == 0) h->inverted = true;
+  return read_device_error(h, st);
+}
+
+int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_factor) {
+  if (!h) return PSELINV_ERR_ARG;
+  const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
+  if (launches_selinv)
+    *launches_selinv = h->selinv_plan[sched].built ? (int64_t)h->selinv_plan[sched].steps.size() : 0;
+  if (launches_factor)
+    *launches_factor = h->factor_plan.built ? (int64_t)h->factor_plan.steps.size() : 0;
+  return PSELINV_OK;
+}
+
+int pselinv_sync(pselinv_t h, void* stream) {
+  if (!h || h->opts.host_only) return PSELINV_ERR_ARG;
+  CK(cudaSetDevice(h->device));
+  return read_device_error(h, (cudaStream_t)stream);
+}
+
+int64_t pselinv_last_info(pselinv_t h) { return h ? h->last_info : -1; }
+
+void pselinv_free(pselinv_t h) {
+  if (!h) return;
+  if (!h->opts.host_only && h->device >= 0) {
+    cudaSetDevice(h->device);
+    free_numeric(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    cudaFree(h->dsym);
+    cudaFree(h->derr);
+  }
+  delete h;
+}
+
+}  // extern "C"

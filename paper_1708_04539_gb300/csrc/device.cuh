@@ -1,0 +1,178 @@
+// Device-side types shared by the CUDA sources: scalar types, the view of
+// the symbolic structure the kernels read, task/descriptor records and the
+// launch functions implemented in the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pselinv {
+
+// ---------------------------------------------------------------------------
+// scalars
+// ---------------------------------------------------------------------------
+struct cdouble {
+  double x, y;
+};
+
+__host__ __device__ inline double sc_zero(double) { return 0.0; }
+__host__ __device__ inline cdouble sc_zero(cdouble) { return {0.0, 0.0}; }
+__host__ __device__ inline double sc_one(double) { return 1.0; }
+__host__ __device__ inline cdouble sc_one(cdouble) { return {1.0, 0.0}; }
+
+__device__ __forceinline__ double fma_s(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ cdouble fma_s(cdouble a, cdouble b, cdouble c) {
+  return {fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y))};
+}
+__device__ __forceinline__ double mul_s(double a, double b) { return a * b; }
+__device__ __forceinline__ cdouble mul_s(cdouble a, cdouble b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__device__ __forceinline__ double sub_s(double a, double b) { return a - b; }
+__device__ __forceinline__ cdouble sub_s(cdouble a, cdouble b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ double add_s(double a, double b) { return a + b; }
+__device__ __forceinline__ cdouble add_s(cdouble a, cdouble b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ double scale_s(double a, double s) { return a * s; }
+__device__ __forceinline__ cdouble scale_s(cdouble a, double s) { return {a.x * s, a.y * s}; }
+__device__ __forceinline__ double div_s(double a, double b) { return a / b; }
+__device__ __forceinline__ cdouble div_s(cdouble a, cdouble b) {
+  // Smith's algorithm for complex division
+  if (fabs(b.x) >= fabs(b.y)) {
+    const double r = b.y / b.x, d = b.x + b.y * r;
+    return {(a.x + a.y * r) / d, (a.y - a.x * r) / d};
+  }
+  const double r = b.x / b.y, d = b.y + b.x * r;
+  return {(a.x * r + a.y) / d, (a.y * r - a.x) / d};
+}
+__device__ __forceinline__ bool is_zero(double a) { return a == 0.0; }
+__device__ __forceinline__ bool is_zero(cdouble a) { return a.x == 0.0 && a.y == 0.0; }
+__device__ __forceinline__ void atomic_add_s(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_s(cdouble* p, cdouble v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+
+// ---------------------------------------------------------------------------
+// structure view (device pointers), passed by value
+// ---------------------------------------------------------------------------
+struct SymDev {
+  const int32_t* sn_first;
+  const int32_t* sn_width;
+  const int32_t* sn_c;
+  const int64_t* sn_off;
+  const int64_t* rows_ptr;
+  const int32_t* rows_blk;
+  const int32_t* blk_sn;
+  const int32_t* blk_pb;
+  const int64_t* blk_rel;
+  const int32_t* relidx;
+  const int64_t* value_map;
+  int64_t storage;  // scalars per instance
+  int64_t nnz;
+  int32_t ns;
+  int32_t check;    // 1: bounds-check map reads
+  int64_t relidx_size;
+  int* err;         // [0] status, [1] info
+};
+
+enum DevErr { DEV_OK = 0, DEV_ZERO_PIVOT = 1, DEV_CHECK = 2 };
+
+__device__ __forceinline__ void set_error(int* err, int code, int info) {
+  if (atomicCAS(err, 0, code) == 0) err[1] = info;
+}
+
+// Storage slot (within one instance) of entry (R_K[p], R_K[q]) for p, q in
+// [0, c_K): the diagonal block of J when both rows lie in supernode J, the L
+// panel of J = supernode(R_K[q]) when R_K[p] lies in a later supernode, else
+// the U^T panel of I = supernode(R_K[p]).  rb = rows_ptr[K].
+__device__ __forceinline__ int64_t map_slot(const SymDev& S, int64_t rb, int p, int q) {
+  const int bp = S.rows_blk[rb + p];
+  const int bq = S.rows_blk[rb + q];
+  if (bp >= bq) {
+    const int J = S.blk_sn[bq];
+    const int64_t base = S.blk_rel[bq] - S.blk_pb[bq];
+    const int rp = S.relidx[base + p];
+    const int rq = S.relidx[base + q];
+    const int sJ = S.sn_width[J];
+    if (bp == bq) return S.sn_off[J] + rp + (int64_t)rq * sJ;
+    return S.sn_off[J] + (int64_t)sJ * sJ + rp + (int64_t)rq * S.sn_c[J];
+  }
+  const int I = S.blk_sn[bp];
+  const int64_t base = S.blk_rel[bp] - S.blk_pb[bp];
+  const int rq = S.relidx[base + q];  // position of R_K[q] in R_I
+  const int rp = S.relidx[base + p];  // local column of R_K[p] in I
+  const int sI = S.sn_width[I], cI = S.sn_c[I];
+  return S.sn_off[I] + (int64_t)sI * sI + (int64_t)cI * sI + rq + (int64_t)rp * cI;
+}
+
+// ---------------------------------------------------------------------------
+// batched GEMM: C = alpha op(A) op(B) + beta C, or C += alpha op(A) op(B)
+// with atomics (split over K).  Column-major operands; op = T reads the
+// stored matrix transposed.
+// ---------------------------------------------------------------------------
+struct GemmDesc {
+  const void* A;
+  const void* B;
+  void* C;
+  int M, N, K;
+  int lda, ldb, ldc;
+  int transA, transB;
+  double alpha, beta;
+  int atomic;   // 1: atomic accumulation into C (beta ignored)
+  int ksplit;   // number of K chunks (tasks carry the chunk index)
+};
+struct GemmTask {
+  int d, tm, tn, ks;
+};
+
+// per-supernode work item (instance, supernode, extra)
+struct SnTask {
+  int inst, K, a, b;
+};
+
+// contiguous copy segment
+struct CopySeg {
+  const void* src;
+  void* dst;
+  int64_t count;  // scalars
+};
+
+// ---------------------------------------------------------------------------
+// launch functions (kernels_*.cu)
+// ---------------------------------------------------------------------------
+enum DType { DT_F64 = 1, DT_C128 = 2 };
+
+// GEMM tile configurations (rows x cols of C per CTA)
+enum GemmCfg { GEMM_64x64 = 0, GEMM_32x32 = 1, GEMM_128x64 = 2, GEMM_NCFG = 3 };
+void launch_gemm(int dtype, int cfg, const GemmDesc* descs, const GemmTask* tasks, int ntasks,
+                 int grid, cudaStream_t st);
+int gemm_tile_m(int dtype, int cfg);
+int gemm_tile_n(int dtype, int cfg);
+
+// value scatter (A's entries into the storage of every instance)
+void launch_scatter_values(int dtype, const SymDev& S, const void* values, void* store,
+                           int nbatch, cudaStream_t st);
+// in-place LU of the diagonal blocks (no pivoting); tasks: {inst, K}
+void launch_diag_lu(int dtype, const SymDev& S, void* store, const SnTask* tasks, int ntasks,
+                    cudaStream_t st);
+// triangular inverses of the diagonal blocks of `store`:
+// tasks {inst, K, which (0 = L unit lower, 1 = U upper), first column};
+// result (s x s) at out + wofs[task index]
+void launch_tri_inv(int dtype, const SymDev& S, const void* store, void* out,
+                    const int64_t* wofs, const SnTask* tasks, int ntasks, int max_width,
+                    cudaStream_t st);
+// one-time kernel attributes (dynamic shared memory of tri_inv for max_width)
+cudaError_t prepare_dense_kernels(int dtype, int max_width);
+// G_K = Ainv(R_K, R_K) gathered from `store` into out + gofs[task]
+// tasks {inst, K, tile_p, tile_q} (32 x 32 tiles)
+void launch_gather(int dtype, const SymDev& S, const void* store, void* out,
+                   const int64_t* gofs, const SnTask* tasks, int ntasks, cudaStream_t st);
+// store(R_K, R_K) -= Sc_K (atomic) from src + sofs[task]; tasks as for gather
+void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src,
+                        const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st);
+void launch_copy(int dtype, const CopySeg* segs, int nseg, cudaStream_t st);
+// out[p] = store[inst * storage + value_map[p]]
+void launch_extract(int dtype, const SymDev& S, const void* store, int inst, void* out,
+                    cudaStream_t st);
+
+}  // namespace pselinv

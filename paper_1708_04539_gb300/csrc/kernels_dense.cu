@@ -1,0 +1,262 @@
+// Dense block kernels in FP64 / complex128:
+//   * a batched, persistent GEMM over a task list (the block products of
+//     Algorithm 1 steps 2-5 and of the supernodal LU),
+//   * the in-place LU without pivoting of diagonal blocks,
+//   * triangular inverses of the diagonal blocks (one warp per column).
+//
+// On GB300 the FP64 rate is the same for DFMA and the FP64 MMA path (about
+// 4 flop/clk/SM), so the FP64 GEMM is a register-tiled SIMT DFMA kernel:
+// it saturates the FP64 pipe with a 16x16 thread grid and 4x4 (real) or
+// 2x2 (complex) outputs per thread.
+#include "device.cuh"
+
+namespace pselinv {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T, int BM, int BN, int BK>
+struct GemmSmem {
+  T a[BK][BM];
+  T b[BK][BN];
+};
+
+template <typename T, int BM, int BN, int BK>
+__global__ void __launch_bounds__(kThreads)
+gemm_kernel(const GemmDesc* __restrict__ descs, const GemmTask* __restrict__ tasks, int ntasks) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ GemmSmem<T, BM, BN, BK> sm;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const GemmTask task = tasks[t];
+    const GemmDesc d = descs[task.d];
+    const T* __restrict__ A = (const T*)d.A;
+    const T* __restrict__ B = (const T*)d.B;
+    T* __restrict__ C = (T*)d.C;
+    const int m0 = task.tm * BM, n0 = task.tn * BN;
+    int kchunk = (d.K + d.ksplit - 1) / d.ksplit;
+    kchunk = (kchunk + BK - 1) / BK * BK;
+    const int kb = task.ks * kchunk;
+    const int ke = min(d.K, kb + kchunk);
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; i++)
+#pragma unroll
+      for (int j = 0; j < TN; j++) acc[i][j] = sc_zero(T());
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+      // A tile: BM x BK of op(A)
+      for (int e = tid; e < BM * BK; e += kThreads) {
+        int mm, kk;
+        if (d.transA) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+        const int m = m0 + mm, k = k0 + kk;
+        T v = sc_zero(T());
+        if (m < d.M && k < ke)
+          v = d.transA ? A[k + (int64_t)m * d.lda] : A[m + (int64_t)k * d.lda];
+        sm.a[kk][mm] = v;
+      }
+      // B tile: BK x BN of op(B)
+      for (int e = tid; e < BK * BN; e += kThreads) {
+        int kk, nn;
+        if (d.transB) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+        const int n = n0 + nn, k = k0 + kk;
+        T v = sc_zero(T());
+        if (n < d.N && k < ke)
+          v = d.transB ? B[n + (int64_t)k * d.ldb] : B[k + (int64_t)n * d.ldb];
+        sm.b[kk][nn] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; kk++) {
+        T av[TM], bv[TN];
+#pragma unroll
+        for (int i = 0; i < TM; i++) av[i] = sm.a[kk][tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < TN; j++) bv[j] = sm.b[kk][ty + 16 * j];
+#pragma unroll
+        for (int i = 0; i < TM; i++)
+#pragma unroll
+          for (int j = 0; j < TN; j++) acc[i][j] = fma_s(av[i], bv[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; i++) {
+      const int m = m0 + tx + 16 * i;
+      if (m >= d.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; j++) {
+        const int n = n0 + ty + 16 * j;
+        if (n >= d.N) continue;
+        T* c = C + m + (int64_t)n * d.ldc;
+        const T v = scale_s(acc[i][j], d.alpha);
+        if (d.atomic) {
+          atomic_add_s(c, v);
+        } else if (d.beta != 0.0) {
+          *c = add_s(v, scale_s(*c, d.beta));
+        } else {
+          *c = v;
+        }
+      }
+    }
+  }
+}
+
+// In-place LU without pivoting of the s x s diagonal block of supernode K
+// (right-looking, one CTA per block): L_KK unit lower below the diagonal,
+// U_KK on and above it.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+diag_lu_kernel(SymDev S, T* store, const SnTask* __restrict__ tasks, int ntasks) {
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SnTask task = tasks[t];
+    const int K = task.K;
+    const int s = S.sn_width[K];
+    T* D = store + (int64_t)task.inst * S.storage + S.sn_off[K];
+    for (int k = 0; k < s; k++) {
+      const T piv = D[k + (int64_t)k * s];
+      if (is_zero(piv)) {
+        if (threadIdx.x == 0) set_error(S.err, DEV_ZERO_PIVOT, S.sn_first[K] + k);
+        break;  // uniform across the block: every thread read the same pivot
+      }
+      for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x)
+        D[i + (int64_t)k * s] = div_s(D[i + (int64_t)k * s], piv);
+      __syncthreads();
+      const int m = s - k - 1;
+      for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+        const int i = k + 1 + idx % m, j = k + 1 + idx / m;
+        D[i + (int64_t)j * s] = sub_s(D[i + (int64_t)j * s], mul_s(D[i + (int64_t)k * s], D[k + (int64_t)j * s]));
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+// Triangular inverses of the diagonal block: which = 0 gives (L_KK)^{-1}
+// (unit lower), which = 1 gives (U_KK)^{-1} (upper).  Each warp solves for
+// one column j = first + warp: column-oriented substitution with the
+// working vector in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+tri_inv_kernel(SymDev S, const T* store, T* out, const int64_t* __restrict__ wofs,
+               const SnTask* __restrict__ tasks, int ntasks) {
+  extern __shared__ unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SnTask task = tasks[t];
+    const int K = task.K;
+    const int s = S.sn_width[K];
+    T* x = reinterpret_cast<T*>(smem_raw) + (int64_t)warp * s;
+    const T* D = store + (int64_t)task.inst * S.storage + S.sn_off[K];
+    T* W = out + wofs[t];
+    const int j = task.b + warp;
+    if (j < s) {
+      for (int i = lane; i < s; i += 32) x[i] = (i == j) ? sc_one(T()) : sc_zero(T());
+      __syncwarp();
+      if (task.a == 0) {
+        // L x = e_j, L unit lower
+        for (int k = j; k < s - 1; k++) {
+          const T xk = x[k];
+          __syncwarp();
+          if (!is_zero(xk))
+            for (int i = k + 1 + lane; i < s; i += 32)
+              x[i] = sub_s(x[i], mul_s(D[i + (int64_t)k * s], xk));
+          __syncwarp();
+        }
+      } else {
+        // U x = e_j, U upper
+        for (int k = j; k >= 0; k--) {
+          const T ukk = D[k + (int64_t)k * s];
+          if (is_zero(ukk)) {
+            if (lane == 0) set_error(S.err, DEV_ZERO_PIVOT, S.sn_first[K] + k);
+          }
+          const T xk = div_s(x[k], ukk);
+          __syncwarp();
+          if (lane == 0) x[k] = xk;
+          for (int i = lane; i < k; i += 32) x[i] = sub_s(x[i], mul_s(D[i + (int64_t)k * s], xk));
+          __syncwarp();
+        }
+      }
+      for (int i = lane; i < s; i += 32) W[i + (int64_t)j * s] = x[i];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int BM, int BN, int BK>
+void gemm_launch_t(const GemmDesc* descs, const GemmTask* tasks, int ntasks, int grid,
+                   cudaStream_t st) {
+  if (ntasks <= 0) return;
+  gemm_kernel<T, BM, BN, BK><<<grid, kThreads, 0, st>>>(descs, tasks, ntasks);
+}
+
+}  // namespace
+
+int gemm_tile_m(int dtype, int cfg) {
+  if (cfg == GEMM_128x64) return dtype == DT_F64 ? 128 : 64;
+  if (cfg == GEMM_32x32) return 32;
+  return dtype == DT_F64 ? 64 : 32;
+}
+int gemm_tile_n(int dtype, int cfg) {
+  if (cfg == GEMM_128x64) return dtype == DT_F64 ? 64 : 32;
+  if (cfg == GEMM_32x32) return dtype == DT_F64 ? 32 : 16;
+  return dtype == DT_F64 ? 64 : 32;
+}
+
+void launch_gemm(int dtype, int cfg, const GemmDesc* descs, const GemmTask* tasks, int ntasks,
+                 int grid, cudaStream_t st) {
+  if (dtype == DT_F64) {
+    switch (cfg) {
+      case GEMM_32x32: gemm_launch_t<double, 32, 32, 16>(descs, tasks, ntasks, grid, st); break;
+      case GEMM_128x64: gemm_launch_t<double, 128, 64, 8>(descs, tasks, ntasks, grid, st); break;
+      default: gemm_launch_t<double, 64, 64, 16>(descs, tasks, ntasks, grid, st); break;
+    }
+  } else {
+    switch (cfg) {
+      case GEMM_32x32: gemm_launch_t<cdouble, 32, 16, 16>(descs, tasks, ntasks, grid, st); break;
+      case GEMM_128x64: gemm_launch_t<cdouble, 64, 32, 8>(descs, tasks, ntasks, grid, st); break;
+      default: gemm_launch_t<cdouble, 32, 32, 16>(descs, tasks, ntasks, grid, st); break;
+    }
+  }
+}
+
+void launch_diag_lu(int dtype, const SymDev& S, void* store, const SnTask* tasks, int ntasks,
+                    cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  if (dtype == DT_F64)
+    diag_lu_kernel<double><<<grid, kThreads, 0, st>>>(S, (double*)store, tasks, ntasks);
+  else
+    diag_lu_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (cdouble*)store, tasks, ntasks);
+}
+
+int tri_inv_smem_bytes(int dtype, int max_width) {
+  return (kThreads / 32) * max_width * (dtype == DT_F64 ? 8 : 16);
+}
+
+cudaError_t prepare_dense_kernels(int dtype, int max_width) {
+  const int smem = tri_inv_smem_bytes(dtype, max_width);
+  if (dtype == DT_F64)
+    return cudaFuncSetAttribute(tri_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem);
+  return cudaFuncSetAttribute(tri_inv_kernel<cdouble>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem);
+}
+
+void launch_tri_inv(int dtype, const SymDev& S, const void* store, void* out,
+                    const int64_t* wofs, const SnTask* tasks, int ntasks, int max_width,
+                    cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  const int smem = tri_inv_smem_bytes(dtype, max_width);
+  if (dtype == DT_F64)
+    tri_inv_kernel<double><<<grid, kThreads, smem, st>>>(S, (const double*)store, (double*)out,
+                                                         wofs, tasks, ntasks);
+  else
+    tri_inv_kernel<cdouble><<<grid, kThreads, smem, st>>>(S, (const cdouble*)store, (cdouble*)out,
+                                                          wofs, tasks, ntasks);
+}
+
+}  // namespace pselinv

@@ -1,0 +1,200 @@
+// Index-map kernels (HBM/latency bound): the value scatter into the
+// supernodal storage, the gather of Ainv_{C,C} for a supernode (the
+// operand of Algorithm 1 steps 3 and 5), the scatter-subtract of a Schur
+// complement into the ancestors (supernodal LU), panel copies, and the
+// extraction of the selected entries (Algorithm 1 step 6, Theorem 2).
+#include "device.cuh"
+
+namespace pselinv {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTile = 32;
+
+__device__ __forceinline__ bool map_in_range(const SymDev& S, int64_t rb, int p, int q) {
+  const int bp = S.rows_blk[rb + p];
+  const int bq = S.rows_blk[rb + q];
+  const int b = bp >= bq ? bq : bp;
+  if (b < 0) return false;
+  const int64_t base = S.blk_rel[b] - S.blk_pb[b];
+  if (base + p < 0 || base + p >= S.relidx_size || base + q < 0 || base + q >= S.relidx_size)
+    return false;
+  const int64_t slot = map_slot(S, rb, p, q);
+  return slot >= 0 && slot < S.storage;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+scatter_values_kernel(SymDev S, const T* __restrict__ vals, T* store, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / S.nnz, p = e - b * S.nnz;
+    store[b * S.storage + S.value_map[p]] = vals[e];
+  }
+}
+
+// One 32 x 32 tile of G_K = Ainv(R_K, R_K) (column-major, ld = c) per task.
+// Entries below or on the block diagonal are read down panel columns; the
+// ones above it come from U^T panels and are read along their rows, so each
+// half of the tile is loaded with the lane index running over the
+// contiguous direction and transposed through shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+gather_kernel(SymDev S, const T* __restrict__ store, T* out, const int64_t* __restrict__ gofs,
+              const SnTask* __restrict__ tasks, int ntasks) {
+  __shared__ T tile[kTile][kTile + 1];
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SnTask task = tasks[t];
+    const int K = task.K;
+    const int c = S.sn_c[K];
+    const int64_t rb = S.rows_ptr[K];
+    const T* src = store + (int64_t)task.inst * S.storage;
+    T* G = out + gofs[t];
+    const int p0 = task.a * kTile, q0 = task.b * kTile;
+    // pass 1: lane runs over p (rows): lower/diagonal entries
+    for (int r = ly; r < kTile; r += kThreads / 32) {
+      const int p = p0 + lx, q = q0 + r;
+      if (p < c && q < c && S.rows_blk[rb + p] >= S.rows_blk[rb + q]) {
+        if (S.check && !map_in_range(S, rb, p, q)) {
+          set_error(S.err, DEV_CHECK, K);
+          tile[r][lx] = sc_zero(T());
+        } else {
+          tile[r][lx] = src[map_slot(S, rb, p, q)];
+        }
+      }
+    }
+    // pass 2: lane runs over q (columns): entries from U^T panels
+    for (int r = ly; r < kTile; r += kThreads / 32) {
+      const int p = p0 + r, q = q0 + lx;
+      if (p < c && q < c && S.rows_blk[rb + p] < S.rows_blk[rb + q]) {
+        if (S.check && !map_in_range(S, rb, p, q)) {
+          set_error(S.err, DEV_CHECK, K);
+          tile[lx][r] = sc_zero(T());
+        } else {
+          tile[lx][r] = src[map_slot(S, rb, p, q)];
+        }
+      }
+    }
+    __syncthreads();
+    for (int r = ly; r < kTile; r += kThreads / 32) {
+      const int p = p0 + lx, q = q0 + r;
+      if (p < c && q < c) G[p + (int64_t)q * c] = tile[r][lx];
+    }
+    __syncthreads();
+  }
+}
+
+// store(R_K, R_K) -= Sc (atomic: siblings of one level update shared ancestors)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+scatter_sub_kernel(SymDev S, T* store, const T* __restrict__ src, const int64_t* __restrict__ sofs,
+                   const SnTask* __restrict__ tasks, int ntasks) {
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SnTask task = tasks[t];
+    const int K = task.K;
+    const int c = S.sn_c[K];
+    const int64_t rb = S.rows_ptr[K];
+    T* dst = store + (int64_t)task.inst * S.storage;
+    const T* Sc = src + sofs[t];
+    const int p0 = task.a * kTile, q0 = task.b * kTile;
+    for (int r = ly; r < kTile; r += kThreads / 32) {
+      const int p = p0 + lx, q = q0 + r;
+      if (p >= c || q >= c) continue;
+      if (S.check && !map_in_range(S, rb, p, q)) {
+        set_error(S.err, DEV_CHECK, K);
+        continue;
+      }
+      const T v = Sc[p + (int64_t)q * c];
+      atomic_add_s(dst + map_slot(S, rb, p, q), scale_s(v, -1.0));
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+copy_kernel(const CopySeg* __restrict__ segs, int nseg) {
+  for (int s = blockIdx.y; s < nseg; s += gridDim.y) {
+    const CopySeg g = segs[s];
+    const T* a = (const T*)g.src;
+    T* b = (T*)g.dst;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.count;
+         e += (int64_t)gridDim.x * blockDim.x)
+      b[e] = a[e];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+extract_kernel(SymDev S, const T* __restrict__ store, T* out) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < S.nnz;
+       p += (int64_t)gridDim.x * blockDim.x)
+    out[p] = store[S.value_map[p]];
+}
+
+int grid_for(int64_t n) {
+  const int64_t g = (n + kThreads - 1) / kThreads;
+  return (int)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
+}
+
+}  // namespace
+
+void launch_scatter_values(int dtype, const SymDev& S, const void* values, void* store,
+                           int nbatch, cudaStream_t st) {
+  const int64_t total = (int64_t)nbatch * S.nnz;
+  if (total == 0) return;
+  if (dtype == DT_F64)
+    scatter_values_kernel<double><<<grid_for(total), kThreads, 0, st>>>(S, (const double*)values,
+                                                                      (double*)store, total);
+  else
+    scatter_values_kernel<cdouble><<<grid_for(total), kThreads, 0, st>>>(
+        S, (const cdouble*)values, (cdouble*)store, total);
+}
+
+void launch_gather(int dtype, const SymDev& S, const void* store, void* out, const int64_t* gofs,
+                   const SnTask* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  if (dtype == DT_F64)
+    gather_kernel<double><<<grid, kThreads, 0, st>>>(S, (const double*)store, (double*)out, gofs,
+                                                     tasks, ntasks);
+  else
+    gather_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (const cdouble*)store, (cdouble*)out,
+                                                      gofs, tasks, ntasks);
+}
+
+void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src,
+                        const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  if (dtype == DT_F64)
+    scatter_sub_kernel<double><<<grid, kThreads, 0, st>>>(S, (double*)store, (const double*)src,
+                                                          sofs, tasks, ntasks);
+  else
+    scatter_sub_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (cdouble*)store,
+                                                           (const cdouble*)src, sofs, tasks, ntasks);
+}
+
+void launch_copy(int dtype, const CopySeg* segs, int nseg, cudaStream_t st) {
+  if (nseg <= 0) return;
+  dim3 grid(8, nseg < 65535 ? nseg : 65535);
+  if (dtype == DT_F64)
+    copy_kernel<double><<<grid, kThreads, 0, st>>>(segs, nseg);
+  else
+    copy_kernel<cdouble><<<grid, kThreads, 0, st>>>(segs, nseg);
+}
+
+void launch_extract(int dtype, const SymDev& S, const void* store, int inst, void* out,
+                    cudaStream_t st) {
+  if (S.nnz == 0) return;
+  if (dtype == DT_F64)
+    extract_kernel<double><<<grid_for(S.nnz), kThreads, 0, st>>>(
+        S, (const double*)store + (int64_t)inst * S.storage, (double*)out);
+  else
+    extract_kernel<cdouble><<<grid_for(S.nnz), kThreads, 0, st>>>(
+        S, (const cdouble*)store + (int64_t)inst * S.storage, (cdouble*)out);
+}
+
+}  // namespace pselinv

@@ -1,0 +1,126 @@
+"""C-ABI library on the CPU: it loads, exports every declared symbol, and its
+host-only symbolic analysis equals the oracle's (independent) analysis bit
+for bit.  No compute call is made here."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import paper_1708_04539_gb300 as ps
+from paper_1708_04539_gb300.binding import supernodal_coordinates
+from helpers import csc_cols
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1708_04539_gb300 import build
+    build.build()
+
+
+def declared_functions():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(pselinv_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(ps.lib_path())
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_error_strings_and_defaults():
+    lib = ps.load_library()
+    for code in range(0, -9, -1):
+        assert lib.pselinv_error_string(code)
+    o = ps.binding.Opts()
+    lib.pselinv_default_opts(ctypes.byref(o))
+    assert o.max_supernode == 256 and o.relax_pct == 20 and o.use_graph == 1
+
+
+def _compare_with_oracle(p, relax):
+    h = ps.SelInv.from_problem(p, relax_pct=relax, host_only=True)
+    st = h.structure()
+    s = oracle.analyze(p, relax_pct=relax)
+    assert st["nsuper"] == s.nsup
+    assert np.array_equal(st["etree"], s.parent)
+    assert np.array_equal(st["sn_first"], s.supptr[:-1])
+    assert np.array_equal(st["sn_width"], np.diff(s.supptr))
+    assert np.array_equal(st["sn_parent"], s.sup_parent)
+    assert np.array_equal(st["sn_depth"], s.sup_depth)
+    for K in range(s.nsup):
+        assert np.array_equal(st["rows"][st["rows_ptr"][K]:st["rows_ptr"][K + 1]],
+                              s.supernode_rows(K))
+    # levels partition the supernodes by depth
+    for d in range(st["nlevels"]):
+        ks = st["level_sn"][st["level_ptr"][d]:st["level_ptr"][d + 1]]
+        assert np.all(st["sn_depth"][ks] == d)
+    # the supernodal storage covers exactly the oracle's pattern of L+U
+    rows, cols = supernodal_coordinates(st)
+    orows, ocols = s.lu_pattern()
+    assert rows.size == orows.size
+    assert np.array_equal(np.sort(rows * p.n + cols), np.sort(orows * p.n + ocols))
+    # the value map sends each entry of A to its permuted position
+    iperm = np.empty(p.n, dtype=np.int64)
+    iperm[p.perm] = np.arange(p.n)
+    vm = st["value_map"]
+    assert np.array_equal(rows[vm], iperm[p.rowind])
+    assert np.array_equal(cols[vm], iperm[csc_cols(p.colptr)])
+    # flop counts
+    w = st["sn_width"].astype(float)
+    c = np.diff(st["rows_ptr"]).astype(float)
+    assert np.isclose(st["flops_selinv"], np.sum(4 * c * c * w + 4 * c * w * w + 4 / 3 * w ** 3))
+    h.close()
+
+
+@pytest.mark.parametrize("relax", [0, 20, 60])
+@pytest.mark.parametrize("maker", [
+    lambda: gen.make_config(1),
+    lambda: gen.upwind_3d(8, 3, max_sn=32),
+    lambda: gen.stencil27_complex(5, 4, max_sn=48),
+    lambda: gen.dg_blocks(3, 8, 5, max_sn=24),
+    lambda: gen.random_struct_sym(150, 0.03, 6, max_sn=7),
+    lambda: gen.dense(30, 7, max_sn=8),
+    lambda: gen.tridiagonal(50, 8),
+])
+def test_host_analysis_matches_oracle(maker, relax):
+    _compare_with_oracle(maker(), relax)
+
+
+def test_host_analysis_config2_matches_oracle():
+    _compare_with_oracle(gen.make_config(2), 20)
+
+
+def test_analysis_rejects_bad_input():
+    p = gen.tridiagonal(5, 1)
+    bad = p.rowind.copy()
+    bad[1] = 4  # breaks both sorting and symmetry
+    with pytest.raises(ps.PselinvError):
+        ps.SelInv(p.n, p.colptr, bad, host_only=True)
+    n = 3
+    with pytest.raises(ps.PselinvError) as e:
+        ps.SelInv(n, np.array([0, 2, 3, 4]), np.array([0, 1, 1, 2]), host_only=True)
+    assert e.value.code == -2
+    with pytest.raises(ps.PselinvError):
+        ps.SelInv(p.n, p.colptr, p.rowind, perm=np.zeros(5, dtype=np.int64), host_only=True)
+
+
+def test_host_only_handle_refuses_compute():
+    p = gen.tridiagonal(5, 1)
+    h = ps.SelInv.from_problem(p, host_only=True)
+    with pytest.raises(ps.PselinvError):
+        h.factor(p.values)
