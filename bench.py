@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="skip the launch-by-launch replay (roofline fields become null)")
+    ap.add_argument("--size", type=int, default=40,
+                    help="grid side (40 = the benchmark workload; smaller for profiling captures)")
     return ap.parse_args()
 
 
@@ -245,7 +249,9 @@ def run_ours(args):
         dist.barrier()
     ps.load_library()
 
-    p = gen.make_config(2)
+    p = gen.make_config(2, size=args.size)
+    workload = WORKLOAD if args.size == 40 else WORKLOAD.replace(
+        "40^3 (n=64000)", f"{args.size}^3 (n={args.size ** 3})")
     sched = ps.SCHED_PER_SUPERNODE if args.schedule == "per_supernode" else ps.SCHED_LEVEL
     h = ps.SelInv.from_problem(p, relax_pct=20, schedule=sched, use_graph=not args.no_graph)
     st = h.structure()
@@ -297,7 +303,7 @@ def run_ours(args):
     value = world * flops / (ms_per_step * 1e-3) / 1e9
 
     # launch-by-launch replay with CUDA events on the same stream
-    prof = h.profile(0, stream=stream)
+    prof = [] if args.no_profile else h.profile(0, stream=stream)
     gemm = [r for r in prof if r["kind"] == "gemm"]
     tot_ms = sum(r["ms"] for r in prof)
     g_ms = sum(r["ms"] for r in gemm)
@@ -320,38 +326,42 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers: H2D values, factor,
     # selected inversion, D2H of the selected entries
-    vals_host = torch.from_numpy(p.values.copy()).pin_memory()
-    out_host = torch.zeros(p.nnz, dtype=torch.float64).pin_memory()
-    with torch.cuda.stream(stream):
-        h.factor(vals_host, stream=stream)
-        h.selinv(stream=stream)
-        h.get_selected(out_host, stream=stream)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for _ in range(args.e2e_steps):
+    e2e = None
+    if args.e2e_steps > 0:
+        vals_host = torch.from_numpy(p.values.copy()).pin_memory()
+        out_host = torch.zeros(p.nnz, dtype=torch.float64).pin_memory()
+        with torch.cuda.stream(stream):
             h.factor(vals_host, stream=stream)
             h.selinv(stream=stream)
             h.get_selected(out_host, stream=stream)
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * flops / e2e_s / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": int(p.nnz * 8), "d2h_bytes_per_step": int(p.nnz * 8),
-           "ms_per_step": e2e_s * 1e3, "includes": "H2D values, factor, selinv, extract, D2H"}
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for _ in range(args.e2e_steps):
+                h.factor(vals_host, stream=stream)
+                h.selinv(stream=stream)
+                h.get_selected(out_host, stream=stream)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * flops / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(p.nnz * 8), "d2h_bytes_per_step": int(p.nnz * 8),
+               "ms_per_step": e2e_s * 1e3,
+               "includes": "H2D values, factor, selinv, extract, D2H"}
 
-    nl = h.plan_stats()["launches_selinv"]
+    stats = h.plan_stats()
+    nl = stats["launches_selinv"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded generator, nested dissection)",
-        "config": {"workload": WORKLOAD, "n": p.n, "nnz": p.nnz,
+        "config": {"workload": workload, "n": p.n, "nnz": p.nnz,
                    "supernodes": int(st["nsuper"]), "levels": int(st["nlevels"]),
                    "flops_per_matrix": flops, "flops_relaxed_structure": st["flops_selinv"],
                    "schedule": args.schedule, "cuda_graph": not args.no_graph,
@@ -362,12 +372,15 @@ def run_ours(args):
         "factor_ms": factor_ms,
         "e2e": e2e,
         "gpu_launches": int((nl + 1) * args.steps),
+        "launches_factor": int(stats["launches_factor"]),
         "roofline": roofline,
         "kernel_shares": kinds,
         "clocks": clk.summary(),
     }
     h.close()
-    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+    if not prof:
+        line["roofline"] = None
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline and args.size == 40:
         line["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:
         print(json.dumps(line))
