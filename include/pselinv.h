@@ -190,6 +190,29 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
  * pselinv_factor issue with the current plans (0 if not built yet). */
 int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_factor);
 
+/* Allocation-free inverse of one LU-factored diagonal block (the paper has
+ * no counterpart; it serves callers that cannot allocate device memory, such
+ * as code running while a framework's caching allocator owns the device, or
+ * code that must avoid the device-wide synchronisation of cudaMalloc and
+ * cudaFree).
+ *   inv_out = (L U)^{-1} = U^{-1} L^{-1}, where lu_block (s x s, column-major,
+ *   leading dimension ld_in) holds L unit lower below the diagonal and U on
+ *   and above it -- the layout of a diagonal block of
+ *   PSELINV_LAYOUT_FACTORS.  inv_out: s x s, leading dimension ld_out.
+ * Both pointers are device memory owned by the caller; dtype is PSELINV_F64
+ * or PSELINV_C128; 1 <= s <= PSELINV_NOALLOC_MAX_S (larger s returns
+ * PSELINV_ERR_ARG).  The call allocates nothing: the two triangular inverses
+ * are kept in a 2 MiB array compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  The first call on a
+ * device looks up that array's address (with the device current), so make
+ * it before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller.  Work is
+ * queued on `stream`; a zero pivot in U gives non-finite output and is not
+ * reported. */
+#define PSELINV_NOALLOC_MAX_S 256
+int pselinv_block_inverse_noalloc(int dtype, int64_t s, const void* lu_block, int64_t ld_in,
+                                  void* inv_out, int64_t ld_out, void* stream);
+
 /* Wait for `stream` and report a device-side error recorded by earlier calls. */
 int pselinv_sync(pselinv_t h, void* stream);
 

@@ -28,6 +28,7 @@ _EXPORTS = [
     "pselinv_default_opts", "pselinv_analyze", "pselinv_factor", "pselinv_selinv",
     "pselinv_get_selected", "pselinv_get_structure", "pselinv_profile", "pselinv_plan_stats",
     "pselinv_sync", "pselinv_last_info", "pselinv_error_string", "pselinv_free",
+    "pselinv_block_inverse_noalloc",
 ]
 
 STEP_KINDS = {0: "gemm", 1: "tri_inv", 2: "diag_lu", 3: "gather", 4: "scatter_sub", 5: "copy",
@@ -117,6 +118,8 @@ def load_library():
     lib.pselinv_error_string.restype = ctypes.c_char_p
     lib.pselinv_free.argtypes = [P]
     lib.pselinv_free.restype = None
+    lib.pselinv_block_inverse_noalloc.argtypes = [ctypes.c_int, I64, P, I64, P, I64, P]
+    lib.pselinv_block_inverse_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -291,6 +294,22 @@ class SelInv:
 
     def __exit__(self, *a):
         self.close()
+
+
+NOALLOC_MAX_S = 256
+
+
+def block_inverse_noalloc(lu_block, out, s=None, stream=None):
+    """(L U)^{-1} of an LU-factored s x s block (column-major device arrays)
+    through the allocation-free entry point; see pselinv_block_inverse_noalloc."""
+    lib = load_library()
+    s = int(lu_block.shape[0]) if s is None else int(s)
+    dt = C128 if _is_complex(lu_block) else F64
+    rc = lib.pselinv_block_inverse_noalloc(dt, s, _ptr(lu_block), s, _ptr(out), s,
+                                           _stream(stream))
+    if rc != 0:
+        raise PselinvError(rc, "pselinv_block_inverse_noalloc")
+    return out
 
 
 def supernodal_coordinates(st: dict):
