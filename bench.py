@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--schedule", default="level", choices=["level", "per_supernode"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "ozaki"],
+                    help="fp64: every product in FP64; ozaki: FP16-sliced tensor-core products")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
@@ -178,6 +180,61 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline_from_profile(prof, slices):
+    """Roofline record of the kernel kind with the largest share of the step."""
+    kinds = {}
+    for r in prof:
+        k = kinds.setdefault(r["kind"], {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+        k["launches"] += 1
+        k["ms"] += r["ms"]
+        k["flops"] += r["flops"]
+        k["bytes"] += r["bytes"]
+    tot = sum(k["ms"] for k in kinds.values())
+    for k in kinds.values():
+        k["share"] = k["ms"] / tot if tot else 0.0
+    if not kinds:
+        return None, kinds
+    top = max(kinds, key=lambda k: kinds[k]["ms"])
+    k = kinds[top]
+    sec = k["ms"] * 1e-3
+    peaks = measured_peaks()
+    if top == "gemm":
+        achieved = k["flops"] / sec / 1e12
+        rec = {"bound": "alu", "kernel": "gemm_kernel<double,64,64,16> (FP64 DFMA)",
+               "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+               "traffic": traffic_from_profiles("gemm_kernel_f64")}
+    elif top == "ozaki_gemm":
+        pairs = slices * (slices + 1) // 2
+        achieved = pairs * k["flops"] / sec / 1e12
+        peak = float(peaks.get("bf16_tflops", 1925.5))
+        rec = {"bound": "tensor", "kernel": f"ozaki_gemm_kernel<{slices}> (tcgen05 kind::f16)",
+               "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "peak_source": "measured bf16 dense peak (MEASURED_PEAKS.json) x 1.0 nominal "
+                              "fp16/bf16 ratio",
+               "tensor_flops_per_fp64_flop": pairs,
+               "traffic": traffic_from_profiles("ozaki_gemm")}
+    else:
+        achieved = k["bytes"] / sec / 1e9
+        peak = float(peaks.get("hbm_gbs", 6778.7))
+        rec = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+               "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+               "traffic": traffic_from_profiles(top)}
+    rec["frac"] = rec["achieved"] / rec["peak"]
+    rec["share_of_step"] = k["share"]
+    rec["launches_per_step"] = k["launches"]
+    return rec, {n: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]}
+                 for n, v in kinds.items()}
+
+
 def traffic_from_profiles(kernel):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -270,8 +327,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     factor_ms = e0.elapsed_time(e1)
 
+    prec = ps.PREC_OZAKI_FP16 if args.precision == "ozaki" else ps.PREC_FP64
+
     def step():
-        h.selinv(stream=stream)
+        h.selinv(precision=prec, stream=stream)
         h.get_selected(out_dev, stream=stream)
 
     with torch.cuda.stream(stream):
@@ -304,25 +363,7 @@ def run_ours(args):
 
     # launch-by-launch replay with CUDA events on the same stream
     prof = [] if args.no_profile else h.profile(0, stream=stream)
-    gemm = [r for r in prof if r["kind"] == "gemm"]
-    tot_ms = sum(r["ms"] for r in prof)
-    g_ms = sum(r["ms"] for r in gemm)
-    g_fl = sum(r["flops"] for r in gemm)
-    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
-    kinds = {}
-    for r in prof:
-        k = kinds.setdefault(r["kind"], {"launches": 0, "ms": 0.0})
-        k["launches"] += 1
-        k["ms"] += r["ms"]
-    for k in kinds.values():
-        k["share"] = k["ms"] / tot_ms if tot_ms else 0.0
-    roofline = {"bound": "alu", "kernel": "gemm_kernel<double,64,64,16> (FP64 DFMA)",
-                "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_ALU_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
-                "traffic": traffic_from_profiles("gemm_kernel_f64"),
-                "share_of_step": g_ms / tot_ms if tot_ms else None,
-                "launches_per_step": len(gemm)}
+    roofline, kinds = roofline_from_profile(prof, slices=6)
 
     # end to end through the C ABI with host buffers: H2D values, factor,
     # selected inversion, D2H of the selected entries
@@ -332,7 +373,7 @@ def run_ours(args):
         out_host = torch.zeros(p.nnz, dtype=torch.float64).pin_memory()
         with torch.cuda.stream(stream):
             h.factor(vals_host, stream=stream)
-            h.selinv(stream=stream)
+            h.selinv(precision=prec, stream=stream)
             h.get_selected(out_host, stream=stream)
         torch.cuda.synchronize()
         if dist is not None:
@@ -341,7 +382,7 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             for _ in range(args.e2e_steps):
                 h.factor(vals_host, stream=stream)
-                h.selinv(stream=stream)
+                h.selinv(precision=prec, stream=stream)
                 h.get_selected(out_host, stream=stream)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
@@ -359,8 +400,10 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f16-slices",
         "data": "synthetic (seeded generator, nested dissection)",
+        "precision": args.precision,
         "config": {"workload": workload, "n": p.n, "nnz": p.nnz,
                    "supernodes": int(st["nsuper"]), "levels": int(st["nlevels"]),
                    "flops_per_matrix": flops, "flops_relaxed_structure": st["flops_selinv"],

@@ -44,7 +44,10 @@ enum StepKind {
   ST_SCATTER_SUB,
   ST_COPY,
   ST_MEMSET,
-  ST_SCATTER_VALUES
+  ST_SCATTER_VALUES,
+  ST_SLICE,
+  ST_OZGEMM,
+  ST_ZERO
 };
 
 struct Step {
@@ -52,7 +55,7 @@ struct Step {
   int cfg = 0;
   int n = 0;      // tasks / segments
   int grid = 0;
-  size_t tasks = 0, descs = 0, offs = 0;  // byte offsets into the plan arena
+  size_t tasks = 0, descs = 0, offs = 0, offs2 = 0;  // byte offsets into the plan arena
   void* ptr = nullptr;                    // memset target / store
   void* ptr2 = nullptr;                   // second buffer
   size_t bytes = 0;
@@ -112,7 +115,9 @@ struct pselinv_ctx {
   char* outstage = nullptr; // nnz values
   bool factored = false, inverted = false;
   Plan factor_plan;
-  Plan selinv_plan[2];  // by schedule
+  Plan selinv_plan[2][2];  // [precision][schedule]
+  int slices = 6;          // FP16 slices per operand of the split products
+  int last_precision = 0;
   cudaStream_t cap_stream = nullptr;
   int64_t last_info = -1;
   int last_status = 0;
@@ -194,7 +199,10 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
     for (int ks = 0; ks < g.ksplit; ks++)
       for (int tn = 0; tn < ceil_div(g.N, bn); tn++)
         for (int tm = 0; tm < ceil_div(g.M, bm); tm++) tasks.push_back({(int)d, tm, tn, ks});
-    flops += 2.0 * g.M * g.N * g.K * (dtype == DT_F64 ? 1 : 4);
+    double f = 2.0 * g.M * g.N * g.K;
+    if (g.tri == GEMM_TRI_LOWER_B || g.tri == GEMM_TRI_UPPER_B) f = (double)g.M * g.N * (g.N + 1);
+    if (g.tri == (GEMM_TRI_UPPER_A | GEMM_TRI_LOWER_B)) f = 2.0 * g.N * (double)g.N * g.N / 3.0;
+    flops += f * (dtype == DT_F64 ? 1 : 4);
     const double es = dtype == DT_F64 ? 8.0 : 16.0;
     bytes += es * ((double)g.M * g.K + (double)g.K * g.N +
                    (double)g.M * g.N * ((g.atomic || g.beta != 0.0) ? 2.0 : 1.0));
@@ -215,8 +223,9 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
 
 GemmDesc make_desc(const void* A, const void* B, void* C, int M, int N, int K, int lda, int ldb,
                    int ldc, int ta, int tb, double alpha, double beta, int atomic = 0,
-                   int ksplit = 1) {
+                   int ksplit = 1, int tri = 0) {
   GemmDesc d;
+  d.tri = tri;
   d.A = A;
   d.B = B;
   d.C = C;
@@ -233,6 +242,34 @@ GemmDesc make_desc(const void* A, const void* B, void* C, int M, int N, int K, i
   d.atomic = atomic;
   d.ksplit = ksplit < 1 ? 1 : ksplit;
   return d;
+}
+
+inline int64_t r64(int64_t r) { return (r + 63) / 64; }
+inline int64_t k32(int64_t k) { return (k + 31) / 32; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+inline size_t slice_bytes(int64_t R, int64_t Kd, int S) {
+  return align256((size_t)S * r64(R) * k32(Kd) * 4096);
+}
+inline size_t exps_bytes(int64_t R) { return align256((size_t)R * 4); }
+
+// bytes one supernode needs during a split-precision level: G, five slice
+// sets (G by rows, G by columns, Lhat, Uhat^T, Ainv(C,K)) and their exponents
+size_t ozaki_sn_bytes(int64_t s, int64_t c, int S) {
+  if (c == 0) return 0;
+  return align256((size_t)c * c * 8) + 2 * (slice_bytes(c, c, S) + exps_bytes(c)) +
+         3 * (slice_bytes(s, c, S) + exps_bytes(s)) + (size_t)2 * c * 8 + 256;
+}
+size_t ozaki_level_bytes(const HostSym& H, int64_t nb, int S) {
+  size_t mx = 0;
+  for (size_t d = 0; d + 1 < H.level_ptr.size(); d++) {
+    size_t b = 0;
+    for (int64_t i = H.level_ptr[d]; i < H.level_ptr[d + 1]; i++) {
+      const int64_t K = H.level_sn[i];
+      b += ozaki_sn_bytes(H.sn_width[K], H.rows_ptr[K + 1] - H.rows_ptr[K], S);
+    }
+    mx = std::max(mx, b * (size_t)nb);
+  }
+  return mx;
 }
 
 // scratch needed (bytes) by the factor and selected-inversion plans
@@ -257,7 +294,9 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
     fmax = std::max(fmax, f);
   }
   const int64_t sel = w + gmax;
-  return (size_t)(std::max(sel, fmax) * nb) * es + 256;
+  size_t bytes = (size_t)(std::max(sel, fmax) * nb) * es + 256;
+  if (es == 8) bytes = std::max(bytes, (size_t)(w * nb) * es + ozaki_level_bytes(H, nb, 6) + 4096);
+  return bytes;
 }
 
 int choose_cfg(int dtype) { return dtype == DT_F64 ? GEMM_64x64 : GEMM_64x64; }
@@ -310,8 +349,11 @@ int build_factor_plan(pselinv_ctx* h) {
         char* TL = h->scratch + (size_t)t0 * es;
         char* TU = TL + (size_t)c * s * es;
         char* Sc = h->scratch + (size_t)s0 * es;
-        trsm.push_back(make_desc(Lp, Uinv, TL, c, s, s, c, s, c, 0, 0, 1.0, 0.0));
-        trsm.push_back(make_desc(Up, Linv, TU, c, s, s, c, s, c, 0, 1, 1.0, 0.0));
+        // L = A U^-1, U^T = A^T L^-T: both B operands upper triangular
+        trsm.push_back(make_desc(Lp, Uinv, TL, c, s, s, c, s, c, 0, 0, 1.0, 0.0, 0, 1,
+                                 GEMM_TRI_UPPER_B));
+        trsm.push_back(make_desc(Up, Linv, TU, c, s, s, c, s, c, 0, 1, 1.0, 0.0, 0, 1,
+                                 GEMM_TRI_UPPER_B));
         schur.push_back(make_desc(TL, TU, Sc, c, c, s, c, c, c, 0, 1, 1.0, 0.0));
         for (int tq = 0; tq < ceil_div(c, 32); tq++)
           for (int tp = 0; tp < ceil_div(c, 32); tp++) {
@@ -369,9 +411,186 @@ int build_factor_plan(pselinv_ctx* h) {
 //   Ainv_CK = -G Lhat, (Ainv_KC)^T = -G^T Uhat^T, Ainv_KK += -Uhat Ainv_CK.
 // schedule = PER_SUPERNODE issues the three level launches per supernode.
 // ---------------------------------------------------------------------------
-int build_selinv_plan(pselinv_ctx* h, int schedule) {
+void add_zero_step(Plan& P, const std::vector<CopySeg>& segs, int level) {
+  if (segs.empty()) return;
+  Step z;
+  z.kind = ST_ZERO;
+  z.n = (int)segs.size();
+  z.tasks = P.push(segs);
+  z.level = level;
+  P.steps.push_back(z);
+}
+
+void add_slice_step(Plan& P, const std::vector<SliceDesc>& descs, int level) {
+  if (descs.empty()) return;
+  std::vector<SliceTask> tasks;
+  double bytes = 0;
+  for (size_t d = 0; d < descs.size(); d++) {
+    for (int rb = 0; rb < descs[d].R64; rb++) tasks.push_back({(int)d, rb});
+    bytes += 8.0 * descs[d].R * descs[d].Kd + 2.0 * descs[d].S * descs[d].R64 * 64.0 * descs[d].K32 * 32;
+  }
+  Step st;
+  st.kind = ST_SLICE;
+  st.n = (int)tasks.size();
+  st.descs = P.push(descs);
+  st.tasks = P.push(tasks);
+  st.bytes = (size_t)bytes;
+  st.level = level;
+  P.steps.push_back(st);
+}
+
+// ksplit so that a launch has about two CTAs per SM (one CTA fits an SM)
+int choose_ozaki_ksplit(const std::vector<OzDesc>& descs) {
+  int64_t tiles = 0, kmax = 1;
+  for (const auto& d : descs) {
+    tiles += (int64_t)ceil_div(d.M, 128) * ceil_div(d.N, 64);
+    kmax = std::max<int64_t>(kmax, ceil_div(d.K32, 4));
+  }
+  if (tiles == 0) return 1;
+  const int64_t want = (2 * 152 + tiles - 1) / tiles;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, kmax));
+}
+
+void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool force_atomic) {
+  if (descs.empty()) return;
+  const int ks = choose_ozaki_ksplit(descs);
+  std::vector<OzTask> tasks;
+  double flops = 0;
+  for (size_t d = 0; d < descs.size(); d++) {
+    OzDesc& g = descs[d];
+    g.ksplit = std::min(ks, std::max(1, ceil_div(g.K32, 4)));
+    g.atomic = (force_atomic || g.ksplit > 1) ? 1 : 0;
+    for (int k = 0; k < g.ksplit; k++)
+      for (int tn = 0; tn < ceil_div(g.N, 64); tn++)
+        for (int tm = 0; tm < ceil_div(g.M, 128); tm++) tasks.push_back({(int)d, tm, tn, k});
+    flops += 2.0 * g.M * g.N * (double)g.K32 * 32;
+  }
+  Step st;
+  st.kind = ST_OZGEMM;
+  st.cfg = S;
+  st.n = (int)tasks.size();
+  st.descs = P.push(descs);
+  st.tasks = P.push(tasks);
+  st.flops = flops;
+  st.level = level;
+  P.steps.push_back(st);
+}
+
+// One level (or one supernode) of the split-precision sweep: gather G,
+// slice G (by rows and by columns), Lhat and Uhat^T, sliced products for
+// steps 3 and 5, slice Ainv(C,K), sliced product for step 4 accumulated onto
+// D_K.  Scratch layout after the W region (byte offsets).
+void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, int64_t nb,
+                     int64_t gbase_scalars, int lev) {
   const HostSym& H = h->H;
-  Plan& P = h->selinv_plan[schedule];
+  const int S = h->slices;
+  std::vector<SnTask> gt;
+  std::vector<int64_t> gofs, mofs;
+  std::vector<SliceDesc> sl1, sl2;
+  std::vector<OzDesc> main, dg;
+  std::vector<CopySeg> zero;
+  size_t off = (size_t)gbase_scalars * 8;
+  auto take = [&](size_t bytes) {
+    off = align256(off);
+    const size_t o = off;
+    off += bytes;
+    return h->scratch + o;
+  };
+  // row and column maxima of every G of the level, zeroed by one memset
+  int64_t nmax = 0;
+  for (int64_t b = 0; b < nb; b++)
+    for (int64_t K : grp) nmax += 2 * (H.rows_ptr[K + 1] - H.rows_ptr[K]);
+  unsigned long long* maxbase = (unsigned long long*)take(align256((size_t)nmax * 8 + 8));
+  int64_t moff = 0;
+  auto slice_desc = [&](const double* src, int ld, int mode, int R, int Kd) {
+    SliceDesc d;
+    d.src = src;
+    d.ld = ld;
+    d.mode = mode;
+    d.R = R;
+    d.Kd = Kd;
+    d.S = S;
+    d.R64 = (int)r64(R);
+    d.K32 = (int)k32(Kd);
+    d.out = (__half*)take(slice_bytes(R, Kd, S));
+    d.exps = (int*)take(exps_bytes(R));
+    d.maxbits = nullptr;
+    return d;
+  };
+  for (int64_t b = 0; b < nb; b++)
+    for (int64_t K : grp) {
+      const int s = (int)H.sn_width[K], c = (int)(H.rows_ptr[K + 1] - H.rows_ptr[K]);
+      if (c == 0) continue;
+      char* G = take((size_t)c * c * 8);
+      const int64_t g0 = (G - h->scratch) / 8;
+      const int64_t m0 = moff;
+      moff += 2 * c;
+      for (int tq = 0; tq < ceil_div(c, 32); tq++)
+        for (int tp = 0; tp < ceil_div(c, 32); tp++) {
+          gt.push_back({(int)b, (int)K, tp, tq});
+          gofs.push_back(g0);
+          mofs.push_back(m0);
+        }
+      const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * 8;
+      const size_t lo = so + (size_t)s * s * 8, uo = lo + (size_t)c * s * 8;
+      SliceDesc gr = slice_desc((const double*)G, c, SLICE_ROWS, c, c);
+      SliceDesc gc = slice_desc((const double*)G, c, SLICE_COLS, c, c);
+      gr.maxbits = maxbase + m0;      // row maxima of G from the gather
+      gc.maxbits = maxbase + m0 + c;  // column maxima of G
+      const SliceDesc lh = slice_desc((const double*)(h->nf + lo), c, SLICE_COLS, s, c);
+      const SliceDesc uh = slice_desc((const double*)(h->nf + uo), c, SLICE_COLS, s, c);
+      const SliceDesc ak = slice_desc((const double*)(h->ainv + lo), c, SLICE_COLS, s, c);
+      sl1.push_back(gr);
+      sl1.push_back(gc);
+      sl1.push_back(lh);
+      sl1.push_back(uh);
+      sl2.push_back(ak);
+      OzDesc d{};
+      d.alpha = -1.0;
+      d.K32 = (int)k32(c);
+      // step 3: Ainv(C,K) = -G Lhat
+      d.A = gr.out; d.eA = gr.exps; d.A_R64 = gr.R64;
+      d.B = lh.out; d.eB = lh.exps; d.B_R64 = lh.R64;
+      d.C = (double*)(h->ainv + lo); d.ldc = c; d.M = c; d.N = s;
+      main.push_back(d);
+      // step 5: Ainv(K,C)^T = -G^T Uhat^T
+      d.A = gc.out; d.eA = gc.exps; d.A_R64 = gc.R64;
+      d.B = uh.out; d.eB = uh.exps; d.B_R64 = uh.R64;
+      d.C = (double*)(h->ainv + uo);
+      main.push_back(d);
+      // step 4: Ainv(K,K) = D_K - Uhat Ainv(C,K)
+      d.A = uh.out; d.eA = uh.exps; d.A_R64 = uh.R64;
+      d.B = ak.out; d.eB = ak.exps; d.B_R64 = ak.R64;
+      d.C = (double*)(h->ainv + so); d.ldc = s; d.M = s; d.N = s;
+      dg.push_back(d);
+      zero.push_back({nullptr, h->ainv + lo, (int64_t)2 * c * s});
+    }
+  if (gt.empty()) return;
+  Step ms;
+  ms.kind = ST_MEMSET;
+  ms.ptr = maxbase;
+  ms.bytes = (size_t)nmax * 8;
+  ms.level = lev;
+  P.steps.push_back(ms);
+  Step g;
+  g.kind = ST_GATHER;
+  g.n = (int)gt.size();
+  g.tasks = P.push(gt);
+  g.offs = P.push(gofs);
+  g.offs2 = P.push(mofs);
+  g.ptr2 = maxbase;
+  g.level = lev;
+  P.steps.push_back(g);
+  add_slice_step(P, sl1, lev);
+  if (choose_ozaki_ksplit(main) > 1) add_zero_step(P, zero, lev);
+  add_ozgemm_step(P, main, S, lev, false);
+  add_slice_step(P, sl2, lev);
+  add_ozgemm_step(P, dg, S, lev, true);
+}
+
+int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
+  const HostSym& H = h->H;
+  Plan& P = h->selinv_plan[precision][schedule];
   P.release();
   const size_t es = h->esize;
   const int dt = h->dtype;
@@ -401,11 +620,15 @@ int build_selinv_plan(pselinv_ctx* h, int schedule) {
         const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
         char* Linv = h->scratch + (size_t)w0 * es;
         char* Uinv = Linv + (size_t)s * s * es;
-        norm.push_back(make_desc(Uinv, Linv, h->ainv + so, s, s, s, s, s, s, 0, 0, 1.0, 0.0));
+        // D_K = Uinv Linv (upper x lower), Lhat = L Linv, Uhat^T = U^T Uinv^T (lower B)
+        norm.push_back(make_desc(Uinv, Linv, h->ainv + so, s, s, s, s, s, s, 0, 0, 1.0, 0.0, 0, 1,
+                                 GEMM_TRI_UPPER_A | GEMM_TRI_LOWER_B));
         if (c > 0) {
           const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
-          norm.push_back(make_desc(h->lu + lo, Linv, h->nf + lo, c, s, s, c, s, c, 0, 0, 1.0, 0.0));
-          norm.push_back(make_desc(h->lu + uo, Uinv, h->nf + uo, c, s, s, c, s, c, 0, 1, 1.0, 0.0));
+          norm.push_back(make_desc(h->lu + lo, Linv, h->nf + lo, c, s, s, c, s, c, 0, 0, 1.0, 0.0,
+                                   0, 1, GEMM_TRI_LOWER_B));
+          norm.push_back(make_desc(h->lu + uo, Uinv, h->nf + uo, c, s, s, c, s, c, 0, 1, 1.0, 0.0,
+                                   0, 1, GEMM_TRI_LOWER_B));
         }
       }
     Step t;
@@ -427,6 +650,10 @@ int build_selinv_plan(pselinv_ctx* h, int schedule) {
         groups.push_back({H.level_sn[i]});
     }
     for (const auto& grp : groups) {
+      if (precision == PSELINV_PREC_OZAKI_FP16) {
+        add_ozaki_level(h, P, grp, nb, gbase, (int)lev);
+        continue;
+      }
       std::vector<SnTask> gt;
       std::vector<int64_t> gofs;
       std::vector<GemmDesc> main, dg;
@@ -486,7 +713,9 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       break;
     case ST_GATHER:
       launch_gather(h->dtype, h->S, h->ainv, h->scratch, (const int64_t*)(a + s.offs),
-                    (const SnTask*)(a + s.tasks), s.n, st);
+                    (const SnTask*)(a + s.tasks), s.n, st,
+                    s.ptr2 ? (const int64_t*)(a + s.offs2) : nullptr,
+                    (unsigned long long*)s.ptr2);
       break;
     case ST_SCATTER_SUB:
       launch_scatter_sub(h->dtype, h->S, h->lu, h->scratch, (const int64_t*)(a + s.offs),
@@ -500,6 +729,16 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       break;
     case ST_SCATTER_VALUES:
       launch_scatter_values(h->dtype, h->S, h->staging, h->lu, (int)h->nbatch, st);
+      break;
+    case ST_SLICE:
+      launch_slice((const SliceDesc*)(a + s.descs), (const SliceTask*)(a + s.tasks), s.n, st);
+      break;
+    case ST_OZGEMM:
+      launch_ozaki_gemm(s.cfg, (const OzDesc*)(a + s.descs), (const OzTask*)(a + s.tasks), s.n,
+                        h->derr, st);
+      break;
+    case ST_ZERO:
+      launch_zero((const CopySeg*)(a + s.tasks), s.n, st);
       break;
   }
 }
@@ -529,7 +768,8 @@ int run_plan(pselinv_ctx* h, Plan& P, cudaStream_t st, bool graph) {
 
 void free_numeric(pselinv_ctx* h) {
   h->factor_plan.release();
-  for (auto& p : h->selinv_plan) p.release();
+  for (auto& pp : h->selinv_plan)
+    for (auto& p : pp) p.release();
   cudaFree(h->lu);
   cudaFree(h->nf);
   cudaFree(h->ainv);
@@ -554,6 +794,7 @@ int read_device_error(pselinv_ctx* h, cudaStream_t st) {
     h->last_info = herr[1];
     return PSELINV_ERR_CHECK;
   }
+  if (herr[0] == DEV_TIMEOUT) return PSELINV_ERR_TIMEOUT;
   return PSELINV_OK;
 }
 
@@ -654,6 +895,8 @@ int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, v
     CK(cudaMalloc(&h->staging, (size_t)nbatch * h->H.nnz * es + 256));
     CK(cudaMalloc(&h->outstage, (size_t)h->H.nnz * es + 256));
     CK(prepare_dense_kernels(dtype, h->max_width));
+    CK(prepare_ozaki_kernels());
+    h->slices = h->opts.slices <= 0 ? 6 : std::min(6, std::max(4, (int)h->opts.slices));
     int rc = build_factor_plan(h);
     if (rc != PSELINV_OK) return rc;
   }
@@ -672,15 +915,17 @@ int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, v
 int pselinv_selinv(pselinv_t h, int precision, void* stream) {
   if (!h || !h->factored) return PSELINV_ERR_ARG;
   if (precision < 0) precision = h->opts.precision;
-  if (precision != PSELINV_PREC_FP64) return PSELINV_ERR_UNSUPPORTED;
+  if (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16) return PSELINV_ERR_ARG;
+  if (precision == PSELINV_PREC_OZAKI_FP16 && h->dtype != PSELINV_F64) return PSELINV_ERR_UNSUPPORTED;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
-  Plan& P = h->selinv_plan[sched];
+  Plan& P = h->selinv_plan[precision][sched];
   if (!P.built) {
-    const int rc = build_selinv_plan(h, sched);
+    const int rc = build_selinv_plan(h, sched, precision);
     if (rc != PSELINV_OK) return rc;
   }
+  h->last_precision = precision;
   const int rc = run_plan(h, P, st, h->opts.use_graph != 0);
   if (rc != PSELINV_OK) return rc;
   h->inverted = true;
@@ -751,11 +996,12 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
-  if (which == 0 && !h->selinv_plan[sched].built) {
-    const int rc = build_selinv_plan(h, sched);
+  const int prec = h->last_precision;
+  if (which == 0 && !h->selinv_plan[prec][sched].built) {
+    const int rc = build_selinv_plan(h, sched, prec);
     if (rc != PSELINV_OK) return rc;
   }
-  Plan& P = which == 0 ? h->selinv_plan[sched] : h->factor_plan;
+  Plan& P = which == 0 ? h->selinv_plan[prec][sched] : h->factor_plan;
   const size_t ns = P.steps.size();
   std::vector<cudaEvent_t> ev(ns + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e));
@@ -773,7 +1019,8 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
     const Step& s = P.steps[i];
     static const int kinds[] = {PSELINV_STEP_GEMM,    PSELINV_STEP_TRI_INV,    PSELINV_STEP_DIAG_LU,
                                 PSELINV_STEP_GATHER,  PSELINV_STEP_SCATTER_SUB, PSELINV_STEP_COPY,
-                                PSELINV_STEP_MEMSET,  PSELINV_STEP_SCATTER_VALUES};
+                                PSELINV_STEP_MEMSET,  PSELINV_STEP_SCATTER_VALUES,
+                                PSELINV_STEP_SLICE,   PSELINV_STEP_OZAKI_GEMM, PSELINV_STEP_MEMSET};
     out[i].kind = kinds[s.kind];
     out[i].level = s.level;
     out[i].tasks = s.n;
@@ -789,8 +1036,8 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
 int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_factor) {
   if (!h) return PSELINV_ERR_ARG;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
-  if (launches_selinv)
-    *launches_selinv = h->selinv_plan[sched].built ? (int64_t)h->selinv_plan[sched].steps.size() : 0;
+  const Plan& sp = h->selinv_plan[h->last_precision][sched];
+  if (launches_selinv) *launches_selinv = sp.built ? (int64_t)sp.steps.size() : 0;
   if (launches_factor)
     *launches_factor = h->factor_plan.built ? (int64_t)h->factor_plan.steps.size() : 0;
   return PSELINV_OK;

@@ -2,6 +2,7 @@
 // the symbolic structure the kernels read, task/descriptor records and the
 // launch functions implemented in the kernel files.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -75,7 +76,7 @@ struct SymDev {
   int* err;         // [0] status, [1] info
 };
 
-enum DevErr { DEV_OK = 0, DEV_ZERO_PIVOT = 1, DEV_CHECK = 2 };
+enum DevErr { DEV_OK = 0, DEV_ZERO_PIVOT = 1, DEV_CHECK = 2, DEV_TIMEOUT = 3 };
 
 __device__ __forceinline__ void set_error(int* err, int code, int info) {
   if (atomicCAS(err, 0, code) == 0) err[1] = info;
@@ -120,7 +121,14 @@ struct GemmDesc {
   double alpha, beta;
   int atomic;   // 1: atomic accumulation into C (beta ignored)
   int ksplit;   // number of K chunks (tasks carry the chunk index)
+  int tri;      // zero structure of the operands: GEMM_TRI_* bits
 };
+// op(B)(k, n) = 0 for k < n (lower triangular B): a tile needs k >= n0
+constexpr int GEMM_TRI_LOWER_B = 1;
+// op(A)(m, k) = 0 for k < m (upper triangular A): a tile needs k >= m0
+constexpr int GEMM_TRI_UPPER_A = 2;
+// op(B)(k, n) = 0 for k > n (upper triangular B): a tile needs k < n0 + BN
+constexpr int GEMM_TRI_UPPER_B = 4;
 struct GemmTask {
   int d, tm, tn, ks;
 };
@@ -136,6 +144,42 @@ struct CopySeg {
   void* dst;
   int64_t count;  // scalars
 };
+
+// ---------------------------------------------------------------------------
+// split-precision products (kernels_ozaki.cu)
+// ---------------------------------------------------------------------------
+enum SliceMode { SLICE_ROWS = 0, SLICE_COLS = 1 };
+// One slice set: operand X with R rows (M or N direction) and Kd columns
+// (the contracted dimension).  SLICE_ROWS: X(r, k) = src[r + k*ld] (rows of
+// the stored column-major matrix); SLICE_COLS: X(r, k) = src[k + r*ld] (its
+// columns).  Output: S slices of R64 x K32 tiles of 4 KB, exponents[R].
+struct SliceDesc {
+  const double* src;
+  int ld, mode, R, Kd, S, R64, K32;
+  __half* out;
+  int* exps;
+  const unsigned long long* maxbits;  // precomputed max_k |X(r,k)| bit patterns, or null
+};
+struct SliceTask {
+  int d, rb;
+};
+struct OzDesc {
+  const __half* A;  // slice set of the M x K operand
+  const int* eA;
+  const __half* B;  // slice set of the N x K operand
+  const int* eB;
+  double* C;
+  int A_R64, B_R64, K32, M, N, ldc, ksplit, atomic;
+  double alpha;
+};
+struct OzTask {
+  int d, tm, tn, ks;
+};
+cudaError_t prepare_ozaki_kernels();
+void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, cudaStream_t st);
+void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
+                       cudaStream_t st);
+void launch_zero(const CopySeg* segs, int nseg, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // launch functions (kernels_*.cu)
@@ -164,9 +208,13 @@ void launch_tri_inv(int dtype, const SymDev& S, const void* store, void* out,
 // one-time kernel attributes (dynamic shared memory of tri_inv for max_width)
 cudaError_t prepare_dense_kernels(int dtype, int max_width);
 // G_K = Ainv(R_K, R_K) gathered from `store` into out + gofs[task]
-// tasks {inst, K, tile_p, tile_q} (32 x 32 tiles)
+// tasks {inst, K, tile_p, tile_q} (32 x 32 tiles).  With mofs != null
+// (real data only), the row and column maxima of |G_K| are also accumulated
+// (atomicMax on the bit patterns) into maxbase + mofs[task] (rows, c
+// entries) and maxbase + mofs[task] + c (columns).
 void launch_gather(int dtype, const SymDev& S, const void* store, void* out,
-                   const int64_t* gofs, const SnTask* tasks, int ntasks, cudaStream_t st);
+                   const int64_t* gofs, const SnTask* tasks, int ntasks, cudaStream_t st,
+                   const int64_t* mofs = nullptr, unsigned long long* maxbase = nullptr);
 // store(R_K, R_K) -= Sc_K (atomic) from src + sofs[task]; tasks as for gather
 void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src,
                         const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st);

@@ -38,8 +38,11 @@ gemm_kernel(const GemmDesc* __restrict__ descs, const GemmTask* __restrict__ tas
     const int m0 = task.tm * BM, n0 = task.tn * BN;
     int kchunk = (d.K + d.ksplit - 1) / d.ksplit;
     kchunk = (kchunk + BK - 1) / BK * BK;
-    const int kb = task.ks * kchunk;
-    const int ke = min(d.K, kb + kchunk);
+    int kb = task.ks * kchunk;
+    int ke = min(d.K, kb + kchunk);
+    if (d.tri & GEMM_TRI_LOWER_B) kb = max(kb, n0);
+    if (d.tri & GEMM_TRI_UPPER_A) kb = max(kb, m0);
+    if (d.tri & GEMM_TRI_UPPER_B) ke = min(ke, n0 + BN);
     T acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; i++)

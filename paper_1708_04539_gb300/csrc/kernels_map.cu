@@ -34,15 +34,21 @@ scatter_values_kernel(SymDev S, const T* __restrict__ vals, T* store, int64_t to
   }
 }
 
+__device__ __forceinline__ unsigned long long abs_bits_of(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
 // One 32 x 32 tile of G_K = Ainv(R_K, R_K) (column-major, ld = c) per task.
 // Entries below or on the block diagonal are read down panel columns; the
 // ones above it come from U^T panels and are read along their rows, so each
 // half of the tile is loaded with the lane index running over the
 // contiguous direction and transposed through shared memory.
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 gather_kernel(SymDev S, const T* __restrict__ store, T* out, const int64_t* __restrict__ gofs,
-              const SnTask* __restrict__ tasks, int ntasks) {
+              const SnTask* __restrict__ tasks, int ntasks, const int64_t* __restrict__ mofs,
+              unsigned long long* maxbase) {
   __shared__ T tile[kTile][kTile + 1];
   const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
@@ -81,6 +87,21 @@ gather_kernel(SymDev S, const T* __restrict__ store, T* out, const int64_t* __re
     for (int r = ly; r < kTile; r += kThreads / 32) {
       const int p = p0 + lx, q = q0 + r;
       if (p < c && q < c) G[p + (int64_t)q * c] = tile[r][lx];
+    }
+    if constexpr (sizeof(T) == 8) {
+      if (mofs) {
+        // row maxima (warp 0: lane = row p) and column maxima (warp 1: lane = column q)
+        unsigned long long* mrow = maxbase + mofs[t];
+        if (ly == 0 && p0 + lx < c) {
+          unsigned long long m = 0;
+          for (int q = 0; q < kTile && q0 + q < c; q++) m = max(m, abs_bits_of((double)tile[q][lx]));
+          atomicMax(mrow + p0 + lx, m);
+        } else if (ly == 1 && q0 + lx < c) {
+          unsigned long long m = 0;
+          for (int p = 0; p < kTile && p0 + p < c; p++) m = max(m, abs_bits_of((double)tile[lx][p]));
+          atomicMax(mrow + c + q0 + lx, m);
+        }
+      }
     }
     __syncthreads();
   }
@@ -154,15 +175,16 @@ void launch_scatter_values(int dtype, const SymDev& S, const void* values, void*
 }
 
 void launch_gather(int dtype, const SymDev& S, const void* store, void* out, const int64_t* gofs,
-                   const SnTask* tasks, int ntasks, cudaStream_t st) {
+                   const SnTask* tasks, int ntasks, cudaStream_t st, const int64_t* mofs,
+                   unsigned long long* maxbase) {
   if (ntasks <= 0) return;
   const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
   if (dtype == DT_F64)
     gather_kernel<double><<<grid, kThreads, 0, st>>>(S, (const double*)store, (double*)out, gofs,
-                                                     tasks, ntasks);
+                                                     tasks, ntasks, mofs, maxbase);
   else
     gather_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (const cdouble*)store, (cdouble*)out,
-                                                      gofs, tasks, ntasks);
+                                                      gofs, tasks, ntasks, nullptr, nullptr);
 }
 
 void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src,

@@ -1,0 +1,448 @@
+// Split-precision (Ozaki-scheme) products on the 5th-generation tensor
+// cores: the bulk GEMMs of Algorithm 1 steps 3-5 computed as sums of FP16
+// slice products accumulated exactly in FP32 and recombined in 64-bit
+// integers, then scaled back to FP64.
+//
+// Slicing.  Each row r of an operand X (rows = the M or N dimension, columns
+// = the contracted K dimension) is scaled by 2^-e_r with e_r the binary
+// exponent of max_k |X(r,k)| (so |x| 2^-e_r < 1), rounded to the fixed-point
+// integer Q = rint(x 2^{7S - e_r}) (|Q| <= 2^{7S}), and Q is written in
+// balanced base 128:  Q = sum_s a_s 128^{S-1-s},  |a_s| <= 64 for s >= 1,
+// |a_0| <= 128, so every digit is an integer held exactly by FP16 and
+//   x = 2^e_r sum_s a_s 2^{-7(s+1)} + O(2^{e_r - 7S - 1}).
+// The conversion works on the bit pattern of x with integer operations only
+// (the FP64 pipe of GB300 is too slow to slice with).
+// Products.  For slice pairs (s, t) with s + t = d <= S-1, the products
+// a_s(A) b_t(B) are summed in one FP32 tensor-memory accumulator per weight
+// d over 128 values of K: at most 6 pairs x 128 x 2^14 < 2^24, so every
+// partial sum is an exact integer.  After each 128-wide chunk the S
+// accumulators are drained into a 64-bit integer per output,
+//   T += sum_d P_d 2^{7(S-1-d)}  (< 2^60 over the whole K for S <= 6),
+// and at the end C = T 2^{e_r(A) + e_c(B) - 14 - 7(S-1)} in FP64.
+// The only rounding is the slice truncation and the final int64 -> FP64
+// conversion.
+//
+// Layouts.  A slice set stores, for every slice s, every 64-row block and
+// every 32-wide K block, a 4 KB tile in the tcgen05 canonical K-major layout
+// without swizzle: 8x16-byte core matrices, core (row group g, k group kg) at
+// byte (g * 4 + kg) * 128.  Two consecutive 64-row tiles form the 128-row A
+// operand (LBO = 128 B along K, SBO = 512 B along M); one tile is the B
+// operand of a 64-column output tile.
+#include <cuda_fp16.h>
+
+#include "device.cuh"
+
+namespace pselinv {
+
+namespace {
+
+constexpr int kSliceThreads = 256;
+constexpr int kGemmThreads = 128;
+constexpr int kTileBytes = 4096;  // 64 rows x 32 K x 2 bytes
+constexpr long kSpinLimit = 1L << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------------------
+// slicing
+// ---------------------------------------------------------------------------
+// |x| as the bit pattern of a non-negative double (orders like the value)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+// e with max < 2^e (the frexp exponent) from the bits of a non-negative max;
+// zero and subnormal maxima give 0 (those rows are sliced to zero)
+__device__ __forceinline__ int exp_of_max(unsigned long long bits) {
+  const int E = (int)(bits >> 52);
+  return E == 0 ? 0 : E - 1022;
+}
+// Q = rint(x 2^{sh0}) as a signed integer, from the bits of x (|Q| <= 2^{7S})
+__device__ __forceinline__ long long fixed_point(double x, int sh0) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return 0;
+  const long long M = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);  // x = +-M 2^{E-1075}
+  const int sh = E - 1075 + sh0;
+  long long q;
+  if (sh >= 0) {
+    q = M << (sh < 10 ? sh : 10);
+  } else {
+    const int r = -sh;
+    q = r >= 62 ? 0 : (M + (1ll << (r - 1))) >> r;
+  }
+  return b < 0 ? -q : q;
+}
+
+// One task = one 64-row block of a slice set, all K.  The block is staged
+// 64 x 32 at a time through shared memory (coalesced reads in either
+// orientation of the source), and thread t writes bytes [16t, 16t+16) of the
+// 4 KB tile of every slice (coalesced writes).
+__global__ void __launch_bounds__(kSliceThreads)
+slice_kernel(const SliceDesc* __restrict__ descs, const SliceTask* __restrict__ tasks, int ntasks) {
+  __shared__ double blk[64][33];
+  __shared__ unsigned long long mx[64];
+  __shared__ int rexp[64];
+  const int tid = threadIdx.x;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SliceTask task = tasks[t];
+    const SliceDesc d = descs[task.d];
+    const double* __restrict__ src = d.src;
+    const int r0 = task.rb * 64;
+    auto load_block = [&](int kb) {
+      if (d.mode == SLICE_ROWS) {
+        const int rl = tid & 63;
+        for (int kk = tid >> 6; kk < 32; kk += kSliceThreads / 64) {
+          const int r = r0 + rl, k = kb * 32 + kk;
+          blk[rl][kk] = (r < d.R && k < d.Kd) ? src[r + (int64_t)k * d.ld] : 0.0;
+        }
+      } else {
+        const int kk = tid & 31;
+        for (int rl = tid >> 5; rl < 64; rl += kSliceThreads / 32) {
+          const int r = r0 + rl, k = kb * 32 + kk;
+          blk[rl][kk] = (r < d.R && k < d.Kd) ? src[k + (int64_t)r * d.ld] : 0.0;
+        }
+      }
+    };
+    if (tid < 64) mx[tid] = (d.maxbits && r0 + tid < d.R) ? d.maxbits[r0 + tid] : 0ull;
+    __syncthreads();
+    if (!d.maxbits) {
+      for (int kb = 0; kb < d.K32; kb++) {
+        load_block(kb);
+        __syncthreads();
+        const int rl = tid & 63, part = tid >> 6;
+        unsigned long long m = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) m = max(m, abs_bits(blk[rl][part * 8 + q]));
+        atomicMax(&mx[rl], m);
+        __syncthreads();
+      }
+    }
+    if (tid < 64) {
+      const int e = exp_of_max(mx[tid]);
+      rexp[tid] = e;
+      if (r0 + tid < d.R) d.exps[r0 + tid] = e;
+    }
+    __syncthreads();
+    // thread -> (core matrix ci = tid / 8, row rr = tid % 8); ci = mg * 4 + kg
+    const int ci = tid >> 3, rr = tid & 7;
+    const int rl = (ci >> 2) * 8 + rr, kg = ci & 3;
+    const int sh0 = 7 * d.S - rexp[rl];
+    const int64_t slice_stride = (int64_t)d.R64 * d.K32 * (kTileBytes / 2);  // halves
+    for (int kb = 0; kb < d.K32; kb++) {
+      load_block(kb);
+      __syncthreads();
+      long long q[8];
+#pragma unroll
+      for (int j = 0; j < 8; j++) q[j] = fixed_point(blk[rl][kg * 8 + j], sh0);
+      __half* dst = d.out + ((int64_t)task.rb * d.K32 + kb) * (kTileBytes / 2) + tid * 8;
+      // balanced base-128 digits from the least significant slice upwards
+      for (int s = d.S - 1; s >= 0; s--) {
+        __align__(16) __half h[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          long long a = q[j];
+          if (s > 0) {
+            a = ((q[j] + 64) & 127) - 64;
+            q[j] = (q[j] - a) >> 7;
+          }
+          h[j] = __int2half_rn((int)a);
+        }
+        *reinterpret_cast<uint4*>(dst + s * slice_stride) = *reinterpret_cast<uint4*>(h);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  // K-major, no swizzle: LBO (K direction) = 128 B, SBO (M/N direction) = 512 B
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// kind::f16, FP16 x FP16 -> FP32, both operands K-major, M = 128, N = 64
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+// bounded wait on a phase parity; false after the spin limit
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (long it = 0; it < kSpinLimit; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// sliced GEMM: one 128 x 64 output tile (and one K range) per task
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ tasks, int ntasks,
+                  int* err) {
+  constexpr int kAB = S * 2 * kTileBytes;  // A stage bytes (128 rows)
+  constexpr int kBB = S * kTileBytes;      // B stage bytes (64 rows)
+  constexpr int kStage = kAB + kBB;
+  constexpr uint32_t kTmemCols = 512;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_full[2], bar_free[2], bar_acc;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int eB_s[64];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    mbar_init(smem_u32(&bar_full[0]), 1);
+    mbar_init(smem_u32(&bar_full[1]), 1);
+    mbar_init(smem_u32(&bar_free[0]), 1);
+    mbar_init(smem_u32(&bar_free[1]), 1);
+    mbar_init(smem_u32(&bar_acc), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  uint32_t ph_full[2] = {0, 0}, ph_free[2] = {0, 0}, ph_acc = 0;
+  bool ok = true;
+
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const OzTask task = tasks[t];
+    const OzDesc d = descs[task.d];
+    const int m0 = task.tm * 128, n0 = task.tn * 64;
+    int per = (d.K32 + d.ksplit - 1) / d.ksplit;
+    per = (per + 3) / 4 * 4;
+    const int kb0 = task.ks * per;
+    const int kb1 = min(d.K32, kb0 + per);
+    const int nkb = kb1 - kb0;
+    if (tid < 64) eB_s[tid] = (n0 + tid < d.N) ? d.eB[n0 + tid] : 0;
+    // per-thread 64-bit totals live in shared memory: tot[j * 128 + tid]
+    long long* tot = reinterpret_cast<long long*>(smem + 2 * kStage);
+    for (int j = 0; j < 64; j++) tot[j * kGemmThreads + tid] = 0;
+    __syncthreads();
+
+    // stage loader (thread 0): S slices x {2 A tiles, 1 B tile}
+    const bool a_second = 2 * task.tm + 1 < d.A_R64;
+    auto issue_load = [&](int kb, int buf) {
+      unsigned char* st = smem + buf * kStage;
+      const uint32_t fb = smem_u32(&bar_full[buf]);
+      const uint32_t bytes = (uint32_t)(S * (a_second ? 2 : 1) * kTileBytes + S * kTileBytes);
+      mbar_expect_tx(fb, bytes);
+      const int64_t a_sl = (int64_t)d.A_R64 * d.K32 * kTileBytes;
+      const int64_t b_sl = (int64_t)d.B_R64 * d.K32 * kTileBytes;
+      const unsigned char* A = reinterpret_cast<const unsigned char*>(d.A);
+      const unsigned char* B = reinterpret_cast<const unsigned char*>(d.B);
+      for (int s = 0; s < S; s++) {
+        const unsigned char* a0 = A + s * a_sl + ((int64_t)(2 * task.tm) * d.K32 + kb) * kTileBytes;
+        bulk_load(smem_u32(st + s * 2 * kTileBytes), a0, kTileBytes, fb);
+        if (a_second) {
+          const unsigned char* a1 = A + s * a_sl + ((int64_t)(2 * task.tm + 1) * d.K32 + kb) * kTileBytes;
+          bulk_load(smem_u32(st + s * 2 * kTileBytes + kTileBytes), a1, kTileBytes, fb);
+        }
+        const unsigned char* b0 = B + s * b_sl + ((int64_t)task.tn * d.K32 + kb) * kTileBytes;
+        bulk_load(smem_u32(st + kAB + s * kTileBytes), b0, kTileBytes, fb);
+      }
+    };
+
+    for (int i = 0; i < nkb; i++) {
+      const int buf = i & 1;
+      const bool chunk_end = (i % 4 == 3) || (i == nkb - 1);
+      if (tid == 0 && ok) {
+        if (i == 0) issue_load(kb0, 0);
+        if (i + 1 < nkb) {
+          const int nb = buf ^ 1;
+          if (i + 1 >= 2) {
+            ok = mbar_wait(smem_u32(&bar_free[nb]), ph_free[nb]);
+            ph_free[nb] ^= 1;
+          }
+          if (ok) issue_load(kb0 + i + 1, nb);
+        }
+        if (ok) ok = mbar_wait(smem_u32(&bar_full[buf]), ph_full[buf]);
+        ph_full[buf] ^= 1;
+        fence_after();
+        if (ok) {
+          const uint32_t st = smem_u32(smem + buf * kStage);
+          const bool first = (i % 4) == 0;
+#pragma unroll 1
+          for (int s = 0; s < S; s++)
+#pragma unroll 1
+            for (int tt = 0; tt < S - s; tt++) {
+              const uint32_t dt = tmem + (uint32_t)((s + tt) * 64);
+              const uint32_t sa = st + s * 2 * kTileBytes, sb = st + kAB + tt * kTileBytes;
+              mma_f16(dt, smem_desc(sa), smem_desc(sb), (first && s == 0) ? 0u : 1u);
+              mma_f16(dt, smem_desc(sa + 256), smem_desc(sb + 256), 1u);
+            }
+        }
+        mma_commit(smem_u32(&bar_free[buf]));
+        if (chunk_end) mma_commit(smem_u32(&bar_acc));
+      }
+      if (chunk_end) {
+        __syncwarp();
+        bool w = mbar_wait(smem_u32(&bar_acc), ph_acc);
+        ph_acc ^= 1;
+        if (!w) ok = false;
+        fence_after();
+        // drain: warp w holds TMEM lanes 32w..32w+31 = output rows
+#pragma unroll 1
+        for (int h = 0; h < 2; h++) {
+          long long part[32];
+#pragma unroll
+          for (int j = 0; j < 32; j++) part[j] = 0;
+#pragma unroll 1
+          for (int dd = 0; dd < S; dd++) {
+            const int shift = 7 * (S - 1 - dd);
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dd * 64 + h * 32), v);
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+              part[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shift;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; j++) tot[(h * 32 + j) * kGemmThreads + tid] += part[j];
+        }
+        fence_before();
+        __syncthreads();
+      }
+    }
+    if (tid == 0 && nkb > 0) {
+      // resynchronise the free barriers of the last two stages
+      for (int i = max(0, nkb - 2); i < nkb; i++) {
+        const int b = i & 1;
+        if (ok) ok = mbar_wait(smem_u32(&bar_free[b]), ph_free[b]);
+        ph_free[b] ^= 1;
+      }
+    }
+    if (!ok && lane == 0) atomicExch(err, DEV_TIMEOUT);
+    // epilogue: thread row r of the tile
+    const int r = m0 + warp * 32 + lane;
+    if (r < d.M && nkb > 0) {
+      const int ea = d.eA[r] - 14 - 7 * (S - 1);
+      double* C = d.C;
+#pragma unroll 4
+      for (int j = 0; j < 64; j++) {
+        const int n = n0 + j;
+        if (n < d.N) {
+          const double v = d.alpha * ldexp((double)tot[j * kGemmThreads + tid], ea + eB_s[j]);
+          double* c = C + r + (int64_t)n * d.ldc;
+          if (d.atomic) atomicAdd(c, v); else *c = v;
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+template <int S>
+constexpr int gemm_smem() {
+  return 2 * (S * 2 * kTileBytes + S * kTileBytes) + 64 * kGemmThreads * 8;
+}
+
+__global__ void zero_kernel(const CopySeg* __restrict__ segs, int nseg) {
+  for (int s = blockIdx.y; s < nseg; s += gridDim.y) {
+    const CopySeg g = segs[s];
+    double* b = (double*)g.dst;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.count;
+         e += (int64_t)gridDim.x * blockDim.x)
+      b[e] = 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t prepare_ozaki_kernels() {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(ozaki_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem<4>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(ozaki_gemm_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem<5>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(ozaki_gemm_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              gemm_smem<6>());
+}
+
+void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  slice_kernel<<<grid, kSliceThreads, 0, st>>>(descs, tasks, ntasks);
+}
+
+void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
+                       cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 4 ? ntasks : 152 * 4;
+  switch (S) {
+    case 4: ozaki_gemm_kernel<4><<<grid, kGemmThreads, gemm_smem<4>(), st>>>(descs, tasks, ntasks, err); break;
+    case 5: ozaki_gemm_kernel<5><<<grid, kGemmThreads, gemm_smem<5>(), st>>>(descs, tasks, ntasks, err); break;
+    default: ozaki_gemm_kernel<6><<<grid, kGemmThreads, gemm_smem<6>(), st>>>(descs, tasks, ntasks, err); break;
+  }
+}
+
+void launch_zero(const CopySeg* segs, int nseg, cudaStream_t st) {
+  if (nseg <= 0) return;
+  dim3 grid(8, nseg < 65535 ? nseg : 65535);
+  zero_kernel<<<grid, 256, 0, st>>>(segs, nseg);
+}
+
+}  // namespace pselinv

@@ -1,0 +1,96 @@
+"""Split-precision (FP16-sliced, tensor-core) selected inversion against the
+oracle and against the FP64 path.  Bound: selected-entry error below 1e-9
+(each entry relative to the largest selected entry of its row and column)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import gen
+from test_gpu_parity import compare_full, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+TOL_SPLIT = 1e-9
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_04539_gb300 import build
+    build.build()
+    return _t
+
+
+def run_split(torch, p, slices=0, **kw):
+    import paper_1708_04539_gb300 as ps
+    h = ps.SelInv.from_problem(p, slices=slices, **kw)
+    h.factor(torch.from_numpy(np.ascontiguousarray(p.values)).cuda())
+    h.selinv(precision=ps.PREC_OZAKI_FP16)
+    st = h.structure()
+    sn = h.get_selected(layout=ps.LAYOUT_SUPERNODAL)
+    pa = h.get_selected()
+    h.selinv(precision=ps.PREC_FP64)
+    sn64 = h.get_selected(layout=ps.LAYOUT_SUPERNODAL)
+    h.sync()
+    h.close()
+    return st, sn, pa, sn64
+
+
+CASES = [
+    ("cfg1", lambda: gen.make_config(1)),
+    ("upwind12", lambda: gen.upwind_3d(12, 61, max_sn=64)),
+    ("upwind16_wide", lambda: gen.upwind_3d(16, 62, max_sn=256)),
+    ("dg", lambda: gen.dg_blocks(3, 16, 63, max_sn=48)),
+    ("random", lambda: gen.random_struct_sym(300, 0.02, 64, max_sn=24)),
+    ("dense", lambda: gen.dense(200, 65, max_sn=40)),
+]
+
+
+@pytest.mark.parametrize("name,maker", CASES, ids=[c[0] for c in CASES])
+def test_split_matches_oracle(torch, name, maker):
+    p = maker()
+    st, sn, pa, sn64 = run_split(torch, p)
+    _, err = compare_full(p, st, sn, 0, 20, tol=TOL_SPLIT)
+    # and the FP64 path of the same handle
+    scale = np.abs(sn64).max()
+    assert np.abs(sn - sn64).max() <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("slices,bound", [(5, 1e-8), (4, 1e-6)])
+def test_fewer_slices_lose_accuracy_gracefully(torch, slices, bound):
+    p = gen.upwind_3d(10, 66, max_sn=64)
+    st, sn, pa, sn64 = run_split(torch, p, slices=slices)
+    err = np.abs(sn - sn64).max() / np.abs(sn64).max()
+    assert err <= bound
+
+
+def test_split_per_supernode_schedule(torch):
+    import paper_1708_04539_gb300 as ps
+    p = gen.upwind_3d(9, 67, max_sn=64)
+    st, sn, pa, sn64 = run_split(torch, p, schedule=ps.SCHED_PER_SUPERNODE)
+    assert np.abs(sn - sn64).max() <= 1e-9 * np.abs(sn64).max()
+
+
+def test_split_complex_is_reported_unsupported(torch):
+    import paper_1708_04539_gb300 as ps
+    p = gen.stencil27_complex(4, 68, max_sn=32)
+    h = ps.SelInv.from_problem(p)
+    h.factor(torch.from_numpy(p.values).cuda())
+    with pytest.raises(ps.PselinvError) as e:
+        h.selinv(precision=ps.PREC_OZAKI_FP16)
+    assert e.value.code == -8
+    h.close()
+
+
+@pytest.mark.slow
+def test_split_config2_full_size(torch):
+    p = gen.make_config(2)
+    st, sn, pa, sn64 = run_split(torch, p)
+    from paper_1708_04539_gb300.binding import supernodal_coordinates
+    from helpers import selected_error
+    rows, cols = supernodal_coordinates(st)
+    err = selected_error(sn, sn64, rows, cols, p.n)
+    assert err < TOL_SPLIT, err
