@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true",
                     help="skip the launch-by-launch replay (roofline fields become null)")
+    ap.add_argument("--tune", default="exhaustive", choices=["none", "exhaustive"],
+                    help="launch-shape autotuning before the timed region (untimed, like the factorisation)")
+    ap.add_argument("--dump-profile", default=None,
+                    help="write the launch-by-launch profile (JSON) to this path")
     ap.add_argument("--size", type=int, default=40,
                     help="grid side (40 = the benchmark workload; smaller for profiling captures)")
     return ap.parse_args()
@@ -328,6 +332,13 @@ def run_ours(args):
     factor_ms = e0.elapsed_time(e1)
 
     prec = ps.PREC_OZAKI_FP16 if args.precision == "ozaki" else ps.PREC_FP64
+    tune_s = 0.0
+    if args.tune == "exhaustive":
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            h.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE, stream=stream)
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t0
 
     def step():
         h.selinv(precision=prec, stream=stream)
@@ -364,6 +375,9 @@ def run_ours(args):
     # launch-by-launch replay with CUDA events on the same stream
     prof = [] if args.no_profile else h.profile(0, stream=stream)
     roofline, kinds = roofline_from_profile(prof, slices=6)
+    if args.dump_profile and rank == 0:
+        with open(args.dump_profile, "w") as f:
+            json.dump({"precision": args.precision, "size": args.size, "steps": prof}, f)
 
     # end to end through the C ABI with host buffers: H2D values, factor,
     # selected inversion, D2H of the selected entries
@@ -408,6 +422,7 @@ def run_ours(args):
                    "supernodes": int(st["nsuper"]), "levels": int(st["nlevels"]),
                    "flops_per_matrix": flops, "flops_relaxed_structure": st["flops_selinv"],
                    "schedule": args.schedule, "cuda_graph": not args.no_graph,
+                   "tuning": args.tune, "tuning_seconds": tune_s,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.0f MB of factors read per step)"
                          % (st["storage_size"] * 8 / 1e6)},

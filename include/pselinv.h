@@ -73,7 +73,7 @@ enum pselinv_layout {
 };
 
 typedef struct pselinv_opts {
-  int32_t max_supernode; /* widest supernode (columns), >= 1; default 256 */
+  int32_t max_supernode; /* widest supernode (columns), 1..256; default 256 */
   int32_t relax_pct;     /* max share (%) of explicit zeros a relaxed supernode adds; default 20 */
   int32_t precision;     /* pselinv_precision used by pselinv_selinv when it is passed -1 */
   int32_t slices;        /* FP16 slices per operand for PREC_OZAKI_FP16; 0 = default */
@@ -212,6 +212,69 @@ int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_
 #define PSELINV_NOALLOC_MAX_S 256
 int pselinv_block_inverse_noalloc(int dtype, int64_t s, const void* lu_block, int64_t ld_in,
                                   void* inv_out, int64_t ld_out, void* stream);
+
+/* One measurement of the autotuner; also the training data of the learned
+ * cost model.  Not from the paper: tile shapes and K splits are the GPU
+ * batching parameters of the level sweep. */
+typedef struct pselinv_tune_record {
+  int32_t precision; /* pselinv_precision of the plan */
+  int32_t level;     /* tree level of the launch (-1 = normalisation) */
+  int32_t slot;      /* 0 normalisation, 1 steps 3 and 5, 2 step 4 */
+  int32_t kind;      /* PSELINV_STEP_GEMM (param = tile config 0..2: 64x64, 32x32, 128x64)
+                        or PSELINV_STEP_OZAKI_GEMM (param = K split 1..16) */
+  int32_t param;     /* the candidate timed */
+  int32_t chosen;    /* 1 for the candidate the tuner kept */
+  float feat[8];     /* log2(1 + x) of: products, flops, max M, max N, max K, mean M, N, K */
+  double ms;         /* device time of the launch (CUDA events) */
+} pselinv_tune_record;
+
+enum pselinv_tune_mode {
+  PSELINV_TUNE_RESET = 0,      /* back to the built-in heuristic */
+  PSELINV_TUNE_EXHAUSTIVE = 1, /* time every candidate of every tunable launch, keep the best */
+  PSELINV_TUNE_MODEL = 2       /* pick candidates with a trained cost model (no timing) */
+};
+
+/* Autotune the selected-inversion plan of `precision` for the factored
+ * instances (Algorithm 1's products are unchanged; only launch shapes
+ * change).  EXHAUSTIVE runs the plan once per candidate with CUDA events
+ * around every launch (the results it leaves are valid); MODEL needs
+ * `model` (see pselinv_model_*).  Synchronises `stream`. */
+typedef struct pselinv_model* pselinv_model_t;
+int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, void* stream);
+
+/* Learned cost model of the launch shapes (not from the paper): an MLP
+ *   x (16) -> tanh(W1 x + b1) (H) -> tanh(W2 h1 + b2) (H) -> w3 . h2 + b3
+ * predicting log(ms) of a launch.  Input x of a record: feat[0..7] / 32;
+ * [8] kind is GEMM; [9] kind is OZAKI_GEMM; [10..12] one-hot GEMM tile config;
+ * [13] log2(K split) / 4 for OZAKI_GEMM; [14] slot / 2; [15] precision.
+ * Parameters (float32, flat): W1 (H x 16, row-major), b1 (H), W2 (H x H),
+ * b2 (H), w3 (H), b3 (1).  Weights live on the current device; training and
+ * inference run there (one single-CTA kernel runs all epochs of full-batch
+ * Adam on the mean squared error of log(ms)).
+ * create: hidden in [1, 64], Glorot-uniform weights from SplitMix64(seed).
+ * train: n >= 1 records (their ms are the targets), epochs >= 1, lr > 0;
+ *   *final_loss (nullable) = loss of the last epoch's forward pass.
+ * gradients: gradient of the loss (same layout as the parameters) without
+ *   updating them; *loss_out (nullable) = the loss.
+ * predict: pred_ms[i] = exp(network(record i)) (record ms ignored).
+ * get/set_params: copy the flat parameters out / in (set also clears Adam).
+ * encode: the network input of each record (16 floats per record, host).
+ * All synchronise `stream` and return PSELINV_* codes. */
+int pselinv_model_create(int32_t hidden, uint64_t seed, pselinv_model_t* out);
+int pselinv_model_train(pselinv_model_t m, const pselinv_tune_record* recs, int64_t n,
+                        int32_t epochs, float lr, void* stream, float* final_loss);
+int pselinv_model_gradients(pselinv_model_t m, const pselinv_tune_record* recs, int64_t n,
+                            float* grad_out, float* loss_out, void* stream);
+int pselinv_model_predict(pselinv_model_t m, const pselinv_tune_record* recs, int64_t n,
+                          double* pred_ms, void* stream);
+int pselinv_model_get_params(pselinv_model_t m, float* out, int64_t cap, int64_t* count);
+int pselinv_model_set_params(pselinv_model_t m, const float* in, int64_t count);
+int pselinv_model_encode(const pselinv_tune_record* recs, int64_t n, float* x_out);
+void pselinv_model_free(pselinv_model_t m);
+
+/* The records of the last exhaustive tuning (*count = number of records;
+ * up to cap are copied). */
+int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int64_t* count);
 
 /* Wait for `stream` and report a device-side error recorded by earlier calls. */
 int pselinv_sync(pselinv_t h, void* stream);

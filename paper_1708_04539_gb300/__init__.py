@@ -21,4 +21,8 @@ from .binding import (  # noqa: F401
     LAYOUT_PATTERN_A,
     LAYOUT_SUPERNODAL,
     LAYOUT_FACTORS,
+    CostModel,
+    TUNE_RESET,
+    TUNE_EXHAUSTIVE,
+    TUNE_MODEL,
 )

@@ -28,8 +28,13 @@ _EXPORTS = [
     "pselinv_default_opts", "pselinv_analyze", "pselinv_factor", "pselinv_selinv",
     "pselinv_get_selected", "pselinv_get_structure", "pselinv_profile", "pselinv_plan_stats",
     "pselinv_sync", "pselinv_last_info", "pselinv_error_string", "pselinv_free",
-    "pselinv_block_inverse_noalloc",
+    "pselinv_block_inverse_noalloc", "pselinv_tune", "pselinv_tune_records",
+    "pselinv_model_create", "pselinv_model_train", "pselinv_model_gradients",
+    "pselinv_model_predict", "pselinv_model_get_params", "pselinv_model_set_params",
+    "pselinv_model_encode", "pselinv_model_free",
 ]
+
+TUNE_RESET, TUNE_EXHAUSTIVE, TUNE_MODEL = 0, 1, 2
 
 STEP_KINDS = {0: "gemm", 1: "tri_inv", 2: "diag_lu", 3: "gather", 4: "scatter_sub", 5: "copy",
               6: "memset", 7: "scatter_values", 8: "slice", 9: "ozaki_gemm", 10: "recombine"}
@@ -58,6 +63,12 @@ class Opts(ctypes.Structure):
 
 
 _P64 = ctypes.POINTER(ctypes.c_int64)
+
+
+class TuneRecord(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("level", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("kind", ctypes.c_int32), ("param", ctypes.c_int32), ("chosen", ctypes.c_int32),
+                ("feat", ctypes.c_float * 8), ("ms", ctypes.c_double)]
 
 
 class StepStat(ctypes.Structure):
@@ -120,6 +131,30 @@ def load_library():
     lib.pselinv_free.restype = None
     lib.pselinv_block_inverse_noalloc.argtypes = [ctypes.c_int, I64, P, I64, P, I64, P]
     lib.pselinv_block_inverse_noalloc.restype = ctypes.c_int
+    RP = ctypes.POINTER(TuneRecord)
+    lib.pselinv_tune.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.pselinv_tune.restype = ctypes.c_int
+    lib.pselinv_tune_records.argtypes = [P, RP, I64, ctypes.POINTER(I64)]
+    lib.pselinv_tune_records.restype = ctypes.c_int
+    lib.pselinv_model_create.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(P)]
+    lib.pselinv_model_create.restype = ctypes.c_int
+    lib.pselinv_model_train.argtypes = [P, RP, I64, ctypes.c_int32, ctypes.c_float, P,
+                                        ctypes.POINTER(ctypes.c_float)]
+    lib.pselinv_model_train.restype = ctypes.c_int
+    lib.pselinv_model_gradients.argtypes = [P, RP, I64, ctypes.POINTER(ctypes.c_float),
+                                            ctypes.POINTER(ctypes.c_float), P]
+    lib.pselinv_model_gradients.restype = ctypes.c_int
+    lib.pselinv_model_predict.argtypes = [P, RP, I64, ctypes.POINTER(ctypes.c_double), P]
+    lib.pselinv_model_predict.restype = ctypes.c_int
+    lib.pselinv_model_get_params.argtypes = [P, ctypes.POINTER(ctypes.c_float), I64,
+                                             ctypes.POINTER(I64)]
+    lib.pselinv_model_get_params.restype = ctypes.c_int
+    lib.pselinv_model_set_params.argtypes = [P, ctypes.POINTER(ctypes.c_float), I64]
+    lib.pselinv_model_set_params.restype = ctypes.c_int
+    lib.pselinv_model_encode.argtypes = [RP, I64, ctypes.POINTER(ctypes.c_float)]
+    lib.pselinv_model_encode.restype = ctypes.c_int
+    lib.pselinv_model_free.argtypes = [P]
+    lib.pselinv_model_free.restype = None
     _lib = lib
     return lib
 
@@ -249,6 +284,21 @@ class SelInv:
                     "pselinv_plan_stats")
         return {"launches_selinv": a.value, "launches_factor": b.value}
 
+    def tune(self, precision=PREC_FP64, mode=TUNE_EXHAUSTIVE, model=None, stream=None):
+        """Autotune the launch shapes of the selected-inversion plan."""
+        mh = None if model is None else model._h
+        self._check(self._lib.pselinv_tune(self._h, int(precision), int(mode), mh, _stream(stream)),
+                    "pselinv_tune")
+
+    def tune_records(self):
+        cnt = ctypes.c_int64(0)
+        self._check(self._lib.pselinv_tune_records(self._h, None, 0, ctypes.byref(cnt)),
+                    "pselinv_tune_records")
+        buf = (TuneRecord * max(1, cnt.value))()
+        self._check(self._lib.pselinv_tune_records(self._h, buf, cnt.value, ctypes.byref(cnt)),
+                    "pselinv_tune_records")
+        return [buf[i] for i in range(cnt.value)]
+
     def sync(self, stream=None):
         self._check(self._lib.pselinv_sync(self._h, _stream(stream)), "pselinv_sync")
 
@@ -294,6 +344,105 @@ class SelInv:
 
     def __exit__(self, *a):
         self.close()
+
+
+class CostModel:
+    """The learned launch-shape cost model (an MLP on the device)."""
+
+    def __init__(self, hidden=32, seed=1):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self._lib.pselinv_model_create(int(hidden), int(seed), ctypes.byref(h))
+        if rc != 0:
+            raise PselinvError(rc, "pselinv_model_create")
+        self._h = h
+
+    @staticmethod
+    def _recs(records):
+        arr = (TuneRecord * len(records))()
+        for i, r in enumerate(records):
+            arr[i] = r
+        return arr
+
+    def train(self, records, epochs=2000, lr=3e-3, stream=None):
+        loss = ctypes.c_float(0)
+        rc = self._lib.pselinv_model_train(self._h, self._recs(records), len(records), int(epochs),
+                                           float(lr), _stream(stream), ctypes.byref(loss))
+        if rc != 0:
+            raise PselinvError(rc, "pselinv_model_train")
+        return loss.value
+
+    def gradients(self, records, stream=None):
+        n = self.num_params()
+        g = (ctypes.c_float * n)()
+        loss = ctypes.c_float(0)
+        rc = self._lib.pselinv_model_gradients(self._h, self._recs(records), len(records), g,
+                                               ctypes.byref(loss), _stream(stream))
+        if rc != 0:
+            raise PselinvError(rc, "pselinv_model_gradients")
+        return np.array(g[:], dtype=np.float32), loss.value
+
+    def predict(self, records, stream=None):
+        out = (ctypes.c_double * len(records))()
+        rc = self._lib.pselinv_model_predict(self._h, self._recs(records), len(records), out,
+                                             _stream(stream))
+        if rc != 0:
+            raise PselinvError(rc, "pselinv_model_predict")
+        return np.array(out[:])
+
+    def num_params(self):
+        cnt = ctypes.c_int64(0)
+        self._lib.pselinv_model_get_params(self._h, None, 0, ctypes.byref(cnt))
+        return cnt.value
+
+    def params(self):
+        n = self.num_params()
+        buf = (ctypes.c_float * n)()
+        cnt = ctypes.c_int64(0)
+        rc = self._lib.pselinv_model_get_params(self._h, buf, n, ctypes.byref(cnt))
+        if rc != 0:
+            raise PselinvError(rc, "pselinv_model_get_params")
+        return np.array(buf[:], dtype=np.float32)
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        rc = self._lib.pselinv_model_set_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                p.size)
+        if rc != 0:
+            raise PselinvError(rc, "pselinv_model_set_params")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.pselinv_model_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def encode_records(records):
+    """Network inputs (n x 16, float32) of tuning records (host computation)."""
+    lib = load_library()
+    arr = CostModel._recs(records)
+    x = np.zeros((len(records), 16), dtype=np.float32)
+    rc = lib.pselinv_model_encode(arr, len(records), x.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    if rc != 0:
+        raise PselinvError(rc, "pselinv_model_encode")
+    return x
+
+
+def make_record(**kw):
+    r = TuneRecord()
+    for k, v in kw.items():
+        if k == "feat":
+            for i, f in enumerate(v):
+                r.feat[i] = f
+        else:
+            setattr(r, k, v)
+    return r
 
 
 NOALLOC_MAX_S = 256

@@ -10,6 +10,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <map>
+#include <tuple>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -61,6 +64,12 @@ struct Step {
   size_t bytes = 0;
   double flops = 0;                       // useful flops of a GEMM step
   int level = -1;
+  int slot = -1;      // tunable step: 0 normalisation, 1 steps 3+5, 2 step 4
+  int side = 0;       // 1: issued on the side stream (normalisation, one level ahead)
+  int wait = -1;      // event index waited on before the launch
+  int signal = -1;    // event index recorded after the launch
+  int param = 0;      // tuned parameter in use (GEMM tile config or K split)
+  float feat[8] = {}; // shape features of the step (cost model input)
 };
 
 struct Plan {
@@ -70,6 +79,8 @@ struct Plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool built = false;
+  bool two_streams = false;
+  std::vector<cudaEvent_t> ev;  // [0] fork, [1] join, [2 + d] level d normalised
 
   template <class T>
   size_t push(const std::vector<T>& v) {
@@ -82,6 +93,9 @@ struct Plan {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (arena) cudaFree(arena);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+    two_streams = false;
     exec = nullptr;
     graph = nullptr;
     arena = nullptr;
@@ -118,7 +132,11 @@ struct pselinv_ctx {
   Plan selinv_plan[2][2];  // [precision][schedule]
   int slices = 6;          // FP16 slices per operand of the split products
   int last_precision = 0;
+  // tuned parameters: key = (precision, level, slot) -> candidate value
+  std::map<std::tuple<int, int, int>, int> tuned;
+  std::vector<pselinv_tune_record> records;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;
   int64_t last_info = -1;
   int last_status = 0;
 };
@@ -187,8 +205,14 @@ inline int64_t cK(const HostSym& H, int64_t K) { return H.rows_ptr[K + 1] - H.ro
 
 int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+template <class D>
+void gemm_features(Step& st, const std::vector<D>& descs, double kscale);
+template <>
+void gemm_features<GemmDesc>(Step& st, const std::vector<GemmDesc>& descs, double);
+
 // GEMM step from a list of descriptors; tasks enumerate every tile and K chunk
-void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& descs, int level) {
+void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& descs, int level,
+                   int slot = -1) {
   if (descs.empty()) return;
   const int bm = gemm_tile_m(dtype, cfg), bn = gemm_tile_n(dtype, cfg);
   std::vector<GemmTask> tasks;
@@ -218,6 +242,9 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
   s.tasks = P.push(tasks);
   s.flops = flops;
   s.level = level;
+  s.slot = slot;
+  s.param = cfg;
+  gemm_features(s, descs, 0);
   P.steps.push_back(s);
 }
 
@@ -257,7 +284,7 @@ inline size_t exps_bytes(int64_t R) { return align256((size_t)R * 4); }
 size_t ozaki_sn_bytes(int64_t s, int64_t c, int S) {
   if (c == 0) return 0;
   return align256((size_t)c * c * 8) + 2 * (slice_bytes(c, c, S) + exps_bytes(c)) +
-         3 * (slice_bytes(s, c, S) + exps_bytes(s)) + (size_t)2 * c * 8 + 256;
+         3 * (slice_bytes(s, c, S) + exps_bytes(s)) + (size_t)(2 * c + 3 * s) * 8 + 256;
 }
 size_t ozaki_level_bytes(const HostSym& H, int64_t nb, int S) {
   size_t mx = 0;
@@ -301,6 +328,47 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
 
 int choose_cfg(int dtype) { return dtype == DT_F64 ? GEMM_64x64 : GEMM_64x64; }
 
+int tuned_value(const pselinv_ctx* h, int prec, int level, int slot, int dflt) {
+  auto it = h->tuned.find(std::make_tuple(prec, level, slot));
+  return it == h->tuned.end() ? dflt : it->second;
+}
+
+// shape features of a GEMM step (log2 scale): problem count, total flops,
+// largest and mean M, N, K
+template <class D>
+void gemm_features(Step& st, const std::vector<D>& descs, double kscale) {
+  double n = 0, fl = 0, mm = 0, mn = 0, mk = 0, sm = 0, sn = 0, sk = 0;
+  for (const auto& d : descs) {
+    const double K = kscale > 0 ? d.K32 * kscale : 0;
+    n += 1;
+    fl += 2.0 * d.M * d.N * K;
+    mm = std::max(mm, (double)d.M);
+    mn = std::max(mn, (double)d.N);
+    mk = std::max(mk, K);
+    sm += d.M;
+    sn += d.N;
+    sk += K;
+  }
+  const double v[8] = {n, fl, mm, mn, mk, n ? sm / n : 0, n ? sn / n : 0, n ? sk / n : 0};
+  for (int i = 0; i < 8; i++) st.feat[i] = (float)std::log2(1.0 + v[i]);
+}
+template <>
+void gemm_features<GemmDesc>(Step& st, const std::vector<GemmDesc>& descs, double) {
+  double n = 0, fl = 0, mm = 0, mn = 0, mk = 0, sm = 0, sn = 0, sk = 0;
+  for (const auto& d : descs) {
+    n += 1;
+    fl += 2.0 * d.M * d.N * d.K;
+    mm = std::max(mm, (double)d.M);
+    mn = std::max(mn, (double)d.N);
+    mk = std::max(mk, (double)d.K);
+    sm += d.M;
+    sn += d.N;
+    sk += d.K;
+  }
+  const double v[8] = {n, fl, mm, mn, mk, n ? sm / n : 0, n ? sn / n : 0, n ? sk / n : 0};
+  for (int i = 0; i < 8; i++) st.feat[i] = (float)std::log2(1.0 + v[i]);
+}
+
 // ---------------------------------------------------------------------------
 // factor plan: scatter A, then per height level (leaves first):
 //   diagonal LU, triangular inverses, L = A_{C,K} U_KK^{-1},
@@ -337,7 +405,7 @@ int build_factor_plan(pselinv_ctx* h) {
         diag.push_back({(int)b, (int)K, 0, 0});
         if (c == 0) continue;
         for (int which = 0; which < 2; which++)
-          for (int64_t j = 0; j < s; j += 8) {
+          for (int64_t j = 0; j < s; j += 32) {
             tri.push_back({(int)b, (int)K, which, (int)j});
             wofs.push_back(w0 + which * s * s);
           }
@@ -421,15 +489,18 @@ void add_zero_step(Plan& P, const std::vector<CopySeg>& segs, int level) {
   P.steps.push_back(z);
 }
 
-void add_slice_step(Plan& P, const std::vector<SliceDesc>& descs, int level) {
+void add_slice_step(Plan& P, const std::vector<SliceDesc>& descs, int level, bool maxima) {
   if (descs.empty()) return;
   std::vector<SliceTask> tasks;
   double bytes = 0;
   for (size_t d = 0; d < descs.size(); d++) {
-    for (int rb = 0; rb < descs[d].R64; rb++) tasks.push_back({(int)d, rb});
-    bytes += 8.0 * descs[d].R * descs[d].Kd + 2.0 * descs[d].S * descs[d].R64 * 64.0 * descs[d].K32 * 32;
+    for (int kc = 0; kc < ceil_div(descs[d].K32, 2); kc++)
+      for (int rb = 0; rb < descs[d].R64; rb++) tasks.push_back({(int)d, rb, kc});
+    bytes += 8.0 * descs[d].R * descs[d].Kd;
+    if (!maxima) bytes += 2.0 * descs[d].S * descs[d].R64 * 64.0 * descs[d].K32 * 32;
   }
   Step st;
+  st.cfg = maxima ? 1 : 0;
   st.kind = ST_SLICE;
   st.n = (int)tasks.size();
   st.descs = P.push(descs);
@@ -451,9 +522,9 @@ int choose_ozaki_ksplit(const std::vector<OzDesc>& descs) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, kmax));
 }
 
-void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool force_atomic) {
+void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool force_atomic,
+                     int ks, int slot) {
   if (descs.empty()) return;
-  const int ks = choose_ozaki_ksplit(descs);
   std::vector<OzTask> tasks;
   double flops = 0;
   for (size_t d = 0; d < descs.size(); d++) {
@@ -473,6 +544,9 @@ void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool
   st.tasks = P.push(tasks);
   st.flops = flops;
   st.level = level;
+  st.slot = slot;
+  st.param = ks;
+  gemm_features(st, descs, 32.0);
   P.steps.push_back(st);
 }
 
@@ -486,7 +560,7 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   const int S = h->slices;
   std::vector<SnTask> gt;
   std::vector<int64_t> gofs, mofs;
-  std::vector<SliceDesc> sl1, sl2;
+  std::vector<SliceDesc> sl1, sl2, mx1;
   std::vector<OzDesc> main, dg;
   std::vector<CopySeg> zero;
   size_t off = (size_t)gbase_scalars * 8;
@@ -499,7 +573,9 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   // row and column maxima of every G of the level, zeroed by one memset
   int64_t nmax = 0;
   for (int64_t b = 0; b < nb; b++)
-    for (int64_t K : grp) nmax += 2 * (H.rows_ptr[K + 1] - H.rows_ptr[K]);
+    for (int64_t K : grp)
+      if (H.rows_ptr[K + 1] > H.rows_ptr[K])
+        nmax += 2 * (H.rows_ptr[K + 1] - H.rows_ptr[K]) + 3 * H.sn_width[K];
   unsigned long long* maxbase = (unsigned long long*)take(align256((size_t)nmax * 8 + 8));
   int64_t moff = 0;
   auto slice_desc = [&](const double* src, int ld, int mode, int R, int Kd) {
@@ -524,7 +600,7 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
       char* G = take((size_t)c * c * 8);
       const int64_t g0 = (G - h->scratch) / 8;
       const int64_t m0 = moff;
-      moff += 2 * c;
+      moff += 2 * c + 3 * s;
       for (int tq = 0; tq < ceil_div(c, 32); tq++)
         for (int tp = 0; tp < ceil_div(c, 32); tp++) {
           gt.push_back({(int)b, (int)K, tp, tq});
@@ -537,13 +613,18 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
       SliceDesc gc = slice_desc((const double*)G, c, SLICE_COLS, c, c);
       gr.maxbits = maxbase + m0;      // row maxima of G from the gather
       gc.maxbits = maxbase + m0 + c;  // column maxima of G
-      const SliceDesc lh = slice_desc((const double*)(h->nf + lo), c, SLICE_COLS, s, c);
-      const SliceDesc uh = slice_desc((const double*)(h->nf + uo), c, SLICE_COLS, s, c);
-      const SliceDesc ak = slice_desc((const double*)(h->ainv + lo), c, SLICE_COLS, s, c);
+      SliceDesc lh = slice_desc((const double*)(h->nf + lo), c, SLICE_COLS, s, c);
+      SliceDesc uh = slice_desc((const double*)(h->nf + uo), c, SLICE_COLS, s, c);
+      SliceDesc ak = slice_desc((const double*)(h->ainv + lo), c, SLICE_COLS, s, c);
+      lh.maxbits = maxbase + m0 + 2 * c;
+      uh.maxbits = maxbase + m0 + 2 * c + s;
+      ak.maxbits = maxbase + m0 + 2 * c + 2 * s;
       sl1.push_back(gr);
       sl1.push_back(gc);
       sl1.push_back(lh);
       sl1.push_back(uh);
+      mx1.push_back(lh);
+      mx1.push_back(uh);
       sl2.push_back(ak);
       OzDesc d{};
       d.alpha = -1.0;
@@ -581,11 +662,16 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   g.ptr2 = maxbase;
   g.level = lev;
   P.steps.push_back(g);
-  add_slice_step(P, sl1, lev);
-  if (choose_ozaki_ksplit(main) > 1) add_zero_step(P, zero, lev);
-  add_ozgemm_step(P, main, S, lev, false);
-  add_slice_step(P, sl2, lev);
-  add_ozgemm_step(P, dg, S, lev, true);
+  const int prec = PSELINV_PREC_OZAKI_FP16;
+  const int ks_main = tuned_value(h, prec, lev, 1, choose_ozaki_ksplit(main));
+  const int ks_diag = tuned_value(h, prec, lev, 2, choose_ozaki_ksplit(dg));
+  add_slice_step(P, mx1, lev, true);
+  add_slice_step(P, sl1, lev, false);
+  if (ks_main > 1) add_zero_step(P, zero, lev);
+  add_ozgemm_step(P, main, S, lev, false, ks_main, 1);
+  add_slice_step(P, sl2, lev, true);
+  add_slice_step(P, sl2, lev, false);
+  add_ozgemm_step(P, dg, S, lev, true, ks_diag, 2);
 }
 
 int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
@@ -605,18 +691,37 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       off += 2 * H.sn_width[K] * H.sn_width[K];
     }
   const int64_t gbase = off;
+  // Normalisation (Algorithm 1 step 2 and D_K) on the side stream: the
+  // triangular inverses of every diagonal block in one launch, then one
+  // product launch per depth level, one level ahead of the sweep, so that its
+  // FP64 work overlaps the previous level's products.
   {
     std::vector<SnTask> tri;
     std::vector<int64_t> wofs;
-    std::vector<GemmDesc> norm;
     for (int64_t b = 0; b < nb; b++)
-      for (int64_t K = 0; K < H.ns; K++) {
-        const int64_t s = H.sn_width[K], c = cK(H, K), w0 = wbase[b * H.ns + K];
+      for (size_t i = 0; i < H.level_sn.size(); i++) {  // roots first
+        const int64_t K = H.level_sn[i];
+        const int64_t s = H.sn_width[K], w0 = wbase[b * H.ns + K];
         for (int which = 0; which < 2; which++)
-          for (int64_t j = 0; j < s; j += 8) {
+          for (int64_t j = 0; j < s; j += 32) {
             tri.push_back({(int)b, (int)K, which, (int)j});
             wofs.push_back(w0 + which * s * s);
           }
+      }
+    Step t;
+    t.kind = ST_TRI_INV;
+    t.n = (int)tri.size();
+    t.tasks = P.push(tri);
+    t.offs = P.push(wofs);
+    t.side = 1;
+    P.steps.push_back(t);
+  }
+  auto add_normalize = [&](int lev) {
+    std::vector<GemmDesc> norm;
+    for (int64_t b = 0; b < nb; b++)
+      for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
+        const int64_t K = H.level_sn[i];
+        const int64_t s = H.sn_width[K], c = cK(H, K), w0 = wbase[b * H.ns + K];
         const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
         char* Linv = h->scratch + (size_t)w0 * es;
         char* Uinv = Linv + (size_t)s * s * es;
@@ -631,15 +736,17 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
                                    0, 1, GEMM_TRI_LOWER_B));
         }
       }
-    Step t;
-    t.kind = ST_TRI_INV;
-    t.n = (int)tri.size();
-    t.tasks = P.push(tri);
-    t.offs = P.push(wofs);
-    P.steps.push_back(t);
-    add_gemm_step(P, dt, cfg, norm, -1);
-  }
+    add_gemm_step(P, dt, tuned_value(h, precision, lev, 0, cfg), norm, lev, 0);
+    P.steps.back().side = 1;
+    P.steps.back().signal = 2 + lev;
+  };
+  const int nlev = (int)H.level_ptr.size() - 1;
+  P.two_streams = true;
+  P.ev.assign(2 + std::max(nlev, 0), nullptr);
+  for (auto& e : P.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (size_t lev = 0; lev + 1 < H.level_ptr.size(); lev++) {
+    add_normalize((int)lev);
+    const size_t first_main = P.steps.size();
     // groups: the whole level, or one supernode at a time
     std::vector<std::vector<int64_t>> groups;
     if (schedule == PSELINV_SCHED_LEVEL) {
@@ -687,9 +794,10 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       g.offs = P.push(gofs);
       g.level = (int)lev;
       P.steps.push_back(g);
-      add_gemm_step(P, dt, cfg, main, (int)lev);
-      add_gemm_step(P, dt, cfg, dg, (int)lev);
+      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, 1, cfg), main, (int)lev, 1);
+      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, 2, cfg), dg, (int)lev, 2);
     }
+    if (P.steps.size() > first_main) P.steps[first_main].wait = 2 + (int)lev;
   }
   CK(cudaMalloc(&P.arena, P.host.size() + 256));
   CK(cudaMemcpy(P.arena, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
@@ -731,7 +839,8 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       launch_scatter_values(h->dtype, h->S, h->staging, h->lu, (int)h->nbatch, st);
       break;
     case ST_SLICE:
-      launch_slice((const SliceDesc*)(a + s.descs), (const SliceTask*)(a + s.tasks), s.n, st);
+      launch_slice((const SliceDesc*)(a + s.descs), (const SliceTask*)(a + s.tasks), s.n,
+                   s.cfg == 1, st);
       break;
     case ST_OZGEMM:
       launch_ozaki_gemm(s.cfg, (const OzDesc*)(a + s.descs), (const OzTask*)(a + s.tasks), s.n,
@@ -743,16 +852,43 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
   }
 }
 
-int run_plan(pselinv_ctx* h, Plan& P, cudaStream_t st, bool graph) {
-  if (!graph) {
+// Issue the plan on `st`; steps marked `side` go to the side stream, forked
+// from and joined back into `st` with events (also inside a graph capture).
+int run_steps(pselinv_ctx* h, Plan& P, cudaStream_t st) {
+  if (!P.two_streams) {
     for (const Step& s : P.steps) launch_step(h, P, s, st);
     CK(cudaGetLastError());
     return PSELINV_OK;
   }
+  if (!h->side_stream) CK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+  cudaStream_t side = h->side_stream;
+  CK(cudaEventRecord(P.ev[0], st));
+  CK(cudaStreamWaitEvent(side, P.ev[0], 0));
+  for (const Step& s : P.steps) {
+    cudaStream_t q = s.side ? side : st;
+    if (s.wait >= 0) CK(cudaStreamWaitEvent(q, P.ev[s.wait], 0));
+    launch_step(h, P, s, q);
+    if (s.signal >= 0) CK(cudaEventRecord(P.ev[s.signal], q));
+  }
+  CK(cudaEventRecord(P.ev[1], side));
+  CK(cudaStreamWaitEvent(st, P.ev[1], 0));
+  CK(cudaGetLastError());
+  return PSELINV_OK;
+}
+
+int run_plan(pselinv_ctx* h, Plan& P, cudaStream_t st, bool graph) {
+  if (!graph) return run_steps(h, P, st);
   if (!P.exec) {
     if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (const Step& s : P.steps) launch_step(h, P, s, h->cap_stream);
+    const int rc = run_steps(h, P, h->cap_stream);
+    if (rc != PSELINV_OK) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(h->cap_stream, &junk);
+      if (junk) cudaGraphDestroy(junk);
+      (void)cudaGetLastError();
+      return rc;
+    }
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess) {
@@ -847,7 +983,7 @@ int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind, con
   pselinv_ctx* h = new (std::nothrow) pselinv_ctx();
   if (!h) return PSELINV_ERR_OOM;
   if (opts) h->opts = *opts; else pselinv_default_opts(&h->opts);
-  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 1024) {
+  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 256) {
     delete h;
     return PSELINV_ERR_ARG;
   }
@@ -1043,6 +1179,169 @@ int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_
   return PSELINV_OK;
 }
 
+}  // extern "C"
+
+// Cost-model tuning: predict the time of every candidate of every tunable
+// launch with the model and keep the argmin (no timing).
+template <class RB>
+static int model_tune(pselinv_ctx* h, Plan& P0, int precision, pselinv_model_t model, RB rebuild) {
+  if (!model) return PSELINV_ERR_ARG;
+  static const int gemm_cands[3] = {GEMM_64x64, GEMM_32x32, GEMM_128x64};
+  static const int ks_cands[5] = {1, 2, 4, 8, 16};
+  std::vector<std::tuple<int, int, int>> keys;
+  std::vector<pselinv_tune_record> q;
+  for (const Step& s : P0.steps) {
+    if (s.slot < 0) continue;
+    const auto key = std::make_tuple(s.level, s.slot, (int)s.kind);
+    if (std::find(keys.begin(), keys.end(), key) != keys.end()) continue;
+    keys.push_back(key);
+    const int nc = s.kind == ST_GEMM ? 3 : 5;
+    for (int v = 0; v < nc; v++) {
+      pselinv_tune_record r{};
+      r.precision = precision;
+      r.level = s.level;
+      r.slot = s.slot;
+      r.kind = s.kind == ST_GEMM ? PSELINV_STEP_GEMM : PSELINV_STEP_OZAKI_GEMM;
+      r.param = s.kind == ST_GEMM ? gemm_cands[v] : ks_cands[v];
+      for (int i = 0; i < 8; i++) r.feat[i] = s.feat[i];
+      q.push_back(r);
+    }
+  }
+  std::vector<double> pred(q.size());
+  int rc = pselinv_model_predict(model, q.data(), (int64_t)q.size(), pred.data(), nullptr);
+  if (rc != PSELINV_OK) return rc;
+  for (const auto& key : keys) {
+    double bp = 1e300;
+    int best = -1;
+    for (size_t i = 0; i < q.size(); i++)
+      if (q[i].level == std::get<0>(key) && q[i].slot == std::get<1>(key) && pred[i] < bp) {
+        bp = pred[i];
+        best = q[i].param;
+      }
+    if (best >= 0) h->tuned[std::make_tuple(precision, std::get<0>(key), std::get<1>(key))] = best;
+  }
+  return rebuild();
+}
+
+template <class RB>
+static int model_tune(pselinv_ctx* h, Plan& P0, int precision, pselinv_model_t model, RB rebuild);
+
+extern "C" {
+
+int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, void* stream) {
+  if (!h || !h->factored || (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16))
+    return PSELINV_ERR_ARG;
+  if (precision == PSELINV_PREC_OZAKI_FP16 && h->dtype != PSELINV_F64) return PSELINV_ERR_UNSUPPORTED;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
+  auto rebuild = [&]() -> int {
+    for (auto& p : h->selinv_plan[precision]) p.release();
+    return build_selinv_plan(h, sched, precision);
+  };
+  // drop this precision's tuned values
+  for (auto it = h->tuned.begin(); it != h->tuned.end();)
+    it = std::get<0>(it->first) == precision ? h->tuned.erase(it) : std::next(it);
+  int rc = rebuild();
+  if (rc != PSELINV_OK || mode == PSELINV_TUNE_RESET) return rc;
+  Plan& P0 = h->selinv_plan[precision][sched];
+  if (mode == PSELINV_TUNE_MODEL) return model_tune(h, P0, precision, model, rebuild);
+  if (mode != PSELINV_TUNE_EXHAUSTIVE) return PSELINV_ERR_ARG;
+
+  static const int gemm_cands[3] = {GEMM_64x64, GEMM_32x32, GEMM_128x64};
+  static const int ks_cands[5] = {1, 2, 4, 8, 16};
+  struct Key {
+    int level, slot, kind;
+  };
+  std::vector<Key> keys;
+  std::map<std::tuple<int, int, int>, std::vector<float>> feats;
+  for (const Step& s : P0.steps)
+    if (s.slot >= 0) {
+      const auto k = std::make_tuple(s.level, s.slot, (int)s.kind);
+      if (!feats.count(k)) {
+        keys.push_back({s.level, s.slot, (int)s.kind});
+        feats[k] = std::vector<float>(s.feat, s.feat + 8);
+      }
+    }
+  std::map<std::tuple<int, int, int, int>, double> best_ms;  // (level, slot, kind, value) -> ms
+  const int ncand = precision == PSELINV_PREC_FP64 ? 3 : 5;
+  std::vector<pselinv_step_stat> stats;
+  for (int v = 0; v < ncand; v++) {
+    for (const Key& k : keys) {
+      const int val = k.kind == ST_GEMM ? gemm_cands[v % 3] : ks_cands[v];
+      h->tuned[std::make_tuple(precision, k.level, k.slot)] = val;
+    }
+    rc = rebuild();
+    if (rc != PSELINV_OK) return rc;
+    h->last_precision = precision;
+    Plan& P = h->selinv_plan[precision][sched];
+    for (int rep = 0; rep < 2; rep++) {
+      stats.assign(P.steps.size(), pselinv_step_stat{});
+      int64_t cnt = 0;
+      rc = pselinv_profile(h, 0, stream, stats.data(), (int64_t)stats.size(), &cnt);
+      if (rc != PSELINV_OK) return rc;
+      std::map<std::tuple<int, int, int, int>, double> acc;
+      for (size_t i = 0; i < P.steps.size(); i++) {
+        const Step& s = P.steps[i];
+        if (s.slot < 0) continue;
+        acc[std::make_tuple(s.level, s.slot, (int)s.kind, s.param)] += stats[i].ms;
+      }
+      for (const auto& kv : acc) {
+        auto it = best_ms.find(kv.first);
+        if (it == best_ms.end() || kv.second < it->second) best_ms[kv.first] = kv.second;
+      }
+    }
+  }
+  // keep the fastest candidate of every tunable launch; record everything
+  h->records.clear();
+  for (const Key& k : keys) {
+    int best = -1;
+    double bms = 1e300;
+    for (const auto& kv : best_ms) {
+      if (std::get<0>(kv.first) != k.level || std::get<1>(kv.first) != k.slot ||
+          std::get<2>(kv.first) != k.kind)
+        continue;
+      if (kv.second < bms) {
+        bms = kv.second;
+        best = std::get<3>(kv.first);
+      }
+    }
+    if (best < 0) continue;
+    h->tuned[std::make_tuple(precision, k.level, k.slot)] = best;
+    for (const auto& kv : best_ms) {
+      if (std::get<0>(kv.first) != k.level || std::get<1>(kv.first) != k.slot ||
+          std::get<2>(kv.first) != k.kind)
+        continue;
+      pselinv_tune_record r{};
+      r.precision = precision;
+      r.level = k.level;
+      r.slot = k.slot;
+      r.kind = k.kind == ST_GEMM ? PSELINV_STEP_GEMM : PSELINV_STEP_OZAKI_GEMM;
+      r.param = std::get<3>(kv.first);
+      r.chosen = r.param == best ? 1 : 0;
+      const auto& f = feats[std::make_tuple(k.level, k.slot, k.kind)];
+      for (int i = 0; i < 8; i++) r.feat[i] = f[i];
+      r.ms = kv.second;
+      h->records.push_back(r);
+    }
+  }
+  rc = rebuild();
+  if (rc != PSELINV_OK) return rc;
+  // leave valid results of the tuned plan
+  rc = run_plan(h, h->selinv_plan[precision][sched], st, false);
+  if (rc != PSELINV_OK) return rc;
+  CK(cudaStreamSynchronize(st));
+  h->inverted = true;
+  return PSELINV_OK;
+}
+
+int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int64_t* count) {
+  if (!h || !count || (cap > 0 && !out)) return PSELINV_ERR_ARG;
+  *count = (int64_t)h->records.size();
+  for (int64_t i = 0; i < *count && i < cap; i++) out[i] = h->records[i];
+  return PSELINV_OK;
+}
+
 int pselinv_sync(pselinv_t h, void* stream) {
   if (!h || h->opts.host_only) return PSELINV_ERR_ARG;
   CK(cudaSetDevice(h->device));
@@ -1057,6 +1356,7 @@ void pselinv_free(pselinv_t h) {
     cudaSetDevice(h->device);
     free_numeric(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->side_stream) cudaStreamDestroy(h->side_stream);
     cudaFree(h->dsym);
     cudaFree(h->derr);
   }

@@ -158,10 +158,11 @@ struct SliceDesc {
   int ld, mode, R, Kd, S, R64, K32;
   __half* out;
   int* exps;
-  const unsigned long long* maxbits;  // precomputed max_k |X(r,k)| bit patterns, or null
+  unsigned long long* maxbits;  // max_k |X(r,k)| as bit patterns (from the gather or a maxima pass)
 };
+// one 64-row block and one chunk of 64 K values (two K blocks) of a slice set
 struct SliceTask {
-  int d, rb;
+  int d, rb, kc;
 };
 struct OzDesc {
   const __half* A;  // slice set of the M x K operand
@@ -176,7 +177,9 @@ struct OzTask {
   int d, tm, tn, ks;
 };
 cudaError_t prepare_ozaki_kernels();
-void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, cudaStream_t st);
+// maxima = true: accumulate row maxima into desc.maxbits; false: write the slices
+void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bool maxima,
+                  cudaStream_t st);
 void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
                        cudaStream_t st);
 void launch_zero(const CopySeg* segs, int nseg, cudaStream_t st);

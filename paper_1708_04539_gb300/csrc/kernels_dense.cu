@@ -138,52 +138,77 @@ diag_lu_kernel(SymDev S, T* store, const SnTask* __restrict__ tasks, int ntasks)
 }
 
 // Triangular inverses of the diagonal block: which = 0 gives (L_KK)^{-1}
-// (unit lower), which = 1 gives (U_KK)^{-1} (upper).  Each warp solves for
-// one column j = first + warp: column-oriented substitution with the
-// working vector in shared memory.
+// (unit lower), which = 1 gives (U_KK)^{-1} (upper).  A task inverts a panel
+// of kTriPanel columns j0.. by substitution on all of them at once: the
+// panel X (s x kTriPanel) lives in shared memory, the triangle is streamed
+// through shared memory kTriChunk columns at a time, and the thread layout
+// (lane = panel column, warp = row group) lets every warp read one factor
+// entry per row and update 32 right-hand sides with it.
+constexpr int kTriPanel = 32;
+constexpr int kTriChunk = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 tri_inv_kernel(SymDev S, const T* store, T* out, const int64_t* __restrict__ wofs,
                const SnTask* __restrict__ tasks, int ntasks) {
   extern __shared__ unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;  // panel column, row group (8)
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const SnTask task = tasks[t];
     const int K = task.K;
     const int s = S.sn_width[K];
-    T* x = reinterpret_cast<T*>(smem_raw) + (int64_t)warp * s;
+    const int j0 = task.b;
+    const int np = min(kTriPanel, s - j0);
+    // X: s rows x (kTriPanel + 1) (padded), F: kTriChunk factor columns of s rows
+    T* X = reinterpret_cast<T*>(smem_raw);
+    T* F = X + (int64_t)s * (kTriPanel + 1);
     const T* D = store + (int64_t)task.inst * S.storage + S.sn_off[K];
     T* W = out + wofs[t];
-    const int j = task.b + warp;
-    if (j < s) {
-      for (int i = lane; i < s; i += 32) x[i] = (i == j) ? sc_one(T()) : sc_zero(T());
-      __syncwarp();
-      if (task.a == 0) {
-        // L x = e_j, L unit lower
-        for (int k = j; k < s - 1; k++) {
-          const T xk = x[k];
-          __syncwarp();
-          if (!is_zero(xk))
-            for (int i = k + 1 + lane; i < s; i += 32)
-              x[i] = sub_s(x[i], mul_s(D[i + (int64_t)k * s], xk));
-          __syncwarp();
+    for (int i = rg; i < s; i += 8) X[i * (kTriPanel + 1) + c] = (i == j0 + c) ? sc_one(T()) : sc_zero(T());
+    __syncthreads();
+    if (task.a == 0) {
+      // L X = E: forward substitution, rows j0.. only
+      for (int k0 = j0; k0 < s - 1; k0 += kTriChunk) {
+        const int kn = min(kTriChunk, s - 1 - k0);
+        for (int e = threadIdx.x; e < kn * s; e += blockDim.x) {
+          const int kk = e / s, i = e % s;
+          F[kk * s + i] = D[i + (int64_t)(k0 + kk) * s];
         }
-      } else {
-        // U x = e_j, U upper
-        for (int k = j; k >= 0; k--) {
-          const T ukk = D[k + (int64_t)k * s];
-          if (is_zero(ukk)) {
-            if (lane == 0) set_error(S.err, DEV_ZERO_PIVOT, S.sn_first[K] + k);
-          }
-          const T xk = div_s(x[k], ukk);
-          __syncwarp();
-          if (lane == 0) x[k] = xk;
-          for (int i = lane; i < k; i += 32) x[i] = sub_s(x[i], mul_s(D[i + (int64_t)k * s], xk));
-          __syncwarp();
+        __syncthreads();
+        for (int kk = 0; kk < kn; kk++) {
+          const int k = k0 + kk;
+          const T xk = X[k * (kTriPanel + 1) + c];
+          for (int i = k + 1 + rg; i < s; i += 8)
+            X[i * (kTriPanel + 1) + c] = sub_s(X[i * (kTriPanel + 1) + c], mul_s(F[kk * s + i], xk));
+          __syncthreads();
         }
       }
-      for (int i = lane; i < s; i += 32) W[i + (int64_t)j * s] = x[i];
+    } else {
+      // U X = E: backward substitution from row j0 + np - 1 down
+      const int kend = j0 + np - 1;
+      for (int k0 = kend; k0 >= 0; k0 -= kTriChunk) {
+        const int kn = min(kTriChunk, k0 + 1);
+        for (int e = threadIdx.x; e < kn * (k0 + 1); e += blockDim.x) {
+          const int kk = e / (k0 + 1), i = e % (k0 + 1);
+          F[kk * s + i] = D[i + (int64_t)(k0 - kk) * s];
+        }
+        __syncthreads();
+        for (int kk = 0; kk < kn; kk++) {
+          const int k = k0 - kk;
+          const T ukk = F[kk * s + k];
+          if (is_zero(ukk) && threadIdx.x == 0) set_error(S.err, DEV_ZERO_PIVOT, S.sn_first[K] + k);
+          const T xk = div_s(X[k * (kTriPanel + 1) + c], ukk);
+          __syncthreads();
+          if (rg == 0) X[k * (kTriPanel + 1) + c] = xk;
+          for (int i = rg; i < k; i += 8)
+            X[i * (kTriPanel + 1) + c] = sub_s(X[i * (kTriPanel + 1) + c], mul_s(F[kk * s + i], xk));
+          __syncthreads();
+        }
+      }
     }
+    // write the panel column-major: lanes run over rows
+    for (int q = rg; q < np; q += 8)
+      for (int i = c; i < s; i += 32) W[i + (int64_t)(j0 + q) * s] = X[i * (kTriPanel + 1) + q];
     __syncthreads();
   }
 }
@@ -236,7 +261,7 @@ void launch_diag_lu(int dtype, const SymDev& S, void* store, const SnTask* tasks
 }
 
 int tri_inv_smem_bytes(int dtype, int max_width) {
-  return (kThreads / 32) * max_width * (dtype == DT_F64 ? 8 : 16);
+  return max_width * (kTriPanel + 1 + kTriChunk) * (dtype == DT_F64 ? 8 : 16);
 }
 
 cudaError_t prepare_dense_kernels(int dtype, int max_width) {

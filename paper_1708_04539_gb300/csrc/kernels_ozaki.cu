@@ -75,67 +75,73 @@ __device__ __forceinline__ long long fixed_point(double x, int sh0) {
   return b < 0 ? -q : q;
 }
 
-// One task = one 64-row block of a slice set, all K.  The block is staged
-// 64 x 32 at a time through shared memory (coalesced reads in either
-// orientation of the source), and thread t writes bytes [16t, 16t+16) of the
-// 4 KB tile of every slice (coalesced writes).
+// Work item of the slicing kernels: thread t of a task covers row
+// rl = (ci / 4) * 8 + rr and the 8 values of K group kg = ci % 4 of one
+// 32-wide K block (ci = t / 8, rr = t % 8), i.e. bytes [16t, 16t+16) of the
+// block's 4 KB tile in every slice.  One task = one 64-row block and
+// kSliceSpan consecutive K blocks; the values are loaded straight into
+// registers (each lane reads its 8 values; lanes of a warp cover 8 rows x 4
+// groups).
+constexpr int kSliceSpan = 2;
+
+__device__ __forceinline__ void load8(const SliceDesc& d, int r, int k0, double (&x)[8]) {
+  const double* __restrict__ src = d.src;
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int k = k0 + j;
+    x[j] = (r < d.R && k < d.Kd)
+               ? (d.mode == SLICE_ROWS ? src[r + (int64_t)k * d.ld] : src[k + (int64_t)r * d.ld])
+               : 0.0;
+  }
+}
+
+// Row maxima of |X| (bit patterns), accumulated with atomicMax into
+// d.maxbits (zeroed beforehand).
 __global__ void __launch_bounds__(kSliceThreads)
-slice_kernel(const SliceDesc* __restrict__ descs, const SliceTask* __restrict__ tasks, int ntasks) {
-  __shared__ double blk[64][33];
-  __shared__ unsigned long long mx[64];
-  __shared__ int rexp[64];
+slice_max_kernel(const SliceDesc* __restrict__ descs, const SliceTask* __restrict__ tasks, int ntasks) {
   const int tid = threadIdx.x;
+  const int ci = tid >> 3, rr = tid & 7;
+  const int rl = (ci >> 2) * 8 + rr, kg = ci & 3;
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const SliceTask task = tasks[t];
     const SliceDesc d = descs[task.d];
-    const double* __restrict__ src = d.src;
-    const int r0 = task.rb * 64;
-    auto load_block = [&](int kb) {
-      if (d.mode == SLICE_ROWS) {
-        const int rl = tid & 63;
-        for (int kk = tid >> 6; kk < 32; kk += kSliceThreads / 64) {
-          const int r = r0 + rl, k = kb * 32 + kk;
-          blk[rl][kk] = (r < d.R && k < d.Kd) ? src[r + (int64_t)k * d.ld] : 0.0;
-        }
-      } else {
-        const int kk = tid & 31;
-        for (int rl = tid >> 5; rl < 64; rl += kSliceThreads / 32) {
-          const int r = r0 + rl, k = kb * 32 + kk;
-          blk[rl][kk] = (r < d.R && k < d.Kd) ? src[k + (int64_t)r * d.ld] : 0.0;
-        }
-      }
-    };
-    if (tid < 64) mx[tid] = (d.maxbits && r0 + tid < d.R) ? d.maxbits[r0 + tid] : 0ull;
-    __syncthreads();
-    if (!d.maxbits) {
-      for (int kb = 0; kb < d.K32; kb++) {
-        load_block(kb);
-        __syncthreads();
-        const int rl = tid & 63, part = tid >> 6;
-        unsigned long long m = 0;
+    const int r = task.rb * 64 + rl;
+    unsigned long long m = 0;
+    const int kb1 = min(d.K32, (task.kc + 1) * kSliceSpan);
+    for (int kb = task.kc * kSliceSpan; kb < kb1; kb++) {
+      double x[8];
+      load8(d, r, kb * 32 + kg * 8, x);
 #pragma unroll
-        for (int q = 0; q < 8; q++) m = max(m, abs_bits(blk[rl][part * 8 + q]));
-        atomicMax(&mx[rl], m);
-        __syncthreads();
-      }
+      for (int j = 0; j < 8; j++) m = max(m, abs_bits(x[j]));
     }
-    if (tid < 64) {
-      const int e = exp_of_max(mx[tid]);
-      rexp[tid] = e;
-      if (r0 + tid < d.R) d.exps[r0 + tid] = e;
-    }
-    __syncthreads();
-    // thread -> (core matrix ci = tid / 8, row rr = tid % 8); ci = mg * 4 + kg
-    const int ci = tid >> 3, rr = tid & 7;
-    const int rl = (ci >> 2) * 8 + rr, kg = ci & 3;
-    const int sh0 = 7 * d.S - rexp[rl];
+    // the 4 lanes sharing a row are tid ^ 8, ^ 16 (same rr, kg = 0..3 inside a warp)
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 8));
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
+    if (kg == 0 && r < d.R && m) atomicMax(d.maxbits + r, m);
+  }
+}
+
+// Slices (see the work item above); exponents come from d.maxbits.
+__global__ void __launch_bounds__(kSliceThreads)
+slice_kernel(const SliceDesc* __restrict__ descs, const SliceTask* __restrict__ tasks, int ntasks) {
+  const int tid = threadIdx.x;
+  const int ci = tid >> 3, rr = tid & 7;
+  const int rl = (ci >> 2) * 8 + rr, kg = ci & 3;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SliceTask task = tasks[t];
+    const SliceDesc d = descs[task.d];
+    const int r = task.rb * 64 + rl;
+    const int e = r < d.R ? exp_of_max(d.maxbits[r]) : 0;
+    if (task.kc == 0 && kg == 0 && r < d.R) d.exps[r] = e;
+    const int sh0 = 7 * d.S - e;
     const int64_t slice_stride = (int64_t)d.R64 * d.K32 * (kTileBytes / 2);  // halves
-    for (int kb = 0; kb < d.K32; kb++) {
-      load_block(kb);
-      __syncthreads();
+    const int kb1 = min(d.K32, (task.kc + 1) * kSliceSpan);
+    for (int kb = task.kc * kSliceSpan; kb < kb1; kb++) {
+      double x[8];
+      load8(d, r, kb * 32 + kg * 8, x);
       long long q[8];
 #pragma unroll
-      for (int j = 0; j < 8; j++) q[j] = fixed_point(blk[rl][kg * 8 + j], sh0);
+      for (int j = 0; j < 8; j++) q[j] = fixed_point(x[j], sh0);
       __half* dst = d.out + ((int64_t)task.rb * d.K32 + kb) * (kTileBytes / 2) + tid * 8;
       // balanced base-128 digits from the least significant slice upwards
       for (int s = d.S - 1; s >= 0; s--) {
@@ -151,7 +157,6 @@ slice_kernel(const SliceDesc* __restrict__ descs, const SliceTask* __restrict__ 
         }
         *reinterpret_cast<uint4*>(dst + s * slice_stride) = *reinterpret_cast<uint4*>(h);
       }
-      __syncthreads();
     }
   }
 }
@@ -222,6 +227,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// v * 2^e as the nearest double (ties to even), built from the integer bits
+// without FP64 arithmetic; results below the normal range flush to zero.
+__device__ __forceinline__ double scaled_int_to_double(long long v, int e, bool negate) {
+  if (v == 0) return 0.0;
+  unsigned long long sign = (v < 0) != negate ? (1ull << 63) : 0ull;
+  unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll(u);
+  u <<= lz;  // leading one at bit 63
+  unsigned long long m = u >> 11;
+  const unsigned long long r = u & 0x7FFull;
+  if (r > 0x400ull || (r == 0x400ull && (m & 1ull))) m++;
+  int E = e + 63 - lz + 1023;
+  if (m == (1ull << 53)) {
+    m >>= 1;
+    E++;
+  }
+  if (E <= 0) return 0.0;
+  if (E >= 2047) return __longlong_as_double((long long)(sign | (0x7FFull << 52)));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
 // ---------------------------------------------------------------------------
@@ -372,13 +398,15 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
     // epilogue: thread row r of the tile
     const int r = m0 + warp * 32 + lane;
     if (r < d.M && nkb > 0) {
+      // alpha is +-1: its sign is folded into the assembled doubles
       const int ea = d.eA[r] - 14 - 7 * (S - 1);
+      const bool neg = d.alpha < 0.0;
       double* C = d.C;
 #pragma unroll 4
       for (int j = 0; j < 64; j++) {
         const int n = n0 + j;
         if (n < d.N) {
-          const double v = d.alpha * ldexp((double)tot[j * kGemmThreads + tid], ea + eB_s[j]);
+          const double v = scaled_int_to_double(tot[j * kGemmThreads + tid], ea + eB_s[j], neg);
           double* c = C + r + (int64_t)n * d.ldc;
           if (d.atomic) atomicAdd(c, v); else *c = v;
         }
@@ -422,16 +450,21 @@ cudaError_t prepare_ozaki_kernels() {
                               gemm_smem<6>());
 }
 
-void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, cudaStream_t st) {
+void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bool maxima,
+                  cudaStream_t st) {
   if (ntasks <= 0) return;
-  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
-  slice_kernel<<<grid, kSliceThreads, 0, st>>>(descs, tasks, ntasks);
+  const int grid = ntasks < 152 * 16 ? ntasks : 152 * 16;
+  if (maxima)
+    slice_max_kernel<<<grid, kSliceThreads, 0, st>>>(descs, tasks, ntasks);
+  else
+    slice_kernel<<<grid, kSliceThreads, 0, st>>>(descs, tasks, ntasks);
 }
 
 void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
                        cudaStream_t st) {
   if (ntasks <= 0) return;
-  const int grid = ntasks < 152 * 4 ? ntasks : 152 * 4;
+  // one CTA fits an SM (shared memory and tensor memory): persistent grid
+  const int grid = ntasks < 152 ? ntasks : 152;
   switch (S) {
     case 4: ozaki_gemm_kernel<4><<<grid, kGemmThreads, gemm_smem<4>(), st>>>(descs, tasks, ntasks, err); break;
     case 5: ozaki_gemm_kernel<5><<<grid, kGemmThreads, gemm_smem<5>(), st>>>(descs, tasks, ntasks, err); break;

@@ -1,0 +1,126 @@
+"""Autotuner and learned cost model on the GPU: the model's device gradients
+against the CPU reference, training, tuned plans keep their results, and
+the gain of model-driven tuning over the built-in heuristic (with its regret
+against the exhaustive tuner) on a held-out matrix."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import gen
+from oracle import mlp
+from test_gpu_parity import compare_full
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_04539_gb300 import build
+    build.build()
+    return _t
+
+
+def synthetic_records(n, seed):
+    from paper_1708_04539_gb300.binding import make_record
+    rng = np.random.default_rng(seed)
+    recs = []
+    for _ in range(n):
+        kind = int(rng.integers(0, 2)) * 9
+        param = int(rng.integers(0, 3)) if kind == 0 else int(2 ** rng.integers(0, 5))
+        feat = list(rng.uniform(0, 30, 8))
+        ms = float(np.exp(0.15 * feat[1] - 0.05 * feat[4] + 0.3 * (param % 3) - 2.0))
+        recs.append(make_record(kind=kind, param=param, slot=int(rng.integers(0, 3)),
+                                precision=int(rng.integers(0, 2)), feat=feat, ms=ms))
+    return recs
+
+
+def test_model_gradients_match_cpu_reference(torch):
+    import paper_1708_04539_gb300 as ps
+    m = ps.CostModel(hidden=32, seed=3)
+    recs = synthetic_records(300, 1)
+    g, loss = m.gradients(recs)
+    p = m.params()
+    X = mlp.encode(recs)
+    y = np.log([r.ms for r in recs])
+    loss_ref, g_ref = mlp.loss_and_grad(p.astype(np.float64), 32, X, y)
+    assert abs(loss - loss_ref) <= 1e-4 * max(1.0, loss_ref)
+    assert np.max(np.abs(g - g_ref)) <= 1e-4 * max(1.0, np.max(np.abs(g_ref)))
+    m.close()
+
+
+def test_model_training_converges(torch):
+    import paper_1708_04539_gb300 as ps
+    m = ps.CostModel(hidden=32, seed=4)
+    recs = synthetic_records(400, 2)
+    _, loss0 = m.gradients(recs)
+    loss = m.train(recs, epochs=3000, lr=3e-3)
+    assert loss < 0.05 * loss0
+    test = synthetic_records(100, 3)
+    pred = np.log(m.predict(test))
+    truth = np.log([r.ms for r in test])
+    assert np.corrcoef(pred, truth)[0, 1] > 0.95
+    m.close()
+
+
+def test_exhaustive_tuning_keeps_results(torch):
+    import paper_1708_04539_gb300 as ps
+    p = gen.upwind_3d(14, 71, max_sn=128)
+    h = ps.SelInv.from_problem(p)
+    h.factor(torch.from_numpy(p.values).cuda())
+    st = h.structure()
+    for prec, tol in ((ps.PREC_FP64, 1e-10), (ps.PREC_OZAKI_FP16, 1e-9)):
+        h.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE)
+        recs = h.tune_records()
+        keys = {(r.level, r.slot) for r in recs}
+        assert len(recs) > len(keys) >= 1
+        assert sum(r.chosen for r in recs) == len(keys)
+        h.selinv(precision=prec)
+        compare_full(p, st, h.get_selected(layout=ps.LAYOUT_SUPERNODAL), 0, 20, tol=tol)
+    h.close()
+
+
+def plan_ms(h, prec, reps=3):
+    best = 1e30
+    for _ in range(reps):
+        h.selinv(precision=prec)
+        best = min(best, sum(r["ms"] for r in h.profile(0)))
+    return best
+
+
+@pytest.mark.slow
+def test_model_tuning_gains_over_heuristic(torch):
+    """Train on the tuner's records of smaller matrices, then tune a held-out
+    one with the model alone."""
+    import paper_1708_04539_gb300 as ps
+    recs = []
+    for size in (20, 24, 28):
+        q = gen.upwind_3d(size, 80 + size, max_sn=256)
+        h = ps.SelInv.from_problem(q)
+        h.factor(torch.from_numpy(q.values).cuda())
+        for prec in (ps.PREC_FP64, ps.PREC_OZAKI_FP16):
+            h.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE)
+            recs += h.tune_records()
+        h.close()
+    m = ps.CostModel(hidden=32, seed=5)
+    m.train(recs, epochs=4000, lr=3e-3)
+    p = gen.upwind_3d(34, 99, max_sn=256)
+    h = ps.SelInv.from_problem(p)
+    h.factor(torch.from_numpy(p.values).cuda())
+    out = {}
+    for prec in (ps.PREC_FP64, ps.PREC_OZAKI_FP16):
+        h.tune(precision=prec, mode=ps.TUNE_RESET)
+        heur = plan_ms(h, prec)
+        h.tune(precision=prec, mode=ps.TUNE_MODEL, model=m)
+        model = plan_ms(h, prec)
+        h.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE)
+        exh = plan_ms(h, prec)
+        out[prec] = (heur, model, exh)
+        print(f"precision {prec}: heuristic {heur:.3f} ms, model {model:.3f} ms, "
+              f"exhaustive {exh:.3f} ms, regret {(model - exh) / exh:.3f}")
+        assert model <= heur * 1.03
+    h.close()
+    m.close()
