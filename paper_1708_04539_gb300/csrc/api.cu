@@ -281,18 +281,19 @@ inline size_t exps_bytes(int64_t R) { return align256((size_t)R * 4); }
 
 // bytes one supernode needs during a split-precision level: G, five slice
 // sets (G by rows, G by columns, Lhat, Uhat^T, Ainv(C,K)) and their exponents
-size_t ozaki_sn_bytes(int64_t s, int64_t c, int S) {
+size_t ozaki_sn_bytes(int64_t s, int64_t c, int S, size_t es) {
   if (c == 0) return 0;
-  return align256((size_t)c * c * 8) + 2 * (slice_bytes(c, c, S) + exps_bytes(c)) +
-         3 * (slice_bytes(s, c, S) + exps_bytes(s)) + (size_t)(2 * c + 3 * s) * 8 + 256;
+  const size_t parts = es / 8;  // complex: real and imaginary slice halves
+  return align256((size_t)c * c * es) + 2 * (parts * slice_bytes(c, c, S) + exps_bytes(c)) +
+         3 * (parts * slice_bytes(s, c, S) + exps_bytes(s)) + (size_t)(2 * c + 3 * s) * 8 + 2048;
 }
-size_t ozaki_level_bytes(const HostSym& H, int64_t nb, int S) {
+size_t ozaki_level_bytes(const HostSym& H, int64_t nb, int S, size_t es) {
   size_t mx = 0;
   for (size_t d = 0; d + 1 < H.level_ptr.size(); d++) {
     size_t b = 0;
     for (int64_t i = H.level_ptr[d]; i < H.level_ptr[d + 1]; i++) {
       const int64_t K = H.level_sn[i];
-      b += ozaki_sn_bytes(H.sn_width[K], H.rows_ptr[K + 1] - H.rows_ptr[K], S);
+      b += ozaki_sn_bytes(H.sn_width[K], H.rows_ptr[K + 1] - H.rows_ptr[K], S, es);
     }
     mx = std::max(mx, b * (size_t)nb);
   }
@@ -322,7 +323,7 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
   }
   const int64_t sel = w + gmax;
   size_t bytes = (size_t)(std::max(sel, fmax) * nb) * es + 256;
-  if (es == 8) bytes = std::max(bytes, (size_t)(w * nb) * es + ozaki_level_bytes(H, nb, 6) + 4096);
+  bytes = std::max(bytes, (size_t)(w * nb) * es + ozaki_level_bytes(H, nb, 6, es) + 4096);
   return bytes;
 }
 
@@ -558,19 +559,21 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
                      int64_t gbase_scalars, int lev) {
   const HostSym& H = h->H;
   const int S = h->slices;
+  const size_t es = h->esize;
+  const int cplx = h->dtype == PSELINV_C128 ? 1 : 0;
   std::vector<SnTask> gt;
   std::vector<int64_t> gofs, mofs;
   std::vector<SliceDesc> sl1, sl2, mx1;
   std::vector<OzDesc> main, dg;
   std::vector<CopySeg> zero;
-  size_t off = (size_t)gbase_scalars * 8;
+  size_t off = (size_t)gbase_scalars * es;
   auto take = [&](size_t bytes) {
     off = align256(off);
     const size_t o = off;
     off += bytes;
     return h->scratch + o;
   };
-  // row and column maxima of every G of the level, zeroed by one memset
+  // row and column maxima of every G and panel of the level, zeroed by one memset
   int64_t nmax = 0;
   for (int64_t b = 0; b < nb; b++)
     for (int64_t K : grp)
@@ -587,18 +590,42 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
     d.Kd = Kd;
     d.S = S;
     d.R64 = (int)r64(R);
-    d.K32 = (int)k32(Kd);
-    d.out = (__half*)take(slice_bytes(R, Kd, S));
+    d.K32 = (int)k32(Kd) * (cplx ? 2 : 1);
+    d.cplx = cplx;
+    d.out = (__half*)take(slice_bytes(R, Kd, S) * (cplx ? 2 : 1));
     d.exps = (int*)take(exps_bytes(R));
     d.maxbits = nullptr;
     return d;
+  };
+  // one product (real) or two (real and imaginary parts) for C = -A B
+  auto push_product = [&](std::vector<OzDesc>& out, const SliceDesc& a, const SliceDesc& b,
+                          char* C, int ldc, int M, int N) {
+    OzDesc d{};
+    d.alpha = -1.0;
+    d.A = a.out; d.eA = a.exps; d.A_R64 = a.R64;
+    d.B = b.out; d.eB = b.exps; d.B_R64 = b.R64;
+    d.C = (double*)C; d.ldc = ldc; d.M = M; d.N = N;
+    d.K32 = a.K32;
+    d.cscale = cplx ? 2 : 1;
+    if (!cplx) {
+      out.push_back(d);
+      return;
+    }
+    d.half = a.K32 / 2;
+    d.neg_half = 1;  // Re C = Re A Re B - Im A Im B
+    d.coff = 0;
+    out.push_back(d);
+    d.neg_half = 0;  // Im C = Re A Im B + Im A Re B
+    d.swap_b = 1;
+    d.coff = 1;
+    out.push_back(d);
   };
   for (int64_t b = 0; b < nb; b++)
     for (int64_t K : grp) {
       const int s = (int)H.sn_width[K], c = (int)(H.rows_ptr[K + 1] - H.rows_ptr[K]);
       if (c == 0) continue;
-      char* G = take((size_t)c * c * 8);
-      const int64_t g0 = (G - h->scratch) / 8;
+      char* G = take((size_t)c * c * es);
+      const int64_t g0 = (G - h->scratch) / (int64_t)es;
       const int64_t m0 = moff;
       moff += 2 * c + 3 * s;
       for (int tq = 0; tq < ceil_div(c, 32); tq++)
@@ -607,11 +634,11 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
           gofs.push_back(g0);
           mofs.push_back(m0);
         }
-      const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * 8;
-      const size_t lo = so + (size_t)s * s * 8, uo = lo + (size_t)c * s * 8;
+      const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
+      const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
       SliceDesc gr = slice_desc((const double*)G, c, SLICE_ROWS, c, c);
       SliceDesc gc = slice_desc((const double*)G, c, SLICE_COLS, c, c);
-      gr.maxbits = maxbase + m0;      // row maxima of G from the gather
+      gr.maxbits = maxbase + m0;      // row maxima of G (from the gather for real data)
       gc.maxbits = maxbase + m0 + c;  // column maxima of G
       SliceDesc lh = slice_desc((const double*)(h->nf + lo), c, SLICE_COLS, s, c);
       SliceDesc uh = slice_desc((const double*)(h->nf + uo), c, SLICE_COLS, s, c);
@@ -623,28 +650,19 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
       sl1.push_back(gc);
       sl1.push_back(lh);
       sl1.push_back(uh);
+      if (cplx) {
+        mx1.push_back(gr);
+        mx1.push_back(gc);
+      }
       mx1.push_back(lh);
       mx1.push_back(uh);
       sl2.push_back(ak);
-      OzDesc d{};
-      d.alpha = -1.0;
-      d.K32 = (int)k32(c);
-      // step 3: Ainv(C,K) = -G Lhat
-      d.A = gr.out; d.eA = gr.exps; d.A_R64 = gr.R64;
-      d.B = lh.out; d.eB = lh.exps; d.B_R64 = lh.R64;
-      d.C = (double*)(h->ainv + lo); d.ldc = c; d.M = c; d.N = s;
-      main.push_back(d);
-      // step 5: Ainv(K,C)^T = -G^T Uhat^T
-      d.A = gc.out; d.eA = gc.exps; d.A_R64 = gc.R64;
-      d.B = uh.out; d.eB = uh.exps; d.B_R64 = uh.R64;
-      d.C = (double*)(h->ainv + uo);
-      main.push_back(d);
+      // step 3: Ainv(C,K) = -G Lhat;  step 5: Ainv(K,C)^T = -G^T Uhat^T
+      push_product(main, gr, lh, h->ainv + lo, c, c, s);
+      push_product(main, gc, uh, h->ainv + uo, c, c, s);
       // step 4: Ainv(K,K) = D_K - Uhat Ainv(C,K)
-      d.A = uh.out; d.eA = uh.exps; d.A_R64 = uh.R64;
-      d.B = ak.out; d.eB = ak.exps; d.B_R64 = ak.R64;
-      d.C = (double*)(h->ainv + so); d.ldc = s; d.M = s; d.N = s;
-      dg.push_back(d);
-      zero.push_back({nullptr, h->ainv + lo, (int64_t)2 * c * s});
+      push_product(dg, uh, ak, h->ainv + so, s, s, s);
+      zero.push_back({nullptr, h->ainv + lo, (int64_t)2 * c * s * (cplx ? 2 : 1)});
     }
   if (gt.empty()) return;
   Step ms;
@@ -658,8 +676,10 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   g.n = (int)gt.size();
   g.tasks = P.push(gt);
   g.offs = P.push(gofs);
-  g.offs2 = P.push(mofs);
-  g.ptr2 = maxbase;
+  if (!cplx) {
+    g.offs2 = P.push(mofs);
+    g.ptr2 = maxbase;
+  }
   g.level = lev;
   P.steps.push_back(g);
   const int prec = PSELINV_PREC_OZAKI_FP16;
@@ -1052,7 +1072,6 @@ int pselinv_selinv(pselinv_t h, int precision, void* stream) {
   if (!h || !h->factored) return PSELINV_ERR_ARG;
   if (precision < 0) precision = h->opts.precision;
   if (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16) return PSELINV_ERR_ARG;
-  if (precision == PSELINV_PREC_OZAKI_FP16 && h->dtype != PSELINV_F64) return PSELINV_ERR_UNSUPPORTED;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
@@ -1231,7 +1250,6 @@ extern "C" {
 int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, void* stream) {
   if (!h || !h->factored || (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16))
     return PSELINV_ERR_ARG;
-  if (precision == PSELINV_PREC_OZAKI_FP16 && h->dtype != PSELINV_F64) return PSELINV_ERR_UNSUPPORTED;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;

@@ -153,9 +153,13 @@ enum SliceMode { SLICE_ROWS = 0, SLICE_COLS = 1 };
 // (the contracted dimension).  SLICE_ROWS: X(r, k) = src[r + k*ld] (rows of
 // the stored column-major matrix); SLICE_COLS: X(r, k) = src[k + r*ld] (its
 // columns).  Output: S slices of R64 x K32 tiles of 4 KB, exponents[R].
+// Complex sources (cplx = 1): src holds interleaved (re, im) pairs and the
+// slice set covers K32 = 2 * ceil(Kd / 32) blocks: the real parts in the
+// first half and the imaginary parts in the second, one exponent per row
+// for both.
 struct SliceDesc {
   const double* src;
-  int ld, mode, R, Kd, S, R64, K32;
+  int ld, mode, R, Kd, S, R64, K32, cplx;
   __half* out;
   int* exps;
   unsigned long long* maxbits;  // max_k |X(r,k)| as bit patterns (from the gather or a maxima pass)
@@ -164,6 +168,11 @@ struct SliceDesc {
 struct SliceTask {
   int d, rb, kc;
 };
+// Complex products use the real embedding: with A = [Re | Im] and
+// B = [Re ; Im] slice sets (half = K blocks of one part),
+//   Re C: B as stored, MMAs of the second half negated (neg_half = 1),
+//   Im C: B halves swapped (swap_b = 1), no negation;
+// the result goes to C[(r + n ldc) * cscale + coff] (cscale 2, coff 0 / 1).
 struct OzDesc {
   const __half* A;  // slice set of the M x K operand
   const int* eA;
@@ -171,6 +180,7 @@ struct OzDesc {
   const int* eB;
   double* C;
   int A_R64, B_R64, K32, M, N, ldc, ksplit, atomic;
+  int half, swap_b, neg_half, cscale, coff;
   double alpha;
 };
 struct OzTask {

@@ -84,14 +84,28 @@ __device__ __forceinline__ long long fixed_point(double x, int sh0) {
 // groups).
 constexpr int kSliceSpan = 2;
 
+// 8 consecutive values X(r, k0 .. k0+7) of the slice set's K range (for a
+// complex source: real parts in the first half of the range, imaginary
+// parts in the second)
 __device__ __forceinline__ void load8(const SliceDesc& d, int r, int k0, double (&x)[8]) {
   const double* __restrict__ src = d.src;
+  int part = 0;
+  if (d.cplx) {
+    const int half = (d.K32 / 2) * 32;
+    if (k0 >= half) {
+      part = 1;
+      k0 -= half;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < 8; j++) {
     const int k = k0 + j;
-    x[j] = (r < d.R && k < d.Kd)
-               ? (d.mode == SLICE_ROWS ? src[r + (int64_t)k * d.ld] : src[k + (int64_t)r * d.ld])
-               : 0.0;
+    double v = 0.0;
+    if (r < d.R && k < d.Kd) {
+      const int64_t idx = d.mode == SLICE_ROWS ? r + (int64_t)k * d.ld : k + (int64_t)r * d.ld;
+      v = d.cplx ? src[2 * idx + part] : src[idx];
+    }
+    x[j] = v;
   }
 }
 
@@ -175,12 +189,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 }
 // kind::f16, FP16 x FP16 -> FP32, both operands K-major, M = 128, N = 64
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t kIdescNegA = kIdesc | (1u << 13);  // D += (-A) B
 
-__device__ __forceinline__ void mma_f16(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc,
+                                        uint32_t idesc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -321,7 +337,8 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
           const unsigned char* a1 = A + s * a_sl + ((int64_t)(2 * task.tm + 1) * d.K32 + kb) * kTileBytes;
           bulk_load(smem_u32(st + s * 2 * kTileBytes + kTileBytes), a1, kTileBytes, fb);
         }
-        const unsigned char* b0 = B + s * b_sl + ((int64_t)task.tn * d.K32 + kb) * kTileBytes;
+        const int kbb = d.swap_b ? (kb < d.half ? kb + d.half : kb - d.half) : kb;
+        const unsigned char* b0 = B + s * b_sl + ((int64_t)task.tn * d.K32 + kbb) * kTileBytes;
         bulk_load(smem_u32(st + kAB + s * kTileBytes), b0, kTileBytes, fb);
       }
     };
@@ -345,14 +362,15 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
         if (ok) {
           const uint32_t st = smem_u32(smem + buf * kStage);
           const bool first = (i % 4) == 0;
+          const uint32_t idesc = (d.neg_half && kb0 + i >= d.half) ? kIdescNegA : kIdesc;
 #pragma unroll 1
           for (int s = 0; s < S; s++)
 #pragma unroll 1
             for (int tt = 0; tt < S - s; tt++) {
               const uint32_t dt = tmem + (uint32_t)((s + tt) * 64);
               const uint32_t sa = st + s * 2 * kTileBytes, sb = st + kAB + tt * kTileBytes;
-              mma_f16(dt, smem_desc(sa), smem_desc(sb), (first && s == 0) ? 0u : 1u);
-              mma_f16(dt, smem_desc(sa + 256), smem_desc(sb + 256), 1u);
+              mma_f16(dt, smem_desc(sa), smem_desc(sb), (first && s == 0) ? 0u : 1u, idesc);
+              mma_f16(dt, smem_desc(sa + 256), smem_desc(sb + 256), 1u, idesc);
             }
         }
         mma_commit(smem_u32(&bar_free[buf]));
@@ -407,7 +425,7 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
         const int n = n0 + j;
         if (n < d.N) {
           const double v = scaled_int_to_double(tot[j * kGemmThreads + tid], ea + eB_s[j], neg);
-          double* c = C + r + (int64_t)n * d.ldc;
+          double* c = C + (r + (int64_t)n * d.ldc) * d.cscale + d.coff;
           if (d.atomic) atomicAdd(c, v); else *c = v;
         }
       }

@@ -74,14 +74,34 @@ def test_split_per_supernode_schedule(torch):
     assert np.abs(sn - sn64).max() <= 1e-9 * np.abs(sn64).max()
 
 
-def test_split_complex_is_reported_unsupported(torch):
+COMPLEX_CASES = [
+    ("stencil27_c", lambda: gen.stencil27_complex(8, 68, max_sn=64)),
+    ("cfg3_small", lambda: gen.make_config(3, size=10)),
+    ("grid2d_c", lambda: gen.conv_diff_2d(24, 69, imag_diag=0.1, max_sn=64)),
+    ("random_c", lambda: gen.random_struct_sym(250, 0.03, 70, complex_values=True, max_sn=20)),
+]
+
+
+@pytest.mark.parametrize("name,maker", COMPLEX_CASES, ids=[c[0] for c in COMPLEX_CASES])
+def test_split_complex_matches_oracle(torch, name, maker):
+    """Complex products through the real embedding of the sliced GEMM."""
+    p = maker()
+    st, sn, pa, sn64 = run_split(torch, p)
+    compare_full(p, st, sn, 0, 20, tol=TOL_SPLIT)
+    assert np.abs(sn - sn64).max() <= 1e-9 * np.abs(sn64).max()
+
+
+def test_split_complex_shift_batch(torch):
+    """Several complex shifts of one pattern (a pole-expansion batch)."""
     import paper_1708_04539_gb300 as ps
-    p = gen.stencil27_complex(4, 68, max_sn=32)
+    p = gen.shifted_family(7, 71, nshift=4, max_sn=64)
     h = ps.SelInv.from_problem(p)
     h.factor(torch.from_numpy(p.values).cuda())
-    with pytest.raises(ps.PselinvError) as e:
-        h.selinv(precision=ps.PREC_OZAKI_FP16)
-    assert e.value.code == -8
+    h.selinv(precision=ps.PREC_OZAKI_FP16)
+    st = h.structure()
+    for b in range(p.nbatch):
+        compare_full(p, st, h.get_selected(batch=b, layout=ps.LAYOUT_SUPERNODAL), b, 20,
+                     tol=TOL_SPLIT)
     h.close()
 
 
