@@ -511,12 +511,22 @@ void add_slice_step(Plan& P, const std::vector<SliceDesc>& descs, int level, boo
   P.steps.push_back(st);
 }
 
+// K blocks (of 32) of one exact accumulation chunk of the sliced GEMM, and
+// the most chunks one task may add into its 64-bit totals
+constexpr int kOzChunkBlocks = 16;
+constexpr int kOzMaxChunks = 31;
+
+// smallest K split keeping every task within kOzMaxChunks chunks
+int min_ozaki_ksplit(const OzDesc& d) {
+  return std::max(1, ceil_div(d.K32, kOzChunkBlocks * kOzMaxChunks));
+}
+
 // ksplit so that a launch has about two CTAs per SM (one CTA fits an SM)
 int choose_ozaki_ksplit(const std::vector<OzDesc>& descs) {
   int64_t tiles = 0, kmax = 1;
   for (const auto& d : descs) {
     tiles += (int64_t)ceil_div(d.M, 128) * ceil_div(d.N, 64);
-    kmax = std::max<int64_t>(kmax, ceil_div(d.K32, 4));
+    kmax = std::max<int64_t>(kmax, ceil_div(d.K32, kOzChunkBlocks));
   }
   if (tiles == 0) return 1;
   const int64_t want = (2 * 152 + tiles - 1) / tiles;
@@ -530,7 +540,7 @@ void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool
   double flops = 0;
   for (size_t d = 0; d < descs.size(); d++) {
     OzDesc& g = descs[d];
-    g.ksplit = std::min(ks, std::max(1, ceil_div(g.K32, 4)));
+    g.ksplit = std::max(min_ozaki_ksplit(g), std::min(ks, std::max(1, ceil_div(g.K32, kOzChunkBlocks))));
     g.atomic = (force_atomic || g.ksplit > 1) ? 1 : 0;
     for (int k = 0; k < g.ksplit; k++)
       for (int tn = 0; tn < ceil_div(g.N, 64); tn++)

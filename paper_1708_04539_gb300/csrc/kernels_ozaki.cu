@@ -14,10 +14,12 @@
 // (the FP64 pipe of GB300 is too slow to slice with).
 // Products.  For slice pairs (s, t) with s + t = d <= S-1, the products
 // a_s(A) b_t(B) are summed in one FP32 tensor-memory accumulator per weight
-// d over 128 values of K: at most 6 pairs x 128 x 2^14 < 2^24, so every
-// partial sum is an exact integer.  After each 128-wide chunk the S
-// accumulators are drained into a 64-bit integer per output,
-//   T += sum_d P_d 2^{7(S-1-d)}  (< 2^60 over the whole K for S <= 6),
+// d over 512 values of K: one value of K adds at most 2^14 (d = 0, 1) and at
+// most 2 x 2^13 + (d-1) 2^12 <= 2^15 (d <= 5) to an accumulator, so every
+// partial sum stays an integer of magnitude <= 2^24, exact in FP32.  After
+// each 512-wide chunk the S accumulators are drained into a 64-bit integer
+// per output held in tensor memory,
+//   T += sum_d P_d 2^{7(S-1-d)}   (|T| < 31 x 2^58.01 < 2^63 for K <= 31 x 512),
 // and at the end C = T 2^{e_r(A) + e_c(B) - 14 - 7(S-1)} in FP64.
 // The only rounding is the slice truncation and the final int64 -> FP64
 // conversion.
@@ -40,6 +42,7 @@ constexpr int kSliceThreads = 256;
 constexpr int kGemmThreads = 128;
 constexpr int kTileBytes = 4096;  // 64 rows x 32 K x 2 bytes
 constexpr long kSpinLimit = 1L << 26;
+constexpr int kChunk = 16;  // 32-wide K blocks per exact accumulation chunk (512 values)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -266,6 +269,43 @@ __device__ __forceinline__ double scaled_int_to_double(long long v, int e, bool 
   return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,"
+      "%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,"
+      "%62,%63}, [%64];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]),
+        "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]),
+        "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]),
+        "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+        "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]),
+        "=r"(v[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint32_t (&v)[64]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,"
+      "%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,"
+      "%61,%62,%63,%64};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+      "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+      "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]),
+      "r"(v[32]), "r"(v[33]), "r"(v[34]), "r"(v[35]), "r"(v[36]), "r"(v[37]), "r"(v[38]), "r"(v[39]),
+      "r"(v[40]), "r"(v[41]), "r"(v[42]), "r"(v[43]), "r"(v[44]), "r"(v[45]), "r"(v[46]), "r"(v[47]),
+      "r"(v[48]), "r"(v[49]), "r"(v[50]), "r"(v[51]), "r"(v[52]), "r"(v[53]), "r"(v[54]), "r"(v[55]),
+      "r"(v[56]), "r"(v[57]), "r"(v[58]), "r"(v[59]), "r"(v[60]), "r"(v[61]), "r"(v[62]), "r"(v[63])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // sliced GEMM: one 128 x 64 output tile (and one K range) per task
 // ---------------------------------------------------------------------------
@@ -309,14 +349,16 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
     const OzDesc d = descs[task.d];
     const int m0 = task.tm * 128, n0 = task.tn * 64;
     int per = (d.K32 + d.ksplit - 1) / d.ksplit;
-    per = (per + 3) / 4 * 4;
+    per = (per + kChunk - 1) / kChunk * kChunk;
     const int kb0 = task.ks * per;
     const int kb1 = min(d.K32, kb0 + per);
     const int nkb = kb1 - kb0;
     if (tid < 64) eB_s[tid] = (n0 + tid < d.N) ? d.eB[n0 + tid] : 0;
-    // per-thread 64-bit totals live in shared memory: tot[j * 128 + tid]
-    long long* tot = reinterpret_cast<long long*>(smem + 2 * kStage);
-    for (int j = 0; j < 64; j++) tot[j * kGemmThreads + tid] = 0;
+    // per-row 64-bit totals live in tensor memory after the S accumulators:
+    // value j of the thread's row at columns S*64 + 2j (low) and + 2j + 1 (high)
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t ttot = trow + (uint32_t)(S * 64);
+    bool first_chunk = true;
     __syncthreads();
 
     // stage loader (thread 0): S slices x {2 A tiles, 1 B tile}
@@ -345,7 +387,7 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
 
     for (int i = 0; i < nkb; i++) {
       const int buf = i & 1;
-      const bool chunk_end = (i % 4 == 3) || (i == nkb - 1);
+      const bool chunk_end = (i % kChunk == kChunk - 1) || (i == nkb - 1);
       if (tid == 0 && ok) {
         if (i == 0) issue_load(kb0, 0);
         if (i + 1 < nkb) {
@@ -361,16 +403,20 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
         fence_after();
         if (ok) {
           const uint32_t st = smem_u32(smem + buf * kStage);
-          const bool first = (i % 4) == 0;
+          const bool first = (i % kChunk) == 0;
           const uint32_t idesc = (d.neg_half && kb0 + i >= d.half) ? kIdescNegA : kIdesc;
-#pragma unroll 1
+          // descriptors of the stage bases; an offset within shared memory is
+          // added to the address field (bits 0-13 hold address >> 4)
+          const uint64_t a0 = smem_desc(st), b0 = smem_desc(st + kAB);
+#pragma unroll
           for (int s = 0; s < S; s++)
-#pragma unroll 1
+#pragma unroll
             for (int tt = 0; tt < S - s; tt++) {
               const uint32_t dt = tmem + (uint32_t)((s + tt) * 64);
-              const uint32_t sa = st + s * 2 * kTileBytes, sb = st + kAB + tt * kTileBytes;
-              mma_f16(dt, smem_desc(sa), smem_desc(sb), (first && s == 0) ? 0u : 1u, idesc);
-              mma_f16(dt, smem_desc(sa + 256), smem_desc(sb + 256), 1u, idesc);
+              const uint64_t ad = a0 + (uint64_t)((s * 2 * kTileBytes) >> 4);
+              const uint64_t bd = b0 + (uint64_t)((tt * kTileBytes) >> 4);
+              mma_f16(dt, ad, bd, (s == 0 && first) ? 0u : 1u, idesc);
+              mma_f16(dt, ad + (256 >> 4), bd + (256 >> 4), 1u, idesc);
             }
         }
         mma_commit(smem_u32(&bar_free[buf]));
@@ -392,14 +438,23 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
           for (int dd = 0; dd < S; dd++) {
             const int shift = 7 * (S - 1 - dd);
             uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dd * 64 + h * 32), v);
+            tmem_ld32(trow + (uint32_t)(dd * 64 + h * 32), v);
 #pragma unroll
             for (int j = 0; j < 32; j++)
               part[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shift;
           }
+          uint32_t tv[64];
+          if (!first_chunk) tmem_ld64(ttot + (uint32_t)(h * 64), tv);
 #pragma unroll
-          for (int j = 0; j < 32; j++) tot[(h * 32 + j) * kGemmThreads + tid] += part[j];
+          for (int j = 0; j < 32; j++) {
+            long long t = part[j];
+            if (!first_chunk) t += (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
+            tv[2 * j] = (uint32_t)t;
+            tv[2 * j + 1] = (uint32_t)((unsigned long long)t >> 32);
+          }
+          tmem_st64(ttot + (uint32_t)(h * 64), tv);
         }
+        first_chunk = false;
         fence_before();
         __syncthreads();
       }
@@ -415,20 +470,30 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
     if (!ok && lane == 0) atomicExch(err, DEV_TIMEOUT);
     // epilogue: thread row r of the tile
     const int r = m0 + warp * 32 + lane;
-    if (r < d.M && nkb > 0) {
+    if (nkb > 0) {
       // alpha is +-1: its sign is folded into the assembled doubles
-      const int ea = d.eA[r] - 14 - 7 * (S - 1);
+      const int ea = (r < d.M ? d.eA[r] : 0) - 14 - 7 * (S - 1);
       const bool neg = d.alpha < 0.0;
       double* C = d.C;
-#pragma unroll 4
-      for (int j = 0; j < 64; j++) {
-        const int n = n0 + j;
-        if (n < d.N) {
-          const double v = scaled_int_to_double(tot[j * kGemmThreads + tid], ea + eB_s[j], neg);
-          double* c = C + (r + (int64_t)n * d.ldc) * d.cscale + d.coff;
-          if (d.atomic) atomicAdd(c, v); else *c = v;
+      fence_after();
+#pragma unroll 1
+      for (int h = 0; h < 2; h++) {
+        uint32_t tv[64];
+        tmem_ld64(ttot + (uint32_t)(h * 64), tv);  // all lanes: the load is warp-wide
+        if (r < d.M) {
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            const int n = n0 + h * 32 + j;
+            if (n < d.N) {
+              const long long t = (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
+              const double v = scaled_int_to_double(t, ea + eB_s[h * 32 + j], neg);
+              double* c = C + (r + (int64_t)n * d.ldc) * d.cscale + d.coff;
+              if (d.atomic) atomicAdd(c, v); else *c = v;
+            }
+          }
         }
       }
+      fence_before();
     }
     if (__syncthreads_or(!ok)) {
       ok = false;
@@ -443,7 +508,7 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
 
 template <int S>
 constexpr int gemm_smem() {
-  return 2 * (S * 2 * kTileBytes + S * kTileBytes) + 64 * kGemmThreads * 8;
+  return 2 * (S * 2 * kTileBytes + S * kTileBytes);
 }
 
 __global__ void zero_kernel(const CopySeg* __restrict__ segs, int nseg) {
