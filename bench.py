@@ -239,6 +239,23 @@ def roofline_from_profile(prof, slices):
                  for n, v in kinds.items()}
 
 
+def max_over_ranks(value, dist, device):
+    """Largest value over all ranks (the job's time is its slowest replica)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(flops_per_rank, elapsed_ms_max, steps, world):
+    """Whole-job throughput (GFLOP/s) of `world` replicas that each ran `steps`
+    steps of `flops_per_rank` in at most `elapsed_ms_max` ms."""
+    ms_per_step = elapsed_ms_max / steps
+    return world * flops_per_rank / (ms_per_step * 1e-3) / 1e9, ms_per_step
+
+
 def traffic_from_profiles(kernel):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -364,13 +381,8 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     h.sync(stream=stream)
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    ms_per_step = elapsed_ms / args.steps
-    value = world * flops / (ms_per_step * 1e-3) / 1e9
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    value, ms_per_step = aggregate_throughput(flops, elapsed_ms, args.steps, world)
 
     # launch-by-launch replay with CUDA events on the same stream
     prof = [] if args.no_profile else h.profile(0, stream=stream)
@@ -399,11 +411,7 @@ def run_ours(args):
                 h.selinv(precision=prec, stream=stream)
                 h.get_selected(out_host, stream=stream)
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, "cuda")
         e2e = {"value": world * flops / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(p.nnz * 8), "d2h_bytes_per_step": int(p.nnz * 8),
                "ms_per_step": e2e_s * 1e3,

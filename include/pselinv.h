@@ -276,6 +276,15 @@ void pselinv_model_free(pselinv_model_t m);
  * up to cap are copied). */
 int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int64_t* count);
 
+/* Exercise the bounded-wait failure path (not from the paper): launch a
+ * kernel whose only wait (on a tensor-core completion barrier) can never
+ * complete, with a budget of budget_us microseconds (1 .. 2e6).  Every wait
+ * in the library is bounded the same way (2 s): it records a timeout status
+ * and the kernel returns instead of hanging.  Returns PSELINV_ERR_TIMEOUT
+ * when the timeout was detected and reported to the host (the expected
+ * result), PSELINV_OK if it was not. */
+int pselinv_wait_selftest(void* stream, int64_t budget_us);
+
 /* Wait for `stream` and report a device-side error recorded by earlier calls. */
 int pselinv_sync(pselinv_t h, void* stream);
 

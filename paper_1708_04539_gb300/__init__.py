@@ -6,6 +6,7 @@ arguments.  There is no CPU fallback: if the library has not been built,
 every entry point raises ``LibraryMissing``.
 """
 from .binding import (  # noqa: F401
+    supernodal_coordinates,
     LibraryMissing,
     PselinvError,
     SelInv,
@@ -22,6 +23,7 @@ from .binding import (  # noqa: F401
     LAYOUT_SUPERNODAL,
     LAYOUT_FACTORS,
     CostModel,
+    InstanceGroup,
     TUNE_RESET,
     TUNE_EXHAUSTIVE,
     TUNE_MODEL,

@@ -29,6 +29,7 @@ _EXPORTS = [
     "pselinv_get_selected", "pselinv_get_structure", "pselinv_profile", "pselinv_plan_stats",
     "pselinv_sync", "pselinv_last_info", "pselinv_error_string", "pselinv_free",
     "pselinv_block_inverse_noalloc", "pselinv_tune", "pselinv_tune_records",
+    "pselinv_wait_selftest",
     "pselinv_model_create", "pselinv_model_train", "pselinv_model_gradients",
     "pselinv_model_predict", "pselinv_model_get_params", "pselinv_model_set_params",
     "pselinv_model_encode", "pselinv_model_free",
@@ -131,6 +132,8 @@ def load_library():
     lib.pselinv_free.restype = None
     lib.pselinv_block_inverse_noalloc.argtypes = [ctypes.c_int, I64, P, I64, P, I64, P]
     lib.pselinv_block_inverse_noalloc.restype = ctypes.c_int
+    lib.pselinv_wait_selftest.argtypes = [P, I64]
+    lib.pselinv_wait_selftest.restype = ctypes.c_int
     RP = ctypes.POINTER(TuneRecord)
     lib.pselinv_tune.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     lib.pselinv_tune.restype = ctypes.c_int
@@ -459,6 +462,52 @@ def block_inverse_noalloc(lu_block, out, s=None, stream=None):
     if rc != 0:
         raise PselinvError(rc, "pselinv_block_inverse_noalloc")
     return out
+
+
+class InstanceGroup:
+    """Several independent matrices of different patterns in one handle.
+
+    The direct sum A_1 (+) A_2 (+) ... is block diagonal, its elimination tree
+    is the forest of the instances' trees, and the depth levels of the sweep
+    then hold supernodes of every instance: one factorisation and one
+    selected inversion (one set of level launches) serve the whole group.
+    The selected inverse of a block-diagonal matrix is the block diagonal of
+    the selected inverses, so each instance's result is a slice of the
+    group's.
+    """
+
+    def __init__(self, patterns, **kw):
+        """patterns: list of (n, colptr, rowind, perm or None)."""
+        self.n = [int(p[0]) for p in patterns]
+        self.nnz = [int(np.asarray(p[1])[-1]) for p in patterns]
+        self.row_off = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
+        self.nz_off = np.concatenate([[0], np.cumsum(self.nnz)]).astype(np.int64)
+        N = int(self.row_off[-1])
+        colptr = [np.zeros(1, dtype=np.int64)]
+        rowind, perm = [], []
+        for i, (n, cp, ri, pm) in enumerate(patterns):
+            cp = np.asarray(cp, dtype=np.int64)
+            colptr.append(cp[1:] + self.nz_off[i])
+            rowind.append(np.asarray(ri, dtype=np.int64) + self.row_off[i])
+            pm = np.arange(n, dtype=np.int64) if pm is None else np.asarray(pm, dtype=np.int64)
+            perm.append(pm + self.row_off[i])
+        self.colptr = np.concatenate(colptr)
+        self.rowind = np.concatenate(rowind)
+        self.perm = np.concatenate(perm)
+        self.handle = SelInv(N, self.colptr, self.rowind, self.perm, **kw)
+
+    def values(self, per_instance):
+        """Concatenate the instances' CSC values (host arrays)."""
+        return np.concatenate([np.asarray(v) for v in per_instance])
+
+    def split(self, out):
+        """Per-instance views of a pattern-of-A result of the group."""
+        return [out[self.nz_off[i]:self.nz_off[i + 1]] for i in range(len(self.n))]
+
+
+def wait_selftest(budget_us=20000, stream=None):
+    """Status of the bounded-wait check (PSELINV_ERR_TIMEOUT = -6 expected)."""
+    return int(load_library().pselinv_wait_selftest(_stream(stream), int(budget_us)))
 
 
 def supernodal_coordinates(st: dict):

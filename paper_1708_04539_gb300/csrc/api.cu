@@ -890,7 +890,12 @@ int run_steps(pselinv_ctx* h, Plan& P, cudaStream_t st) {
     CK(cudaGetLastError());
     return PSELINV_OK;
   }
-  if (!h->side_stream) CK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+  if (!h->side_stream) {
+    // lowest priority: pending CTAs of the sweep are scheduled first
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(cudaStreamCreateWithPriority(&h->side_stream, cudaStreamNonBlocking, lo));
+  }
   cudaStream_t side = h->side_stream;
   CK(cudaEventRecord(P.ev[0], st));
   CK(cudaStreamWaitEvent(side, P.ev[0], 0));
@@ -1361,6 +1366,27 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
   CK(cudaStreamSynchronize(st));
   h->inverted = true;
   return PSELINV_OK;
+}
+
+int pselinv_wait_selftest(void* stream, int64_t budget_us) {
+  if (budget_us < 1 || budget_us > 2000000) return PSELINV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* derr = nullptr;
+  CK(cudaMalloc(&derr, 4 * sizeof(int)));
+  int herr[2] = {0, 0};
+  cudaError_t e = cudaMemsetAsync(derr, 0, 4 * sizeof(int), st);
+  if (e == cudaSuccess) {
+    launch_wait_selftest(derr, (unsigned long long)budget_us * 1000ull, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(herr, derr, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(derr);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_status(e);
+  }
+  return herr[0] == DEV_TIMEOUT ? PSELINV_ERR_TIMEOUT : PSELINV_OK;
 }
 
 int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int64_t* count) {

@@ -193,6 +193,9 @@ void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bo
 void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
                        cudaStream_t st);
 void launch_zero(const CopySeg* segs, int nseg, cudaStream_t st);
+// a kernel whose only wait never completes: it gives up after budget_ns and
+// records DEV_TIMEOUT in err[0]
+void launch_wait_selftest(int* err, unsigned long long budget_ns, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // launch functions (kernels_*.cu)

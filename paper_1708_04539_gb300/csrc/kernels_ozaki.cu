@@ -41,7 +41,7 @@ namespace {
 constexpr int kSliceThreads = 256;
 constexpr int kGemmThreads = 128;
 constexpr int kTileBytes = 4096;  // 64 rows x 32 K x 2 bytes
-constexpr long kSpinLimit = 1L << 26;
+constexpr unsigned long long kWaitBudgetNs = 2000000000ull;  // 2 s per bounded wait
 constexpr int kChunk = 16;  // 32-wide K blocks per exact accumulation chunk (512 values)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -212,9 +212,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
                : "memory");
 }
-// bounded wait on a phase parity; false after the spin limit
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long it = 0; it < kSpinLimit; it++) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait on a phase parity: false once `budget_ns` of wall-clock time
+// has passed without the phase completing
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          unsigned long long budget_ns = kWaitBudgetNs) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -223,8 +231,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
+    if (global_ns() - t0 > budget_ns) return false;
   }
-  return false;
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
   asm volatile(
@@ -511,6 +519,18 @@ constexpr int gemm_smem() {
   return 2 * (S * 2 * kTileBytes + S * kTileBytes);
 }
 
+// Failure-path check: wait on an mbarrier that nothing will complete, with a
+// short budget, and record the timeout like any other bounded wait.
+__global__ void wait_selftest_kernel(int* err, unsigned long long budget_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0, budget_ns)) set_error(err, DEV_TIMEOUT, 0);
+}
+
 __global__ void zero_kernel(const CopySeg* __restrict__ segs, int nseg) {
   for (int s = blockIdx.y; s < nseg; s += gridDim.y) {
     const CopySeg g = segs[s];
@@ -553,6 +573,10 @@ void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntas
     case 5: ozaki_gemm_kernel<5><<<grid, kGemmThreads, gemm_smem<5>(), st>>>(descs, tasks, ntasks, err); break;
     default: ozaki_gemm_kernel<6><<<grid, kGemmThreads, gemm_smem<6>(), st>>>(descs, tasks, ntasks, err); break;
   }
+}
+
+void launch_wait_selftest(int* err, unsigned long long budget_ns, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(err, budget_ns);
 }
 
 void launch_zero(const CopySeg* segs, int nseg, cudaStream_t st) {

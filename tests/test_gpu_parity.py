@@ -228,3 +228,39 @@ def test_config2_full_size_sampled(torch):
     np.add.at(rowsum, p.rowind, p.values * B[tpos])
     assert np.abs(rowsum - 1).max() < 1e-11
     h.close()
+
+
+def test_uneven_instances_in_one_sweep(torch):
+    """Matrices of different sizes (the uneven 2D grids of the pole-expansion
+    workload, at reduced sizes) grouped as a direct sum: one factorisation and
+    one selected inversion; every instance matches its own oracle result."""
+    import paper_1708_04539_gb300 as ps
+    probs = gen.make_config(4, size=12, instances=6)[1:]   # 6 complex 2D grids, sides 6..12
+    g = ps.InstanceGroup([(q.n, q.colptr, q.rowind, q.perm) for q in probs], max_supernode=64)
+    vals = g.values([q.values for q in probs])
+    g.handle.factor(torch.from_numpy(vals).cuda())
+    for prec, tol in ((ps.PREC_FP64, 1e-10), (ps.PREC_OZAKI_FP16, 1e-9)):
+        g.handle.selinv(precision=prec)
+        parts = g.split(g.handle.get_selected())
+        for q, got in zip(probs, parts):
+            ref = oracle.extract(oracle.selected_inverse(q), q.colptr, q.rowind)
+            assert selected_error(got, ref, q.rowind, csc_cols(q.colptr), q.n) < tol
+    st = g.handle.structure()
+    roots = np.sum(st["sn_parent"] == -1)
+    assert roots >= len(probs)   # a forest: at least one root per instance
+    g.handle.close()
+
+
+def test_bounded_wait_reports_timeout(torch):
+    """A device wait that can never complete gives up within its budget and
+    the host sees PSELINV_ERR_TIMEOUT; the context stays usable."""
+    import time
+    from paper_1708_04539_gb300.binding import wait_selftest
+    t0 = time.perf_counter()
+    assert wait_selftest(20000) == -6
+    assert time.perf_counter() - t0 < 10.0
+    # the device still works afterwards
+    p = gen.make_config(1)
+    h, st, sn, pa, fac = gpu_run(torch, p)
+    compare_full(p, st, sn[0], 0, 20)
+    h.close()
