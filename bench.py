@@ -46,8 +46,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--schedule", default="level", choices=["level", "per_supernode"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "ozaki"],
-                    help="fp64: every product in FP64; ozaki: FP16-sliced tensor-core products")
+    ap.add_argument("--precision", default="ozaki", choices=["fp64", "ozaki"],
+                    help="ozaki: FP16-sliced tensor-core products (default); fp64: every product in FP64")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP64 level-batched / per-supernode comparison and error report")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
@@ -237,6 +239,62 @@ def roofline_from_profile(prof, slices):
     rec["launches_per_step"] = k["launches"]
     return rec, {n: {"launches": v["launches"], "ms": v["ms"], "share": v["share"]}
                  for n, v in kinds.items()}
+
+
+def selected_error(x, r, rows, cols, n):
+    """max |x - r| / max(row max, column max of |r|) over the entries given."""
+    a = np.abs(r)
+    rowmax = np.zeros(n)
+    colmax = np.zeros(n)
+    np.maximum.at(rowmax, rows, a)
+    np.maximum.at(colmax, cols, a)
+    rho = np.maximum(rowmax[rows], colmax[cols])
+    rho[rho == 0] = 1.0
+    return float(np.max(np.abs(x - r) / rho))
+
+
+def time_steps(h, prec, stream, steps, out_dev):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        h.selinv(precision=prec, stream=stream)
+        h.get_selected(out_dev, stream=stream)
+        e0.record(stream)
+        for _ in range(steps):
+            h.selinv(precision=prec, stream=stream)
+            h.get_selected(out_dev, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def comparison(p, h, stream, out_dev, flops):
+    """FP64 level-batched and FP64 per-supernode sweeps of the same matrix,
+    and the error of the split-precision result against the FP64 one."""
+    import torch
+    import paper_1708_04539_gb300 as ps
+    from paper_1708_04539_gb300.binding import supernodal_coordinates
+    st = h.structure()
+    rows, cols = supernodal_coordinates(st)
+    h.selinv(precision=ps.PREC_OZAKI_FP16, stream=stream)
+    split = h.get_selected(layout=ps.LAYOUT_SUPERNODAL, stream=stream)
+    h.tune(precision=ps.PREC_FP64, mode=ps.TUNE_EXHAUSTIVE, stream=stream)
+    fp64_level_ms = time_steps(h, ps.PREC_FP64, stream, 3, out_dev)
+    ref = h.get_selected(layout=ps.LAYOUT_SUPERNODAL, stream=stream)
+    err = selected_error(split, ref, rows, cols, p.n)
+    normwise = float(np.max(np.abs(split - ref)) / np.max(np.abs(ref)))
+    g = ps.SelInv.from_problem(p, relax_pct=20, schedule=ps.SCHED_PER_SUPERNODE)
+    with torch.cuda.stream(stream):
+        g.factor(torch.from_numpy(p.values).cuda(), stream=stream)
+    per_sn_ms = time_steps(g, ps.PREC_FP64, stream, 2, out_dev)
+    g.close()
+    return {"fp64_level_batched_ms": fp64_level_ms,
+            "fp64_level_batched_gflops": flops / (fp64_level_ms * 1e-3) / 1e9,
+            "fp64_per_supernode_ms": per_sn_ms,
+            "fp64_per_supernode_gflops": flops / (per_sn_ms * 1e-3) / 1e9,
+            "split_vs_fp64_selected_error": err, "split_vs_fp64_normwise_error": normwise,
+            "error_metric": "max |x - r| / max(max_k |r_ik|, max_k |r_kj|) over every entry "
+                            "of the pattern of L+U; r = FP64 GPU result"}
 
 
 def max_over_ranks(value, dist, device):
@@ -443,9 +501,11 @@ def run_ours(args):
         "kernel_shares": kinds,
         "clocks": clk.summary(),
     }
-    h.close()
     if not prof:
         line["roofline"] = None
+    if not args.no_compare and args.precision == "ozaki" and rank == 0:
+        line["comparison"] = comparison(p, h, stream, out_dev, flops)
+    h.close()
     if rank == 0 and world == 1 and not args.skip_cpu_baseline and args.size == 40:
         line["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:

@@ -786,8 +786,23 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++)
         groups.push_back({H.level_sn[i]});
     }
+    // split precision: each level runs either the sliced tensor-core products
+    // or (for levels whose products are too small to pay for the slicing) the
+    // FP64 ones; the default is a flop threshold, the tuner times both
+    int mode = 0;
+    if (precision == PSELINV_PREC_OZAKI_FP16) {
+      double lf = 0;
+      for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
+        const double c = (double)cK(H, H.level_sn[i]), w = (double)H.sn_width[H.level_sn[i]];
+        lf += 4.0 * c * c * w;
+      }
+      lf *= (double)nb * (dt == DT_F64 ? 1.0 : 4.0);
+      mode = tuned_value(h, precision, (int)lev, 3, lf < 2e8 ? 1 : 0);
+    }
+    const int slot_main = precision == PSELINV_PREC_OZAKI_FP16 ? 4 : 1;
+    const int slot_diag = precision == PSELINV_PREC_OZAKI_FP16 ? 5 : 2;
     for (const auto& grp : groups) {
-      if (precision == PSELINV_PREC_OZAKI_FP16) {
+      if (precision == PSELINV_PREC_OZAKI_FP16 && mode == 0) {
         add_ozaki_level(h, P, grp, nb, gbase, (int)lev);
         continue;
       }
@@ -824,8 +839,10 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       g.offs = P.push(gofs);
       g.level = (int)lev;
       P.steps.push_back(g);
-      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, 1, cfg), main, (int)lev, 1);
-      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, 2, cfg), dg, (int)lev, 2);
+      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_main, cfg), main, (int)lev,
+                    slot_main);
+      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_diag, cfg), dg, (int)lev,
+                    slot_diag);
     }
     if (P.steps.size() > first_main) P.steps[first_main].wait = 2 + (int)lev;
   }
@@ -1297,25 +1314,31 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
       }
     }
   std::map<std::tuple<int, int, int, int>, double> best_ms;  // (level, slot, kind, value) -> ms
-  const int ncand = precision == PSELINV_PREC_FP64 ? 3 : 5;
+  std::map<std::pair<int, int>, double> level_ms;             // (level, mode) -> main-stream ms
   std::vector<pselinv_step_stat> stats;
-  for (int v = 0; v < ncand; v++) {
-    for (const Key& k : keys) {
-      const int val = k.kind == ST_GEMM ? gemm_cands[v % 3] : ks_cands[v];
-      h->tuned[std::make_tuple(precision, k.level, k.slot)] = val;
-    }
-    rc = rebuild();
-    if (rc != PSELINV_OK) return rc;
+  auto measure = [&](int mode_tag) -> int {
+    int r = rebuild();
+    if (r != PSELINV_OK) return r;
     h->last_precision = precision;
     Plan& P = h->selinv_plan[precision][sched];
+    for (const Step& s : P.steps)
+      if (s.slot >= 0) {
+        const auto k = std::make_tuple(s.level, s.slot, (int)s.kind);
+        if (!feats.count(k)) {
+          keys.push_back({s.level, s.slot, (int)s.kind});
+          feats[k] = std::vector<float>(s.feat, s.feat + 8);
+        }
+      }
     for (int rep = 0; rep < 2; rep++) {
       stats.assign(P.steps.size(), pselinv_step_stat{});
       int64_t cnt = 0;
-      rc = pselinv_profile(h, 0, stream, stats.data(), (int64_t)stats.size(), &cnt);
-      if (rc != PSELINV_OK) return rc;
+      r = pselinv_profile(h, 0, stream, stats.data(), (int64_t)stats.size(), &cnt);
+      if (r != PSELINV_OK) return r;
       std::map<std::tuple<int, int, int, int>, double> acc;
+      std::map<int, double> lev_acc;
       for (size_t i = 0; i < P.steps.size(); i++) {
         const Step& s = P.steps[i];
+        if (!s.side && s.level >= 0) lev_acc[s.level] += stats[i].ms;
         if (s.slot < 0) continue;
         acc[std::make_tuple(s.level, s.slot, (int)s.kind, s.param)] += stats[i].ms;
       }
@@ -1323,7 +1346,45 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
         auto it = best_ms.find(kv.first);
         if (it == best_ms.end() || kv.second < it->second) best_ms[kv.first] = kv.second;
       }
+      if (mode_tag >= 0)
+        for (const auto& kv : lev_acc) {
+          const auto k = std::make_pair(kv.first, mode_tag);
+          auto it = level_ms.find(k);
+          if (it == level_ms.end() || kv.second < it->second) level_ms[k] = kv.second;
+        }
     }
+    return PSELINV_OK;
+  };
+  const int nlev = (int)h->H.level_ptr.size() - 1;
+  if (precision == PSELINV_PREC_FP64) {
+    for (int v = 0; v < 3; v++) {
+      for (const Key& k : keys) h->tuned[std::make_tuple(precision, k.level, k.slot)] = gemm_cands[v];
+      rc = measure(-1);
+      if (rc != PSELINV_OK) return rc;
+    }
+  } else {
+    // phase A: every level split, K splits 1..16
+    for (int v = 0; v < 5; v++) {
+      for (int l = 0; l < nlev; l++) {
+        h->tuned[std::make_tuple(precision, l, 3)] = 0;
+        h->tuned[std::make_tuple(precision, l, 1)] = ks_cands[v];
+        h->tuned[std::make_tuple(precision, l, 2)] = ks_cands[v];
+        h->tuned[std::make_tuple(precision, l, 0)] = gemm_cands[v % 3];
+      }
+      rc = measure(0);
+      if (rc != PSELINV_OK) return rc;
+    }
+    // phase B: every level FP64, tile shapes
+    for (int v = 0; v < 3; v++) {
+      for (int l = 0; l < nlev; l++) {
+        h->tuned[std::make_tuple(precision, l, 3)] = 1;
+        h->tuned[std::make_tuple(precision, l, 4)] = gemm_cands[v];
+        h->tuned[std::make_tuple(precision, l, 5)] = gemm_cands[v];
+      }
+      rc = measure(1);
+      if (rc != PSELINV_OK) return rc;
+    }
+    h->tuned.clear();
   }
   // keep the fastest candidate of every tunable launch; record everything
   h->records.clear();
@@ -1358,6 +1419,12 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
       h->records.push_back(r);
     }
   }
+  if (precision == PSELINV_PREC_OZAKI_FP16)
+    for (int l = 0; l < nlev; l++) {
+      auto a = level_ms.find(std::make_pair(l, 0)), b = level_ms.find(std::make_pair(l, 1));
+      if (a != level_ms.end() && b != level_ms.end())
+        h->tuned[std::make_tuple(precision, l, 3)] = b->second < a->second ? 1 : 0;
+    }
   rc = rebuild();
   if (rc != PSELINV_OK) return rc;
   // leave valid results of the tuned plan
