@@ -57,6 +57,11 @@ def parse():
                     help="skip the launch-by-launch replay (roofline fields become null)")
     ap.add_argument("--tune", default="exhaustive", choices=["none", "exhaustive"],
                     help="launch-shape autotuning before the timed region (untimed, like the factorisation)")
+    ap.add_argument("--plan-out", default=None,
+                    help="write the tuned launch shapes (JSON triples) to this path")
+    ap.add_argument("--plan-in", default=None,
+                    help="replay launch shapes written by --plan-out instead of tuning "
+                         "(profiling runs: timings under a profiler would mislead the tuner)")
     ap.add_argument("--dump-profile", default=None,
                     help="write the launch-by-launch profile (JSON) to this path")
     ap.add_argument("--size", type=int, default=40,
@@ -194,6 +199,9 @@ def measured_peaks():
         return {}
 
 
+GEMM_TEMPLATES = {0: "64,64,16", 1: "32,32,16", 2: "128,64,8"}  # tile config -> BM,BN,BK
+
+
 def roofline_from_profile(prof, slices):
     """Roofline record of the kernel kind with the largest share of the step."""
     kinds = {}
@@ -210,11 +218,17 @@ def roofline_from_profile(prof, slices):
         return None, kinds
     top = max(kinds, key=lambda k: kinds[k]["ms"])
     k = kinds[top]
+    by_param = {}
+    for r in prof:
+        if r["kind"] == top:
+            by_param[r.get("param", -1)] = by_param.get(r.get("param", -1), 0.0) + r["ms"]
+    main_param = max(by_param, key=by_param.get) if by_param else -1
     sec = k["ms"] * 1e-3
     peaks = measured_peaks()
     if top == "gemm":
         achieved = k["flops"] / sec / 1e12
-        rec = {"bound": "alu", "kernel": "gemm_kernel<double,64,64,16> (FP64 DFMA)",
+        tile = GEMM_TEMPLATES.get(main_param, "?")
+        rec = {"bound": "alu", "kernel": f"gemm_kernel<double,{tile}> (FP64 DFMA)",
                "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
                "traffic": traffic_from_profiles("gemm_kernel_f64")}
@@ -408,12 +422,21 @@ def run_ours(args):
 
     prec = ps.PREC_OZAKI_FP16 if args.precision == "ozaki" else ps.PREC_FP64
     tune_s = 0.0
-    if args.tune == "exhaustive":
+    tuning = args.tune
+    if args.plan_in:
+        with open(args.plan_in) as f:
+            h.plan_set([tuple(t) for t in json.load(f)["triples"]], prec)
+        tuning = "replayed"
+    elif args.tune == "exhaustive":
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             h.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE, stream=stream)
         torch.cuda.synchronize()
         tune_s = time.perf_counter() - t0
+    if args.plan_out:
+        with open(args.plan_out, "w") as f:
+            json.dump({"precision": args.precision, "size": args.size,
+                       "triples": h.plan_get(prec)}, f)
 
     def step():
         h.selinv(precision=prec, stream=stream)
@@ -446,8 +469,11 @@ def run_ours(args):
     prof = [] if args.no_profile else h.profile(0, stream=stream)
     roofline, kinds = roofline_from_profile(prof, slices=6)
     if args.dump_profile and rank == 0:
+        with torch.cuda.stream(stream):
+            fprof = h.profile(1, stream=stream)
         with open(args.dump_profile, "w") as f:
-            json.dump({"precision": args.precision, "size": args.size, "steps": prof}, f)
+            json.dump({"precision": args.precision, "size": args.size, "steps": prof,
+                       "factor_steps": fprof}, f)
 
     # end to end through the C ABI with host buffers: H2D values, factor,
     # selected inversion, D2H of the selected entries
@@ -488,7 +514,7 @@ def run_ours(args):
                    "supernodes": int(st["nsuper"]), "levels": int(st["nlevels"]),
                    "flops_per_matrix": flops, "flops_relaxed_structure": st["flops_selinv"],
                    "schedule": args.schedule, "cuda_graph": not args.no_graph,
-                   "tuning": args.tune, "tuning_seconds": tune_s,
+                   "tuning": tuning, "tuning_seconds": tune_s,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.0f MB of factors read per step)"
                          % (st["storage_size"] * 8 / 1e6)},

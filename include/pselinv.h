@@ -169,6 +169,9 @@ typedef struct pselinv_step_stat {
   double flops;   /* useful floating-point operations (real) */
   double bytes;   /* algorithmic bytes moved (operands read + results written) */
   double ms;      /* device time from CUDA events around the launch */
+  int32_t param;  /* GEMM: tile config (0 64x64, 1 32x32, 2 128x64); OZAKI_GEMM: K split;
+                     else -1 */
+  int32_t side;   /* 1 if issued on the side stream (overlapped normalisation), else 0 */
 } pselinv_step_stat;
 
 enum pselinv_step_kind {
@@ -186,8 +189,9 @@ enum pselinv_step_kind {
 int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out, int64_t cap,
                     int64_t* count);
 
-/* Number of kernel launches (and memsets) one pselinv_selinv and one
- * pselinv_factor issue with the current plans (0 if not built yet). */
+/* Number of kernel launches one pselinv_selinv and one pselinv_factor issue
+ * with the current plans (0 if not built yet).  Runtime memsets of the plan
+ * are not kernels of the library and are not counted. */
 int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_factor);
 
 /* Allocation-free inverse of one LU-factored diagonal block (the paper has
@@ -275,6 +279,22 @@ void pselinv_model_free(pselinv_model_t m);
 /* The records of the last exhaustive tuning (*count = number of records;
  * up to cap are copied). */
 int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int64_t* count);
+
+/* The tuned launch shapes of the plan of `precision`, as (level, slot,
+ * value) triples of int32 (not from the paper; a tuning cache, so that a
+ * plan tuned once can be replayed in another process).  Slots: 0
+ * normalisation GEMM tile config (0..2); FP64 plan: 1 steps 3+5, 2 step 4
+ * tile config (0..2); split plan: 1 steps 3+5, 2 step 4 K split (1, 2, 4, 8
+ * or 16), 3 level precision (0 split products, 1 FP64), 4 / 5 tile config
+ * of the FP64 launches of steps 3+5 / step 4.  Levels are depth levels
+ * (0 = roots), up to the structure's level count.
+ * get: *count = number of triples; up to cap are written to out[3 * cap].
+ * set: replaces all tuned values of `precision` (count = 0 restores the
+ *   built-in heuristic); the next pselinv_selinv rebuilds the plan.  An
+ *   out-of-range triple returns PSELINV_ERR_ARG and changes nothing.
+ *   Host-only: queues no GPU work. */
+int pselinv_plan_get(pselinv_t h, int precision, int32_t* out, int64_t cap, int64_t* count);
+int pselinv_plan_set(pselinv_t h, int precision, const int32_t* in, int64_t count);
 
 /* Exercise the bounded-wait failure path (not from the paper): launch a
  * kernel whose only wait (on a tensor-core completion barrier) can never

@@ -29,7 +29,7 @@ _EXPORTS = [
     "pselinv_get_selected", "pselinv_get_structure", "pselinv_profile", "pselinv_plan_stats",
     "pselinv_sync", "pselinv_last_info", "pselinv_error_string", "pselinv_free",
     "pselinv_block_inverse_noalloc", "pselinv_tune", "pselinv_tune_records",
-    "pselinv_wait_selftest",
+    "pselinv_plan_get", "pselinv_plan_set", "pselinv_wait_selftest",
     "pselinv_model_create", "pselinv_model_train", "pselinv_model_gradients",
     "pselinv_model_predict", "pselinv_model_get_params", "pselinv_model_set_params",
     "pselinv_model_encode", "pselinv_model_free",
@@ -74,7 +74,8 @@ class TuneRecord(ctypes.Structure):
 
 class StepStat(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("tasks", ctypes.c_int64),
-                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("ms", ctypes.c_double),
+                ("param", ctypes.c_int32), ("side", ctypes.c_int32)]
 
 
 class Structure(ctypes.Structure):
@@ -139,6 +140,10 @@ def load_library():
     lib.pselinv_tune.restype = ctypes.c_int
     lib.pselinv_tune_records.argtypes = [P, RP, I64, ctypes.POINTER(I64)]
     lib.pselinv_tune_records.restype = ctypes.c_int
+    lib.pselinv_plan_get.argtypes = [P, ctypes.c_int, P, I64, ctypes.POINTER(I64)]
+    lib.pselinv_plan_get.restype = ctypes.c_int
+    lib.pselinv_plan_set.argtypes = [P, ctypes.c_int, P, I64]
+    lib.pselinv_plan_set.restype = ctypes.c_int
     lib.pselinv_model_create.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(P)]
     lib.pselinv_model_create.restype = ctypes.c_int
     lib.pselinv_model_train.argtypes = [P, RP, I64, ctypes.c_int32, ctypes.c_float, P,
@@ -279,7 +284,8 @@ class SelInv:
                                               ctypes.byref(cnt)), "pselinv_profile")
         return [{"kind": STEP_KINDS.get(buf[i].kind, buf[i].kind), "level": buf[i].level,
                  "tasks": buf[i].tasks, "flops": buf[i].flops, "bytes": buf[i].bytes,
-                 "ms": buf[i].ms} for i in range(min(cnt.value, cap))]
+                 "ms": buf[i].ms, "param": buf[i].param, "side": buf[i].side}
+                for i in range(min(cnt.value, cap))]
 
     def plan_stats(self):
         a, b = ctypes.c_int64(0), ctypes.c_int64(0)
@@ -301,6 +307,23 @@ class SelInv:
         self._check(self._lib.pselinv_tune_records(self._h, buf, cnt.value, ctypes.byref(cnt)),
                     "pselinv_tune_records")
         return [buf[i] for i in range(cnt.value)]
+
+    def plan_get(self, precision=PREC_FP64):
+        """Tuned launch shapes as a list of (level, slot, value) triples."""
+        cnt = ctypes.c_int64(0)
+        self._check(self._lib.pselinv_plan_get(self._h, int(precision), None, 0, ctypes.byref(cnt)),
+                    "pselinv_plan_get")
+        buf = (ctypes.c_int32 * max(3, 3 * cnt.value))()
+        self._check(self._lib.pselinv_plan_get(self._h, int(precision), buf, cnt.value,
+                                               ctypes.byref(cnt)), "pselinv_plan_get")
+        return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(cnt.value)]
+
+    def plan_set(self, triples, precision=PREC_FP64):
+        """Replace the tuned launch shapes (triples from plan_get)."""
+        flat = [int(v) for t in triples for v in t]
+        buf = (ctypes.c_int32 * max(3, len(flat)))(*flat)
+        self._check(self._lib.pselinv_plan_set(self._h, int(precision), buf, len(flat) // 3),
+                    "pselinv_plan_set")
 
     def sync(self, stream=None):
         self._check(self._lib.pselinv_sync(self._h, _stream(stream)), "pselinv_sync")

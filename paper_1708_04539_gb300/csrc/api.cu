@@ -1214,6 +1214,8 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
     out[i].flops = s.flops;
     out[i].bytes = (double)s.bytes;
     out[i].ms = ms;
+    out[i].param = (s.kind == ST_GEMM || s.kind == ST_OZGEMM) ? s.param : -1;
+    out[i].side = s.side ? 1 : 0;
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (which == 0) h->inverted = true;
@@ -1224,9 +1226,14 @@ int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_
   if (!h) return PSELINV_ERR_ARG;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
   const Plan& sp = h->selinv_plan[h->last_precision][sched];
-  if (launches_selinv) *launches_selinv = sp.built ? (int64_t)sp.steps.size() : 0;
-  if (launches_factor)
-    *launches_factor = h->factor_plan.built ? (int64_t)h->factor_plan.steps.size() : 0;
+  auto kernels = [](const Plan& P) -> int64_t {
+    if (!P.built) return 0;
+    int64_t n = 0;
+    for (const Step& s : P.steps) n += s.kind != ST_MEMSET;
+    return n;
+  };
+  if (launches_selinv) *launches_selinv = kernels(sp);
+  if (launches_factor) *launches_factor = kernels(h->factor_plan);
   return PSELINV_OK;
 }
 
@@ -1454,6 +1461,52 @@ int pselinv_wait_selftest(void* stream, int64_t budget_us) {
     return cuda_status(e);
   }
   return herr[0] == DEV_TIMEOUT ? PSELINV_ERR_TIMEOUT : PSELINV_OK;
+}
+
+int pselinv_plan_get(pselinv_t h, int precision, int32_t* out, int64_t cap, int64_t* count) {
+  if (!h || !count || (cap > 0 && !out) ||
+      (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16))
+    return PSELINV_ERR_ARG;
+  int64_t n = 0;
+  for (const auto& kv : h->tuned) {
+    if (std::get<0>(kv.first) != precision) continue;
+    if (n < cap) {
+      out[3 * n] = std::get<1>(kv.first);
+      out[3 * n + 1] = std::get<2>(kv.first);
+      out[3 * n + 2] = kv.second;
+    }
+    n++;
+  }
+  *count = n;
+  return PSELINV_OK;
+}
+
+int pselinv_plan_set(pselinv_t h, int precision, const int32_t* in, int64_t count) {
+  if (!h || count < 0 || (count > 0 && !in) ||
+      (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16))
+    return PSELINV_ERR_ARG;
+  const int nlev = h->H.level_ptr.empty() ? 0 : (int)h->H.level_ptr.size() - 1;
+  std::vector<std::pair<std::tuple<int, int, int>, int>> entries;
+  for (int64_t i = 0; i < count; i++) {
+    const int lev = in[3 * i], slot = in[3 * i + 1], v = in[3 * i + 2];
+    bool ok = lev >= 0 && lev < nlev && slot >= 0 && slot <= 5;
+    if (ok && precision == PSELINV_PREC_FP64) ok = slot <= 2 && v >= 0 && v <= 2;
+    if (ok && precision == PSELINV_PREC_OZAKI_FP16) {
+      if (slot == 1 || slot == 2)
+        ok = v == 1 || v == 2 || v == 4 || v == 8 || v == 16;
+      else if (slot == 3)
+        ok = v == 0 || v == 1;
+      else
+        ok = v >= 0 && v <= 2;
+    }
+    if (!ok) return PSELINV_ERR_ARG;
+    entries.push_back({std::make_tuple(precision, lev, slot), v});
+  }
+  for (auto it = h->tuned.begin(); it != h->tuned.end();)
+    it = std::get<0>(it->first) == precision ? h->tuned.erase(it) : std::next(it);
+  for (const auto& e : entries) h->tuned[e.first] = e.second;
+  for (auto& p : h->selinv_plan[precision]) p.release();
+  return PSELINV_OK;
 }
 
 int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int64_t* count) {

@@ -124,3 +124,27 @@ def test_host_only_handle_refuses_compute():
     h = ps.SelInv.from_problem(p, host_only=True)
     with pytest.raises(ps.PselinvError):
         h.factor(p.values)
+
+
+def test_plan_cache_round_trip_host_only():
+    """The tuned-plan triples set on a handle come back unchanged; a bad
+    triple is refused without touching the stored ones."""
+    p = gen.conv_diff_2d(24, seed=3)
+    h = ps.SelInv.from_problem(p, host_only=True)
+    nlev = h.structure()["nlevels"]
+    assert h.plan_get(ps.PREC_OZAKI_FP16) == []
+    triples = [(0, 0, 1), (0, 3, 1), (1, 1, 4), (1, 2, 16), (nlev - 1, 4, 2), (nlev - 1, 5, 0)]
+    h.plan_set(triples, ps.PREC_OZAKI_FP16)
+    assert h.plan_get(ps.PREC_OZAKI_FP16) == sorted(triples)
+    assert h.plan_get(ps.PREC_FP64) == []
+    for bad in [(nlev, 0, 0), (-1, 0, 0), (0, 6, 0), (0, 1, 3), (0, 3, 2), (0, 4, 3)]:
+        with pytest.raises(ps.PselinvError):
+            h.plan_set(triples + [bad], ps.PREC_OZAKI_FP16)
+        assert h.plan_get(ps.PREC_OZAKI_FP16) == sorted(triples)
+    with pytest.raises(ps.PselinvError):
+        h.plan_set([(0, 3, 0)], ps.PREC_FP64)  # no precision slot in the FP64 plan
+    h.plan_set([(0, 1, 2)], ps.PREC_FP64)
+    assert h.plan_get(ps.PREC_FP64) == [(0, 1, 2)]
+    h.plan_set([], ps.PREC_OZAKI_FP16)
+    assert h.plan_get(ps.PREC_OZAKI_FP16) == []
+    assert h.plan_get(ps.PREC_FP64) == [(0, 1, 2)]

@@ -83,6 +83,33 @@ def test_exhaustive_tuning_keeps_results(torch):
     h.close()
 
 
+def test_replayed_plan_matches_tuned_plan(torch):
+    """A tuned plan exported with plan_get and loaded into a second handle
+    gives the same launch shapes and the same selected inverse."""
+    import paper_1708_04539_gb300 as ps
+    p = gen.upwind_3d(14, 72, max_sn=128)
+    vals = torch.from_numpy(p.values).cuda()
+    h1, h2 = ps.SelInv.from_problem(p), ps.SelInv.from_problem(p)
+    h1.factor(vals)
+    h2.factor(vals)
+    for prec in (ps.PREC_FP64, ps.PREC_OZAKI_FP16):
+        h1.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE)
+        triples = h1.plan_get(prec)
+        assert triples
+        h2.plan_set(triples, prec)
+        assert h2.plan_get(prec) == triples
+        h1.selinv(precision=prec)
+        h2.selinv(precision=prec)
+        s1 = [(r["kind"], r["level"], r["tasks"]) for r in h1.profile(0)]
+        s2 = [(r["kind"], r["level"], r["tasks"]) for r in h2.profile(0)]
+        assert s1 == s2
+        a = h1.get_selected()
+        b = h2.get_selected()
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a))
+    h1.close()
+    h2.close()
+
+
 def plan_ms(h, prec, reps=3):
     best = 1e30
     for _ in range(reps):
