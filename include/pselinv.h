@@ -170,8 +170,10 @@ typedef struct pselinv_step_stat {
   double bytes;   /* algorithmic bytes moved (operands read + results written) */
   double ms;      /* device time from CUDA events around the launch */
   int32_t param;  /* GEMM: tile config (0 64x64, 1 32x32, 2 128x64); OZAKI_GEMM: K split;
+                     TRI_INV: 0 wide blocks (a warp per column), 1 blocks <= 32 wide;
                      else -1 */
-  int32_t side;   /* 1 if issued on the side stream (overlapped normalisation), else 0 */
+  int32_t side;   /* stream of the launch in a sweep: 0 main, 1 normalisation side stream,
+                     2 third stream (triangular inverses of the deeper levels) */
 } pselinv_step_stat;
 
 enum pselinv_step_kind {

@@ -65,12 +65,15 @@ struct Step {
   double flops = 0;                       // useful flops of a GEMM step
   int level = -1;
   int slot = -1;      // tunable step: 0 normalisation, 1 steps 3+5, 2 step 4
-  int side = 0;       // 1: issued on the side stream (normalisation, one level ahead)
+  int side = 0;       // 1: side stream (normalisation, one level ahead); 2: third stream
   int wait = -1;      // event index waited on before the launch
   int signal = -1;    // event index recorded after the launch
   int param = 0;      // tuned parameter in use (GEMM tile config or K split)
   float feat[8] = {}; // shape features of the step (cost model input)
 };
+
+// events of a multi-stream plan
+enum PlanEvent { EV_FORK = 0, EV_SIDE_JOIN = 1, EV_THIRD_JOIN = 2, EV_THIRD_DONE = 3, EV_LEVEL = 4 };
 
 struct Plan {
   std::vector<Step> steps;
@@ -80,7 +83,7 @@ struct Plan {
   cudaGraphExec_t exec = nullptr;
   bool built = false;
   bool two_streams = false;
-  std::vector<cudaEvent_t> ev;  // [0] fork, [1] join, [2 + d] level d normalised
+  std::vector<cudaEvent_t> ev;  // PlanEvent; EV_LEVEL + d: level d normalised
 
   template <class T>
   size_t push(const std::vector<T>& v) {
@@ -137,6 +140,7 @@ struct pselinv_ctx {
   std::vector<pselinv_tune_record> records;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t side_stream = nullptr;
+  cudaStream_t third_stream = nullptr;
   int64_t last_info = -1;
   int last_status = 0;
 };
@@ -300,10 +304,28 @@ size_t ozaki_level_bytes(const HostSym& H, int64_t nb, int S, size_t es) {
   return mx;
 }
 
-// scratch needed (bytes) by the factor and selected-inversion plans
-size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
-  // selinv: W (2 s^2 for every supernode) + the largest level's G (c^2)
-  int64_t w = 0, gmax = 0, fmax = 0;
+// bytes of the split normalisation of the largest level
+size_t ozaki_norm_bytes(const HostSym& H, int64_t nb, int S, size_t es) {
+  const size_t parts = es / 8;
+  size_t mx = 0;
+  for (size_t d = 0; d + 1 < H.level_ptr.size(); d++) {
+    size_t b = 512;
+    for (int64_t i = H.level_ptr[d]; i < H.level_ptr[d + 1]; i++) {
+      const int64_t K = H.level_sn[i], s = H.sn_width[K], c = cK(H, K);
+      if (c == 0) continue;
+      b += 2 * (parts * slice_bytes(c, s, S) + exps_bytes(c) + 512) +
+           2 * (parts * slice_bytes(s, s, S) + exps_bytes(s) + 512) + (size_t)(2 * c + 2 * s) * 8;
+    }
+    mx = std::max(mx, b * (size_t)nb + 512);
+  }
+  return mx;
+}
+
+// scratch of the selected-inversion sweep before the normalisation region:
+// W (2 s^2 for every supernode) and the largest level's G (FP64 levels) or
+// split-level operands
+size_t selinv_main_bytes(const HostSym& H, int64_t nb, size_t es) {
+  int64_t w = 0, gmax = 0;
   for (int64_t k = 0; k < H.ns; k++) w += 2 * H.sn_width[k] * H.sn_width[k];
   for (size_t d = 0; d + 1 < H.level_ptr.size(); d++) {
     int64_t g = 0;
@@ -313,6 +335,14 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
     }
     gmax = std::max(gmax, g);
   }
+  return align256(std::max((size_t)((w + gmax) * nb) * es + 256,
+                           (size_t)(w * nb) * es + ozaki_level_bytes(H, nb, 6, es) + 4096));
+}
+
+// scratch needed (bytes) by the factor and selected-inversion plans; the
+// split normalisation (side stream) has its own region after the sweep's
+size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
+  int64_t fmax = 0;
   for (size_t d = 0; d + 1 < H.hlevel_ptr.size(); d++) {
     int64_t f = 0;
     for (int64_t i = H.hlevel_ptr[d]; i < H.hlevel_ptr[d + 1]; i++) {
@@ -321,10 +351,8 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
     }
     fmax = std::max(fmax, f);
   }
-  const int64_t sel = w + gmax;
-  size_t bytes = (size_t)(std::max(sel, fmax) * nb) * es + 256;
-  bytes = std::max(bytes, (size_t)(w * nb) * es + ozaki_level_bytes(H, nb, 6, es) + 4096);
-  return bytes;
+  return std::max((size_t)(fmax * nb) * es + 256,
+                  selinv_main_bytes(H, nb, es) + ozaki_norm_bytes(H, nb, 6, es));
 }
 
 int choose_cfg(int dtype) { return dtype == DT_F64 ? GEMM_64x64 : GEMM_64x64; }
@@ -370,6 +398,46 @@ void gemm_features<GemmDesc>(Step& st, const std::vector<GemmDesc>& descs, doubl
   for (int i = 0; i < 8; i++) st.feat[i] = (float)std::log2(1.0 + v[i]);
 }
 
+// Triangular-inverse launches over blocks {instance, supernode, W offset}:
+// blocks of width <= 32 one warp per triangle (cfg 1), wider ones in panels
+// of 8 columns, one warp per column (cfg 0).
+struct TriBlock {
+  int64_t b, K, w0;
+};
+void add_tri_step(Plan& P, const HostSym& H, const std::vector<TriBlock>& blocks, int level,
+                  int stream) {
+  std::vector<SnTask> wide, small;
+  std::vector<int64_t> wofs_wide, wofs_small;
+  for (const TriBlock& t : blocks) {
+    const int64_t s = H.sn_width[t.K];
+    for (int which = 0; which < 2; which++) {
+      if (s <= 32) {
+        small.push_back({(int)t.b, (int)t.K, which, 0});
+        wofs_small.push_back(t.w0 + which * s * s);
+        continue;
+      }
+      for (int64_t j = 0; j < s; j += 8) {
+        wide.push_back({(int)t.b, (int)t.K, which, (int)j});
+        wofs_wide.push_back(t.w0 + which * s * s);
+      }
+    }
+  }
+  auto push = [&](const std::vector<SnTask>& tasks, const std::vector<int64_t>& wofs, int cfg) {
+    if (tasks.empty()) return;
+    Step st;
+    st.kind = ST_TRI_INV;
+    st.cfg = cfg;
+    st.n = (int)tasks.size();
+    st.tasks = P.push(tasks);
+    st.offs = P.push(wofs);
+    st.level = level;
+    st.side = stream;
+    P.steps.push_back(st);
+  };
+  push(wide, wofs_wide, 0);
+  push(small, wofs_small, 1);
+}
+
 // ---------------------------------------------------------------------------
 // factor plan: scatter A, then per height level (leaves first):
 //   diagonal LU, triangular inverses, L = A_{C,K} U_KK^{-1},
@@ -393,8 +461,9 @@ int build_factor_plan(pselinv_ctx* h) {
   P.steps.push_back(sv);
   const int cfg = choose_cfg(dt);
   for (size_t lev = 0; lev + 1 < H.hlevel_ptr.size(); lev++) {
-    std::vector<SnTask> diag, tri, gt;
-    std::vector<int64_t> wofs, gofs;
+    std::vector<SnTask> diag, gt;
+    std::vector<TriBlock> tri;
+    std::vector<int64_t> gofs;
     std::vector<GemmDesc> trsm, schur;
     std::vector<CopySeg> segs;
     int64_t off = 0;  // scalars into scratch
@@ -405,11 +474,7 @@ int build_factor_plan(pselinv_ctx* h) {
         off = s0 + c * c;
         diag.push_back({(int)b, (int)K, 0, 0});
         if (c == 0) continue;
-        for (int which = 0; which < 2; which++)
-          for (int64_t j = 0; j < s; j += 32) {
-            tri.push_back({(int)b, (int)K, which, (int)j});
-            wofs.push_back(w0 + which * s * s);
-          }
+        tri.push_back({b, K, w0});
         char* base = h->lu + ((size_t)b * H.storage + H.sn_offset[K]) * es;
         char* Lp = base + (size_t)s * s * es;
         char* Up = Lp + (size_t)c * s * es;
@@ -437,15 +502,7 @@ int build_factor_plan(pselinv_ctx* h) {
     d.tasks = P.push(diag);
     d.level = (int)lev;
     P.steps.push_back(d);
-    if (!tri.empty()) {
-      Step t;
-      t.kind = ST_TRI_INV;
-      t.n = (int)tri.size();
-      t.tasks = P.push(tri);
-      t.offs = P.push(wofs);
-      t.level = (int)lev;
-      P.steps.push_back(t);
-    }
+    add_tri_step(P, H, tri, (int)lev, 0);
     add_gemm_step(P, dt, cfg, trsm, (int)lev);
     add_gemm_step(P, dt, cfg, schur, (int)lev);
     if (!gt.empty()) {
@@ -561,39 +618,24 @@ void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool
   P.steps.push_back(st);
 }
 
-// One level (or one supernode) of the split-precision sweep: gather G,
-// slice G (by rows and by columns), Lhat and Uhat^T, sliced products for
-// steps 3 and 5, slice Ainv(C,K), sliced product for step 4 accumulated onto
-// D_K.  Scratch layout after the W region (byte offsets).
-void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, int64_t nb,
-                     int64_t gbase_scalars, int lev) {
-  const HostSym& H = h->H;
-  const int S = h->slices;
-  const size_t es = h->esize;
-  const int cplx = h->dtype == PSELINV_C128 ? 1 : 0;
-  std::vector<SnTask> gt;
-  std::vector<int64_t> gofs, mofs;
-  std::vector<SliceDesc> sl1, sl2, mx1;
-  std::vector<OzDesc> main, dg;
-  std::vector<CopySeg> zero;
-  size_t off = (size_t)gbase_scalars * es;
-  auto take = [&](size_t bytes) {
+// Scratch carving and descriptor helpers of the split-precision steps.
+struct OzBuilder {
+  pselinv_ctx* h;
+  size_t off;  // next free byte of the scratch arena
+  int S, cplx;
+  OzBuilder(pselinv_ctx* h_, size_t off_)
+      : h(h_), off(off_), S(h_->slices), cplx(h_->dtype == PSELINV_C128 ? 1 : 0) {}
+  char* take(size_t bytes) {
     off = align256(off);
     const size_t o = off;
     off += bytes;
     return h->scratch + o;
-  };
-  // row and column maxima of every G and panel of the level, zeroed by one memset
-  int64_t nmax = 0;
-  for (int64_t b = 0; b < nb; b++)
-    for (int64_t K : grp)
-      if (H.rows_ptr[K + 1] > H.rows_ptr[K])
-        nmax += 2 * (H.rows_ptr[K + 1] - H.rows_ptr[K]) + 3 * H.sn_width[K];
-  unsigned long long* maxbase = (unsigned long long*)take(align256((size_t)nmax * 8 + 8));
-  int64_t moff = 0;
-  auto slice_desc = [&](const double* src, int ld, int mode, int R, int Kd) {
+  }
+  // slice set of the R x Kd operand X: X(r, k) = src[r + k ld] (SLICE_ROWS)
+  // or src[k + r ld] (SLICE_COLS)
+  SliceDesc slice(const void* src, int ld, int mode, int R, int Kd) {
     SliceDesc d;
-    d.src = src;
+    d.src = (const double*)src;
     d.ld = ld;
     d.mode = mode;
     d.R = R;
@@ -606,12 +648,12 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
     d.exps = (int*)take(exps_bytes(R));
     d.maxbits = nullptr;
     return d;
-  };
-  // one product (real) or two (real and imaginary parts) for C = -A B
-  auto push_product = [&](std::vector<OzDesc>& out, const SliceDesc& a, const SliceDesc& b,
-                          char* C, int ldc, int M, int N) {
+  }
+  // one product (real) or two (real and imaginary parts) for C = alpha A B
+  void product(std::vector<OzDesc>& out, const SliceDesc& a, const SliceDesc& b, char* C,
+               int ldc, int M, int N, double alpha) const {
     OzDesc d{};
-    d.alpha = -1.0;
+    d.alpha = alpha;
     d.A = a.out; d.eA = a.exps; d.A_R64 = a.R64;
     d.B = b.out; d.eB = b.exps; d.B_R64 = b.R64;
     d.C = (double*)C; d.ldc = ldc; d.M = M; d.N = N;
@@ -629,6 +671,99 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
     d.swap_b = 1;
     d.coff = 1;
     out.push_back(d);
+  }
+};
+
+// Split-precision normalisation of one depth level (Algorithm 1 step 2):
+// Lhat = L_{C,K} Linv and Uhat^T = U_{K,C}^T Uinv^T as sliced products (K =
+// s), after the maxima and slicing passes of the four operands.  Linv and
+// Uinv hold exact zeros outside their triangles, so the full products are
+// the triangular ones.  Steps go to the side stream; scratch from `base`.
+void add_ozaki_normalize(pselinv_ctx* h, Plan& P, int lev, int64_t nb,
+                         const std::vector<int64_t>& wbase, size_t base) {
+  const HostSym& H = h->H;
+  const size_t es = h->esize;
+  OzBuilder ob(h, base);
+  int64_t nmax = 0;
+  for (int64_t b = 0; b < nb; b++)
+    for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
+      const int64_t K = H.level_sn[i];
+      if (cK(H, K) > 0) nmax += 2 * cK(H, K) + 2 * H.sn_width[K];
+    }
+  if (nmax == 0) return;
+  unsigned long long* maxbase = (unsigned long long*)ob.take(align256((size_t)nmax * 8 + 8));
+  std::vector<SliceDesc> sl;
+  std::vector<OzDesc> prods;
+  int64_t moff = 0;
+  for (int64_t b = 0; b < nb; b++)
+    for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
+      const int64_t K = H.level_sn[i];
+      const int s = (int)H.sn_width[K], c = (int)cK(H, K);
+      if (c == 0) continue;
+      const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
+      const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
+      const char* Linv = h->scratch + (size_t)wbase[b * H.ns + K] * es;
+      const char* Uinv = Linv + (size_t)s * s * es;
+      SliceDesc la = ob.slice(h->lu + lo, c, SLICE_ROWS, c, s);  // L_{C,K}(m, k)
+      SliceDesc ua = ob.slice(h->lu + uo, c, SLICE_ROWS, c, s);  // U_{K,C}^T(m, k)
+      SliceDesc lb = ob.slice(Linv, s, SLICE_COLS, s, s);        // Linv(k, n)
+      SliceDesc ub = ob.slice(Uinv, s, SLICE_ROWS, s, s);        // Uinv(n, k)
+      la.maxbits = maxbase + moff;
+      ua.maxbits = maxbase + moff + c;
+      lb.maxbits = maxbase + moff + 2 * c;
+      ub.maxbits = maxbase + moff + 2 * c + s;
+      moff += 2 * c + 2 * s;
+      sl.push_back(la);
+      sl.push_back(ua);
+      sl.push_back(lb);
+      sl.push_back(ub);
+      ob.product(prods, la, lb, h->nf + lo, c, c, s, 1.0);
+      ob.product(prods, ua, ub, h->nf + uo, c, c, s, 1.0);
+    }
+  const size_t first = P.steps.size();
+  Step ms;
+  ms.kind = ST_MEMSET;
+  ms.ptr = maxbase;
+  ms.bytes = (size_t)nmax * 8;
+  ms.level = lev;
+  P.steps.push_back(ms);
+  add_slice_step(P, sl, lev, true);
+  add_slice_step(P, sl, lev, false);
+  add_ozgemm_step(P, prods, h->slices, lev, false, 1, -1);
+  for (size_t i = first; i < P.steps.size(); i++) P.steps[i].side = 1;
+}
+
+// One level (or one supernode) of the split-precision sweep: gather G,
+// slice G (by rows and by columns), Lhat and Uhat^T, sliced products for
+// steps 3 and 5, slice Ainv(C,K), sliced product for step 4 accumulated onto
+// D_K.  Scratch layout after the W region (byte offsets).
+void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, int64_t nb,
+                     int64_t gbase_scalars, int lev) {
+  const HostSym& H = h->H;
+  const int S = h->slices;
+  const size_t es = h->esize;
+  const int cplx = h->dtype == PSELINV_C128 ? 1 : 0;
+  std::vector<SnTask> gt;
+  std::vector<int64_t> gofs, mofs;
+  std::vector<SliceDesc> sl1, sl2, mx1;
+  std::vector<OzDesc> main, dg;
+  std::vector<CopySeg> zero;
+  OzBuilder ob(h, (size_t)gbase_scalars * es);
+  auto take = [&](size_t bytes) { return ob.take(bytes); };
+  // row and column maxima of every G and panel of the level, zeroed by one memset
+  int64_t nmax = 0;
+  for (int64_t b = 0; b < nb; b++)
+    for (int64_t K : grp)
+      if (H.rows_ptr[K + 1] > H.rows_ptr[K])
+        nmax += 2 * (H.rows_ptr[K + 1] - H.rows_ptr[K]) + 3 * H.sn_width[K];
+  unsigned long long* maxbase = (unsigned long long*)take(align256((size_t)nmax * 8 + 8));
+  int64_t moff = 0;
+  auto slice_desc = [&](const double* src, int ld, int mode, int R, int Kd) {
+    return ob.slice(src, ld, mode, R, Kd);
+  };
+  auto push_product = [&](std::vector<OzDesc>& out, const SliceDesc& a, const SliceDesc& b,
+                          char* C, int ldc, int M, int N) {
+    ob.product(out, a, b, C, ldc, M, N, -1.0);
   };
   for (int64_t b = 0; b < nb; b++)
     for (int64_t K : grp) {
@@ -721,32 +856,39 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       off += 2 * H.sn_width[K] * H.sn_width[K];
     }
   const int64_t gbase = off;
-  // Normalisation (Algorithm 1 step 2 and D_K) on the side stream: the
-  // triangular inverses of every diagonal block in one launch, then one
-  // product launch per depth level, one level ahead of the sweep, so that its
-  // FP64 work overlaps the previous level's products.
+  // Normalisation (Algorithm 1 step 2 and D_K) on the side stream, one
+  // depth level ahead of the sweep so that it overlaps the previous level's
+  // products.  Triangular inverses first: the blocks of the levels nearest
+  // the roots (needed first, few and wide) in one launch on the side
+  // stream, the rest in one launch on a third stream that runs beside the
+  // first levels; the first normalisation that needs it waits for it.
+  const int nlev = (int)H.level_ptr.size() - 1;
+  int lev_a = -1;
   {
-    std::vector<SnTask> tri;
-    std::vector<int64_t> wofs;
+    int64_t tasks = 0;
+    for (int l = 0; l < nlev; l++) {
+      int64_t t = 0;
+      for (int64_t i = H.level_ptr[l]; i < H.level_ptr[l + 1]; i++)
+        t += 2 * ((H.sn_width[H.level_sn[i]] + 7) / 8);
+      if (l > 0 && tasks + t * nb > 4 * 152) break;
+      tasks += t * nb;
+      lev_a = l;
+    }
+    std::vector<TriBlock> ta, tb;
     for (int64_t b = 0; b < nb; b++)
-      for (size_t i = 0; i < H.level_sn.size(); i++) {  // roots first
-        const int64_t K = H.level_sn[i];
-        const int64_t s = H.sn_width[K], w0 = wbase[b * H.ns + K];
-        for (int which = 0; which < 2; which++)
-          for (int64_t j = 0; j < s; j += 32) {
-            tri.push_back({(int)b, (int)K, which, (int)j});
-            wofs.push_back(w0 + which * s * s);
-          }
-      }
-    Step t;
-    t.kind = ST_TRI_INV;
-    t.n = (int)tri.size();
-    t.tasks = P.push(tri);
-    t.offs = P.push(wofs);
-    t.side = 1;
-    P.steps.push_back(t);
+      for (int l = 0; l < nlev; l++)
+        for (int64_t i = H.level_ptr[l]; i < H.level_ptr[l + 1]; i++) {
+          const int64_t K = H.level_sn[i];
+          (l <= lev_a ? ta : tb).push_back({b, K, wbase[b * H.ns + K]});
+        }
+    add_tri_step(P, H, ta, -1, 1);
+    add_tri_step(P, H, tb, -1, 2);
+    if (!tb.empty()) P.steps.back().signal = EV_THIRD_DONE;
   }
-  auto add_normalize = [&](int lev) {
+  const size_t norm_base = selinv_main_bytes(H, nb, es);
+  bool third_waited = false;
+  // split = true: Lhat and Uhat^T as sliced products (D_K stays FP64)
+  auto add_normalize = [&](int lev, bool split) {
     std::vector<GemmDesc> norm;
     for (int64_t b = 0; b < nb; b++)
       for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
@@ -758,7 +900,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
         // D_K = Uinv Linv (upper x lower), Lhat = L Linv, Uhat^T = U^T Uinv^T (lower B)
         norm.push_back(make_desc(Uinv, Linv, h->ainv + so, s, s, s, s, s, s, 0, 0, 1.0, 0.0, 0, 1,
                                  GEMM_TRI_UPPER_A | GEMM_TRI_LOWER_B));
-        if (c > 0) {
+        if (c > 0 && !split) {
           const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
           norm.push_back(make_desc(h->lu + lo, Linv, h->nf + lo, c, s, s, c, s, c, 0, 0, 1.0, 0.0,
                                    0, 1, GEMM_TRI_LOWER_B));
@@ -766,29 +908,24 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
                                    0, 1, GEMM_TRI_LOWER_B));
         }
       }
+    const size_t first = P.steps.size();
     add_gemm_step(P, dt, tuned_value(h, precision, lev, 0, cfg), norm, lev, 0);
-    P.steps.back().side = 1;
-    P.steps.back().signal = 2 + lev;
+    if (split) add_ozaki_normalize(h, P, lev, nb, wbase, norm_base);
+    for (size_t i = first; i < P.steps.size(); i++) P.steps[i].side = 1;
+    if (P.steps.size() > first) {
+      if (lev > lev_a && !third_waited) P.steps[first].wait = EV_THIRD_DONE;
+      third_waited = third_waited || lev > lev_a;
+      P.steps.back().signal = EV_LEVEL + lev;
+    }
   };
-  const int nlev = (int)H.level_ptr.size() - 1;
   P.two_streams = true;
-  P.ev.assign(2 + std::max(nlev, 0), nullptr);
+  P.ev.assign(EV_LEVEL + std::max(nlev, 0), nullptr);
   for (auto& e : P.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (size_t lev = 0; lev + 1 < H.level_ptr.size(); lev++) {
-    add_normalize((int)lev);
-    const size_t first_main = P.steps.size();
-    // groups: the whole level, or one supernode at a time
-    std::vector<std::vector<int64_t>> groups;
-    if (schedule == PSELINV_SCHED_LEVEL) {
-      groups.emplace_back(H.level_sn.begin() + H.level_ptr[lev],
-                          H.level_sn.begin() + H.level_ptr[lev + 1]);
-    } else {
-      for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++)
-        groups.push_back({H.level_sn[i]});
-    }
     // split precision: each level runs either the sliced tensor-core products
-    // or (for levels whose products are too small to pay for the slicing) the
-    // FP64 ones; the default is a flop threshold, the tuner times both
+    // (normalisation included) or, for levels whose products are too small
+    // to pay for the slicing, the FP64 ones; the default is a flop
+    // threshold, the tuner times both
     int mode = 0;
     if (precision == PSELINV_PREC_OZAKI_FP16) {
       double lf = 0;
@@ -799,10 +936,22 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       lf *= (double)nb * (dt == DT_F64 ? 1.0 : 4.0);
       mode = tuned_value(h, precision, (int)lev, 3, lf < 2e8 ? 1 : 0);
     }
+    const bool split_level = precision == PSELINV_PREC_OZAKI_FP16 && mode == 0;
+    add_normalize((int)lev, split_level);
+    const size_t first_main = P.steps.size();
+    // groups: the whole level, or one supernode at a time
+    std::vector<std::vector<int64_t>> groups;
+    if (schedule == PSELINV_SCHED_LEVEL) {
+      groups.emplace_back(H.level_sn.begin() + H.level_ptr[lev],
+                          H.level_sn.begin() + H.level_ptr[lev + 1]);
+    } else {
+      for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++)
+        groups.push_back({H.level_sn[i]});
+    }
     const int slot_main = precision == PSELINV_PREC_OZAKI_FP16 ? 4 : 1;
     const int slot_diag = precision == PSELINV_PREC_OZAKI_FP16 ? 5 : 2;
     for (const auto& grp : groups) {
-      if (precision == PSELINV_PREC_OZAKI_FP16 && mode == 0) {
+      if (split_level) {
         add_ozaki_level(h, P, grp, nb, gbase, (int)lev);
         continue;
       }
@@ -844,7 +993,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_diag, cfg), dg, (int)lev,
                     slot_diag);
     }
-    if (P.steps.size() > first_main) P.steps[first_main].wait = 2 + (int)lev;
+    if (P.steps.size() > first_main) P.steps[first_main].wait = EV_LEVEL + (int)lev;
   }
   CK(cudaMalloc(&P.arena, P.host.size() + 256));
   CK(cudaMemcpy(P.arena, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
@@ -861,7 +1010,7 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       break;
     case ST_TRI_INV:
       launch_tri_inv(h->dtype, h->S, h->lu, h->scratch, (const int64_t*)(a + s.offs),
-                     (const SnTask*)(a + s.tasks), s.n, h->max_width, st);
+                     (const SnTask*)(a + s.tasks), s.n, h->max_width, s.cfg, st);
       break;
     case ST_DIAG_LU:
       launch_diag_lu(h->dtype, h->S, h->lu, (const SnTask*)(a + s.tasks), s.n, st);
@@ -913,17 +1062,25 @@ int run_steps(pselinv_ctx* h, Plan& P, cudaStream_t st) {
     CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     CK(cudaStreamCreateWithPriority(&h->side_stream, cudaStreamNonBlocking, lo));
   }
-  cudaStream_t side = h->side_stream;
-  CK(cudaEventRecord(P.ev[0], st));
-  CK(cudaStreamWaitEvent(side, P.ev[0], 0));
+  if (!h->third_stream) {
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(cudaStreamCreateWithPriority(&h->third_stream, cudaStreamNonBlocking, lo));
+  }
+  cudaStream_t side = h->side_stream, third = h->third_stream;
+  CK(cudaEventRecord(P.ev[EV_FORK], st));
+  CK(cudaStreamWaitEvent(side, P.ev[EV_FORK], 0));
+  CK(cudaStreamWaitEvent(third, P.ev[EV_FORK], 0));
   for (const Step& s : P.steps) {
-    cudaStream_t q = s.side ? side : st;
+    cudaStream_t q = s.side == 1 ? side : s.side == 2 ? third : st;
     if (s.wait >= 0) CK(cudaStreamWaitEvent(q, P.ev[s.wait], 0));
     launch_step(h, P, s, q);
     if (s.signal >= 0) CK(cudaEventRecord(P.ev[s.signal], q));
   }
-  CK(cudaEventRecord(P.ev[1], side));
-  CK(cudaStreamWaitEvent(st, P.ev[1], 0));
+  CK(cudaEventRecord(P.ev[EV_SIDE_JOIN], side));
+  CK(cudaEventRecord(P.ev[EV_THIRD_JOIN], third));
+  CK(cudaStreamWaitEvent(st, P.ev[EV_SIDE_JOIN], 0));
+  CK(cudaStreamWaitEvent(st, P.ev[EV_THIRD_JOIN], 0));
   CK(cudaGetLastError());
   return PSELINV_OK;
 }
@@ -1214,8 +1371,10 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
     out[i].flops = s.flops;
     out[i].bytes = (double)s.bytes;
     out[i].ms = ms;
-    out[i].param = (s.kind == ST_GEMM || s.kind == ST_OZGEMM) ? s.param : -1;
-    out[i].side = s.side ? 1 : 0;
+    out[i].param = (s.kind == ST_GEMM || s.kind == ST_OZGEMM) ? s.param
+                   : s.kind == ST_TRI_INV                  ? s.cfg
+                                                           : -1;
+    out[i].side = s.side;
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (which == 0) h->inverted = true;
@@ -1321,7 +1480,7 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
       }
     }
   std::map<std::tuple<int, int, int, int>, double> best_ms;  // (level, slot, kind, value) -> ms
-  std::map<std::pair<int, int>, double> level_ms;             // (level, mode) -> main-stream ms
+  std::map<std::pair<int, int>, double> level_ms;  // (level, mode) -> ms of its launches
   std::vector<pselinv_step_stat> stats;
   auto measure = [&](int mode_tag) -> int {
     int r = rebuild();
@@ -1345,7 +1504,7 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
       std::map<int, double> lev_acc;
       for (size_t i = 0; i < P.steps.size(); i++) {
         const Step& s = P.steps[i];
-        if (!s.side && s.level >= 0) lev_acc[s.level] += stats[i].ms;
+        if (s.level >= 0) lev_acc[s.level] += stats[i].ms;
         if (s.slot < 0) continue;
         acc[std::make_tuple(s.level, s.slot, (int)s.kind, s.param)] += stats[i].ms;
       }
@@ -1531,6 +1690,7 @@ void pselinv_free(pselinv_t h) {
     free_numeric(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->side_stream) cudaStreamDestroy(h->side_stream);
+    if (h->third_stream) cudaStreamDestroy(h->third_stream);
     cudaFree(h->dsym);
     cudaFree(h->derr);
   }

@@ -216,11 +216,12 @@ void launch_scatter_values(int dtype, const SymDev& S, const void* values, void*
 void launch_diag_lu(int dtype, const SymDev& S, void* store, const SnTask* tasks, int ntasks,
                     cudaStream_t st);
 // triangular inverses of the diagonal blocks of `store`:
-// tasks {inst, K, which (0 = L unit lower, 1 = U upper), first column};
-// result (s x s) at out + wofs[task index]
+// tasks {inst, K, which (0 = L unit lower, 1 = U upper), first column of a
+// panel of 8 columns}; small = 1: blocks of width <= 32, one task per
+// triangle (first column 0); result (s x s) at out + wofs[task]
 void launch_tri_inv(int dtype, const SymDev& S, const void* store, void* out,
                     const int64_t* wofs, const SnTask* tasks, int ntasks, int max_width,
-                    cudaStream_t st);
+                    int small, cudaStream_t st);
 // one-time kernel attributes (dynamic shared memory of tri_inv for max_width)
 cudaError_t prepare_dense_kernels(int dtype, int max_width);
 // G_K = Ainv(R_K, R_K) gathered from `store` into out + gofs[task]

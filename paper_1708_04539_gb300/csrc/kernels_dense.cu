@@ -137,79 +137,163 @@ diag_lu_kernel(SymDev S, T* store, const SnTask* __restrict__ tasks, int ntasks)
   }
 }
 
-// Triangular inverses of the diagonal block: which = 0 gives (L_KK)^{-1}
-// (unit lower), which = 1 gives (U_KK)^{-1} (upper).  A task inverts a panel
-// of kTriPanel columns j0.. by substitution on all of them at once: the
-// panel X (s x kTriPanel) lives in shared memory, the triangle is streamed
-// through shared memory kTriChunk columns at a time, and the thread layout
-// (lane = panel column, warp = row group) lets every warp read one factor
-// entry per row and update 32 right-hand sides with it.
-constexpr int kTriPanel = 32;
-constexpr int kTriChunk = 8;
+// Triangular inverses of the diagonal blocks: which = 0 gives (L_KK)^{-1}
+// (unit lower), which = 1 gives (U_KK)^{-1} (upper), column j of the
+// inverse being the solution of a triangular system with right-hand side
+// e_j.  FP64 runs at about 4 flop/clk/SM on this GPU, so a launch is fast
+// only when its solves are spread over many SMs and the FP64 pipe is all a
+// solve waits on: one warp per column, the column in registers (lane l holds
+// rows l, l + 32, ...), the factor streamed through shared memory for the
+// eight columns (warps) of a CTA, and no block barrier inside a chunk.
+constexpr int kTriChunk = 8;   // factor columns staged per shared-memory pass
+constexpr int kTriRb = 8;      // 32-row blocks per column (s <= 256)
+constexpr int kTriSmallS = 32; // blocks this wide or narrower: one warp per triangle
 
+__device__ __forceinline__ double shfl_s(double v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ cdouble shfl_s(cdouble v, int src) {
+  return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+
+// s > 32: a task is a panel of 8 consecutive columns j0.. (warp w solves
+// column j0 + w); the factor goes through shared memory kTriChunk columns at
+// a time.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1)
 tri_inv_kernel(SymDev S, const T* store, T* out, const int64_t* __restrict__ wofs,
                const SnTask* __restrict__ tasks, int ntasks) {
-  extern __shared__ unsigned char smem_raw[];
-  const int c = threadIdx.x & 31, rg = threadIdx.x >> 5;  // panel column, row group (8)
+  __shared__ T F[kTriChunk][kTriRb * 32];
+  __shared__ T R[kTriChunk];  // reciprocals of the chunk's diagonal entries of U
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const SnTask task = tasks[t];
     const int K = task.K;
     const int s = S.sn_width[K];
+    const int nrb = (s + 31) >> 5;
     const int j0 = task.b;
-    const int np = min(kTriPanel, s - j0);
-    // X: s rows x (kTriPanel + 1) (padded), F: kTriChunk factor columns of s rows
-    T* X = reinterpret_cast<T*>(smem_raw);
-    T* F = X + (int64_t)s * (kTriPanel + 1);
+    const int col = j0 + w;  // >= s: idle warp (still takes part in the barriers)
     const T* D = store + (int64_t)task.inst * S.storage + S.sn_off[K];
-    T* W = out + wofs[t];
-    for (int i = rg; i < s; i += 8) X[i * (kTriPanel + 1) + c] = (i == j0 + c) ? sc_one(T()) : sc_zero(T());
-    __syncthreads();
+    T x[kTriRb];
+#pragma unroll
+    for (int m = 0; m < kTriRb; m++) x[m] = (lane + 32 * m == col) ? sc_one(T()) : sc_zero(T());
     if (task.a == 0) {
-      // L X = E: forward substitution, rows j0.. only
+      // L x = e_col, forward: rows below k take x_k once it is final
       for (int k0 = j0; k0 < s - 1; k0 += kTriChunk) {
         const int kn = min(kTriChunk, s - 1 - k0);
-        for (int e = threadIdx.x; e < kn * s; e += blockDim.x) {
-          const int kk = e / s, i = e % s;
-          F[kk * s + i] = D[i + (int64_t)(k0 + kk) * s];
+        __syncthreads();
+        for (int e = threadIdx.x; e < kn * s; e += kThreads) {
+          const int kk = e / s, i = e - kk * s;
+          F[kk][i] = D[i + (int64_t)(k0 + kk) * s];
         }
         __syncthreads();
         for (int kk = 0; kk < kn; kk++) {
-          const int k = k0 + kk;
-          const T xk = X[k * (kTriPanel + 1) + c];
-          for (int i = k + 1 + rg; i < s; i += 8)
-            X[i * (kTriPanel + 1) + c] = sub_s(X[i * (kTriPanel + 1) + c], mul_s(F[kk * s + i], xk));
-          __syncthreads();
+          const int k = k0 + kk, mk = k >> 5;
+          T v = x[0];
+#pragma unroll
+          for (int m = 1; m < kTriRb; m++)
+            if (m == mk) v = x[m];
+          const T xk = shfl_s(v, k & 31);
+#pragma unroll
+          for (int m = 0; m < kTriRb; m++) {
+            if (m >= mk && m < nrb) {
+              const int i = lane + 32 * m;
+              if (i > k && i < s) x[m] = sub_s(x[m], mul_s(F[kk][i], xk));
+            }
+          }
         }
       }
     } else {
-      // U X = E: backward substitution from row j0 + np - 1 down
-      const int kend = j0 + np - 1;
+      // U x = e_col, backward from the panel's last column
+      const int kend = min(j0 + kThreads / 32, s) - 1;
       for (int k0 = kend; k0 >= 0; k0 -= kTriChunk) {
         const int kn = min(kTriChunk, k0 + 1);
-        for (int e = threadIdx.x; e < kn * (k0 + 1); e += blockDim.x) {
-          const int kk = e / (k0 + 1), i = e % (k0 + 1);
-          F[kk * s + i] = D[i + (int64_t)(k0 - kk) * s];
+        __syncthreads();
+        for (int e = threadIdx.x; e < kn * (k0 + 1); e += kThreads) {
+          const int kk = e / (k0 + 1), i = e - kk * (k0 + 1);
+          F[kk][i] = D[i + (int64_t)(k0 - kk) * s];
+        }
+        // one division per diagonal entry and CTA: an FP64 division is a
+        // sequence of FP64 operations, too dear to repeat in every column
+        if (threadIdx.x < kn) {
+          const T u = D[(k0 - threadIdx.x) + (int64_t)(k0 - threadIdx.x) * s];
+          if (is_zero(u)) set_error(S.err, DEV_ZERO_PIVOT, S.sn_first[K] + k0 - threadIdx.x);
+          R[threadIdx.x] = div_s(sc_one(T()), u);
         }
         __syncthreads();
         for (int kk = 0; kk < kn; kk++) {
-          const int k = k0 - kk;
-          const T ukk = F[kk * s + k];
-          if (is_zero(ukk) && threadIdx.x == 0) set_error(S.err, DEV_ZERO_PIVOT, S.sn_first[K] + k);
-          const T xk = div_s(X[k * (kTriPanel + 1) + c], ukk);
-          __syncthreads();
-          if (rg == 0) X[k * (kTriPanel + 1) + c] = xk;
-          for (int i = rg; i < k; i += 8)
-            X[i * (kTriPanel + 1) + c] = sub_s(X[i * (kTriPanel + 1) + c], mul_s(F[kk * s + i], xk));
-          __syncthreads();
+          const int k = k0 - kk, mk = k >> 5;
+          T v = x[0];
+#pragma unroll
+          for (int m = 1; m < kTriRb; m++)
+            if (m == mk) v = x[m];
+          const T xk = mul_s(shfl_s(v, k & 31), R[kk]);
+#pragma unroll
+          for (int m = 0; m < kTriRb; m++) {
+            if (m <= mk) {
+              const int i = lane + 32 * m;
+              if (i == k) x[m] = xk;
+              else if (i < k) x[m] = sub_s(x[m], mul_s(F[kk][i], xk));
+            }
+          }
         }
       }
     }
-    // write the panel column-major: lanes run over rows
-    for (int q = rg; q < np; q += 8)
-      for (int i = c; i < s; i += 32) W[i + (int64_t)(j0 + q) * s] = X[i * (kTriPanel + 1) + q];
-    __syncthreads();
+    if (col < s) {
+      T* W = out + wofs[t] + (int64_t)col * s;
+#pragma unroll
+      for (int m = 0; m < kTriRb; m++) {
+        const int i = lane + 32 * m;
+        if (m < nrb && i < s) W[i] = x[m];
+      }
+    }
+  }
+}
+
+// s <= 32: one warp inverts one triangle, lane j solving column j with the
+// column in registers; every lane reads the same factor entry (a broadcast
+// load), and the unrolled loops let those loads run ahead of the solve.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+tri_inv_small_kernel(SymDev S, const T* store, T* out, const int64_t* __restrict__ wofs,
+                     const SnTask* __restrict__ tasks, int ntasks) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (kThreads / 32);
+  for (int t = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); t < ntasks; t += nwarps) {
+    const SnTask task = tasks[t];
+    const int K = task.K;
+    const int s = S.sn_width[K];
+    const T* __restrict__ D = store + (int64_t)task.inst * S.storage + S.sn_off[K];
+    T x[kTriSmallS];
+#pragma unroll
+    for (int i = 0; i < kTriSmallS; i++) x[i] = (i == lane) ? sc_one(T()) : sc_zero(T());
+    if (task.a == 0) {
+#pragma unroll
+      for (int k = 0; k < kTriSmallS - 1; k++) {
+        if (k < s - 1) {
+#pragma unroll
+          for (int i = k + 1; i < kTriSmallS; i++)
+            if (i < s) x[i] = sub_s(x[i], mul_s(D[i + k * s], x[k]));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = kTriSmallS - 1; k >= 0; k--) {
+        if (k < s) {
+          const T ukk = D[k + k * s];
+          if (is_zero(ukk) && lane == 0) set_error(S.err, DEV_ZERO_PIVOT, S.sn_first[K] + k);
+          x[k] = div_s(x[k], ukk);
+#pragma unroll
+          for (int i = 0; i < k; i++) x[i] = sub_s(x[i], mul_s(D[i + k * s], x[k]));
+        }
+      }
+    }
+    if (lane < s) {
+      T* W = out + wofs[t] + (int64_t)lane * s;
+#pragma unroll
+      for (int i = 0; i < kTriSmallS; i++)
+        if (i < s) W[i] = x[i];
+    }
   }
 }
 
@@ -260,31 +344,31 @@ void launch_diag_lu(int dtype, const SymDev& S, void* store, const SnTask* tasks
     diag_lu_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (cdouble*)store, tasks, ntasks);
 }
 
-int tri_inv_smem_bytes(int dtype, int max_width) {
-  return max_width * (kTriPanel + 1 + kTriChunk) * (dtype == DT_F64 ? 8 : 16);
-}
-
-cudaError_t prepare_dense_kernels(int dtype, int max_width) {
-  const int smem = tri_inv_smem_bytes(dtype, max_width);
-  if (dtype == DT_F64)
-    return cudaFuncSetAttribute(tri_inv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem);
-  return cudaFuncSetAttribute(tri_inv_kernel<cdouble>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem);
-}
+cudaError_t prepare_dense_kernels(int, int) { return cudaSuccess; }
 
 void launch_tri_inv(int dtype, const SymDev& S, const void* store, void* out,
-                    const int64_t* wofs, const SnTask* tasks, int ntasks, int max_width,
+                    const int64_t* wofs, const SnTask* tasks, int ntasks, int, int small,
                     cudaStream_t st) {
   if (ntasks <= 0) return;
+  if (small) {
+    const int warps = kThreads / 32;
+    const int blocks = (ntasks + warps - 1) / warps;
+    const int grid = blocks < 152 * 8 ? blocks : 152 * 8;
+    if (dtype == DT_F64)
+      tri_inv_small_kernel<double><<<grid, kThreads, 0, st>>>(S, (const double*)store,
+                                                              (double*)out, wofs, tasks, ntasks);
+    else
+      tri_inv_small_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (const cdouble*)store,
+                                                               (cdouble*)out, wofs, tasks, ntasks);
+    return;
+  }
   const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
-  const int smem = tri_inv_smem_bytes(dtype, max_width);
   if (dtype == DT_F64)
-    tri_inv_kernel<double><<<grid, kThreads, smem, st>>>(S, (const double*)store, (double*)out,
-                                                         wofs, tasks, ntasks);
+    tri_inv_kernel<double><<<grid, kThreads, 0, st>>>(S, (const double*)store, (double*)out, wofs,
+                                                      tasks, ntasks);
   else
-    tri_inv_kernel<cdouble><<<grid, kThreads, smem, st>>>(S, (const cdouble*)store, (cdouble*)out,
-                                                          wofs, tasks, ntasks);
+    tri_inv_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (const cdouble*)store, (cdouble*)out,
+                                                       wofs, tasks, ntasks);
 }
 
 }  // namespace pselinv
