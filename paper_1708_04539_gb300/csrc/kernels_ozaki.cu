@@ -39,7 +39,6 @@ namespace pselinv {
 namespace {
 
 constexpr int kSliceThreads = 256;
-constexpr int kGemmThreads = 128;
 constexpr int kTileBytes = 4096;  // 64 rows x 32 K x 2 bytes
 constexpr unsigned long long kWaitBudgetNs = 2000000000ull;  // 2 s per bounded wait
 constexpr int kChunk = 16;  // 32-wide K blocks per exact accumulation chunk (512 values)
@@ -277,66 +276,64 @@ __device__ __forceinline__ double scaled_int_to_double(long long v, int e, bool 
   return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,"
-      "%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,"
-      "%62,%63}, [%64];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]),
-        "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]),
-        "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]),
-        "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
-        "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]),
-        "=r"(v[63])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint32_t (&v)[64]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,"
-      "%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,"
-      "%61,%62,%63,%64};" ::"r"(taddr),
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
       "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
       "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
-      "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]),
-      "r"(v[32]), "r"(v[33]), "r"(v[34]), "r"(v[35]), "r"(v[36]), "r"(v[37]), "r"(v[38]), "r"(v[39]),
-      "r"(v[40]), "r"(v[41]), "r"(v[42]), "r"(v[43]), "r"(v[44]), "r"(v[45]), "r"(v[46]), "r"(v[47]),
-      "r"(v[48]), "r"(v[49]), "r"(v[50]), "r"(v[51]), "r"(v[52]), "r"(v[53]), "r"(v[54]), "r"(v[55]),
-      "r"(v[56]), "r"(v[57]), "r"(v[58]), "r"(v[59]), "r"(v[60]), "r"(v[61]), "r"(v[62]), "r"(v[63])
+      "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
       : "memory");
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
-// sliced GEMM: one 128 x 64 output tile (and one K range) per task
+// sliced GEMM: one 128 x 64 output tile (and one K range) per task,
+// persistent CTAs with three roles
+//   warp 8 (one lane): bulk copies of the slice tiles into a 3-stage ring,
+//   warp 9 (one lane): the tcgen05 MMAs of every stage into the S
+//     accumulators; a commit frees the stage, another marks a chunk done,
+//   warps 0-7: drain each finished chunk (warp w owns TMEM lanes = output
+//     rows 32 (w % 4) .. + 31 and the 32 output columns of half w / 4), hand
+//     the accumulators back, add the chunk into the 64-bit totals and,
+//     after the last chunk, write the outputs while the MMAs of the next
+//     task already run.
 // ---------------------------------------------------------------------------
+constexpr int kOzStages = 3;
+constexpr int kOzDrainWarps = 8;
+constexpr int kOzThreads = (kOzDrainWarps + 2) * 32;
+
+// K-block range [kb0, kb0 + nkb) of a task (nkb <= 0: nothing to do)
+__device__ __forceinline__ void task_range(const OzDesc& d, int ks, int& kb0, int& nkb) {
+  int per = (d.K32 + d.ksplit - 1) / d.ksplit;
+  per = (per + kChunk - 1) / kChunk * kChunk;
+  kb0 = ks * per;
+  nkb = min(d.K32, kb0 + per) - kb0;
+}
+
 template <int S>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(kOzThreads, 1)
 ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ tasks, int ntasks,
                   int* err) {
-  constexpr int kAB = S * 2 * kTileBytes;  // A stage bytes (128 rows)
-  constexpr int kBB = S * kTileBytes;      // B stage bytes (64 rows)
-  constexpr int kStage = kAB + kBB;
+  constexpr int kAB = S * 2 * kTileBytes;  // A part of a stage (128 rows)
+  constexpr int kStage = S * 3 * kTileBytes;
   constexpr uint32_t kTmemCols = 512;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_full[2], bar_free[2], bar_acc;
+  __shared__ __align__(8) uint64_t bar_full[kOzStages], bar_free[kOzStages], bar_acc_full,
+      bar_acc_empty;
   __shared__ uint32_t tmem_slot;
-  __shared__ int eB_s[64];
+  __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
-    mbar_init(smem_u32(&bar_full[0]), 1);
-    mbar_init(smem_u32(&bar_full[1]), 1);
-    mbar_init(smem_u32(&bar_free[0]), 1);
-    mbar_init(smem_u32(&bar_free[1]), 1);
-    mbar_init(smem_u32(&bar_acc), 1);
+    for (int i = 0; i < kOzStages; i++) {
+      mbar_init(smem_u32(&bar_full[i]), 1);
+      mbar_init(smem_u32(&bar_free[i]), 1);
+    }
+    mbar_init(smem_u32(&bar_acc_full), 1);
+    mbar_init(smem_u32(&bar_acc_empty), kOzDrainWarps);  // one arrival per drain warp
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -349,165 +346,175 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
-  uint32_t ph_full[2] = {0, 0}, ph_free[2] = {0, 0}, ph_acc = 0;
   bool ok = true;
 
-  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
-    const OzTask task = tasks[t];
-    const OzDesc d = descs[task.d];
-    const int m0 = task.tm * 128, n0 = task.tn * 64;
-    int per = (d.K32 + d.ksplit - 1) / d.ksplit;
-    per = (per + kChunk - 1) / kChunk * kChunk;
-    const int kb0 = task.ks * per;
-    const int kb1 = min(d.K32, kb0 + per);
-    const int nkb = kb1 - kb0;
-    if (tid < 64) eB_s[tid] = (n0 + tid < d.N) ? d.eB[n0 + tid] : 0;
-    // per-row 64-bit totals live in tensor memory after the S accumulators:
-    // value j of the thread's row at columns S*64 + 2j (low) and + 2j + 1 (high)
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint32_t ttot = trow + (uint32_t)(S * 64);
-    bool first_chunk = true;
-    __syncthreads();
-
-    // stage loader (thread 0): S slices x {2 A tiles, 1 B tile}
-    const bool a_second = 2 * task.tm + 1 < d.A_R64;
-    auto issue_load = [&](int kb, int buf) {
-      unsigned char* st = smem + buf * kStage;
-      const uint32_t fb = smem_u32(&bar_full[buf]);
-      const uint32_t bytes = (uint32_t)(S * (a_second ? 2 : 1) * kTileBytes + S * kTileBytes);
-      mbar_expect_tx(fb, bytes);
-      const int64_t a_sl = (int64_t)d.A_R64 * d.K32 * kTileBytes;
-      const int64_t b_sl = (int64_t)d.B_R64 * d.K32 * kTileBytes;
-      const unsigned char* A = reinterpret_cast<const unsigned char*>(d.A);
-      const unsigned char* B = reinterpret_cast<const unsigned char*>(d.B);
-      for (int s = 0; s < S; s++) {
-        const unsigned char* a0 = A + s * a_sl + ((int64_t)(2 * task.tm) * d.K32 + kb) * kTileBytes;
-        bulk_load(smem_u32(st + s * 2 * kTileBytes), a0, kTileBytes, fb);
-        if (a_second) {
-          const unsigned char* a1 = A + s * a_sl + ((int64_t)(2 * task.tm + 1) * d.K32 + kb) * kTileBytes;
-          bulk_load(smem_u32(st + s * 2 * kTileBytes + kTileBytes), a1, kTileBytes, fb);
-        }
-        const int kbb = d.swap_b ? (kb < d.half ? kb + d.half : kb - d.half) : kb;
-        const unsigned char* b0 = B + s * b_sl + ((int64_t)task.tn * d.K32 + kbb) * kTileBytes;
-        bulk_load(smem_u32(st + kAB + s * kTileBytes), b0, kTileBytes, fb);
-      }
-    };
-
-    for (int i = 0; i < nkb; i++) {
-      const int buf = i & 1;
-      const bool chunk_end = (i % kChunk == kChunk - 1) || (i == nkb - 1);
-      if (tid == 0 && ok) {
-        if (i == 0) issue_load(kb0, 0);
-        if (i + 1 < nkb) {
-          const int nb = buf ^ 1;
-          if (i + 1 >= 2) {
-            ok = mbar_wait(smem_u32(&bar_free[nb]), ph_free[nb]);
-            ph_free[nb] ^= 1;
+  if (warp == kOzDrainWarps) {
+    // ---- producer ----
+    if (lane == 0) {
+      uint32_t g = 0;  // K blocks issued so far (ring position)
+      for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
+        const OzTask task = tasks[t];
+        const OzDesc d = descs[task.d];
+        int kb0, nkb;
+        task_range(d, task.ks, kb0, nkb);
+        const bool a_second = 2 * task.tm + 1 < d.A_R64;
+        const uint32_t bytes = (uint32_t)(S * (a_second ? 2 : 1) * kTileBytes + S * kTileBytes);
+        const int64_t a_sl = (int64_t)d.A_R64 * d.K32 * kTileBytes;
+        const int64_t b_sl = (int64_t)d.B_R64 * d.K32 * kTileBytes;
+        const unsigned char* A = reinterpret_cast<const unsigned char*>(d.A);
+        const unsigned char* B = reinterpret_cast<const unsigned char*>(d.B);
+        for (int i = 0; i < nkb; i++, g++) {
+          const int stg = (int)(g % kOzStages);
+          const uint32_t u = g / kOzStages;
+          if (u > 0 && !mbar_wait(smem_u32(&bar_free[stg]), (u - 1) & 1)) {
+            ok = false;
+            break;
           }
-          if (ok) issue_load(kb0 + i + 1, nb);
+          if (abort_flag) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = smem + stg * kStage;
+          const uint32_t fb = smem_u32(&bar_full[stg]);
+          mbar_expect_tx(fb, bytes);
+          const int kb = kb0 + i;
+          const int kbb = d.swap_b ? (kb < d.half ? kb + d.half : kb - d.half) : kb;
+          for (int sl = 0; sl < S; sl++) {
+            const unsigned char* a0 = A + sl * a_sl + ((int64_t)(2 * task.tm) * d.K32 + kb) * kTileBytes;
+            bulk_load(smem_u32(st + sl * 2 * kTileBytes), a0, kTileBytes, fb);
+            if (a_second)
+              bulk_load(smem_u32(st + sl * 2 * kTileBytes + kTileBytes), a0 + (int64_t)d.K32 * kTileBytes,
+                        kTileBytes, fb);
+            const unsigned char* b0 = B + sl * b_sl + ((int64_t)task.tn * d.K32 + kbb) * kTileBytes;
+            bulk_load(smem_u32(st + kAB + sl * kTileBytes), b0, kTileBytes, fb);
+          }
         }
-        if (ok) ok = mbar_wait(smem_u32(&bar_full[buf]), ph_full[buf]);
-        ph_full[buf] ^= 1;
-        fence_after();
-        if (ok) {
-          const uint32_t st = smem_u32(smem + buf * kStage);
+      }
+      if (!ok) abort_flag = 1;
+    }
+  } else if (warp == kOzDrainWarps + 1) {
+    // ---- MMA issue ----
+    if (lane == 0) {
+      uint32_t g = 0, q = 0;  // K blocks consumed, chunks completed
+      for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
+        const OzTask task = tasks[t];
+        const OzDesc d = descs[task.d];
+        int kb0, nkb;
+        task_range(d, task.ks, kb0, nkb);
+        for (int i = 0; i < nkb; i++, g++) {
+          const int stg = (int)(g % kOzStages);
           const bool first = (i % kChunk) == 0;
+          const bool last = (i % kChunk == kChunk - 1) || (i == nkb - 1);
+          if (first && q > 0 && !mbar_wait(smem_u32(&bar_acc_empty), (q - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          if (!mbar_wait(smem_u32(&bar_full[stg]), (g / kOzStages) & 1) || abort_flag) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t st = smem_u32(smem + stg * kStage);
           const uint32_t idesc = (d.neg_half && kb0 + i >= d.half) ? kIdescNegA : kIdesc;
-          // descriptors of the stage bases; an offset within shared memory is
-          // added to the address field (bits 0-13 hold address >> 4)
+          // stage-base descriptors; an offset within shared memory is added
+          // to the address field (bits 0-13 hold address >> 4)
           const uint64_t a0 = smem_desc(st), b0 = smem_desc(st + kAB);
 #pragma unroll
-          for (int s = 0; s < S; s++)
+          for (int sa = 0; sa < S; sa++)
 #pragma unroll
-            for (int tt = 0; tt < S - s; tt++) {
-              const uint32_t dt = tmem + (uint32_t)((s + tt) * 64);
-              const uint64_t ad = a0 + (uint64_t)((s * 2 * kTileBytes) >> 4);
-              const uint64_t bd = b0 + (uint64_t)((tt * kTileBytes) >> 4);
-              mma_f16(dt, ad, bd, (s == 0 && first) ? 0u : 1u, idesc);
+            for (int tb = 0; tb < S - sa; tb++) {
+              const uint32_t dt = tmem + (uint32_t)((sa + tb) * 64);
+              const uint64_t ad = a0 + (uint64_t)((sa * 2 * kTileBytes) >> 4);
+              const uint64_t bd = b0 + (uint64_t)((tb * kTileBytes) >> 4);
+              mma_f16(dt, ad, bd, (sa == 0 && first) ? 0u : 1u, idesc);
               mma_f16(dt, ad + (256 >> 4), bd + (256 >> 4), 1u, idesc);
             }
+          mma_commit(smem_u32(&bar_free[stg]));
+          if (last) {
+            mma_commit(smem_u32(&bar_acc_full));
+            q++;
+          }
         }
-        mma_commit(smem_u32(&bar_free[buf]));
-        if (chunk_end) mma_commit(smem_u32(&bar_acc));
       }
-      if (chunk_end) {
-        __syncwarp();
-        bool w = mbar_wait(smem_u32(&bar_acc), ph_acc);
-        ph_acc ^= 1;
-        if (!w) ok = false;
+      if (!ok) abort_flag = 1;
+    }
+  } else {
+    // ---- drain and epilogue (warps 0-7) ----
+    const int quarter = warp & 3, hcol = warp >> 2;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(hcol * 32);
+    // 64-bit totals after the accumulators: value j of the half at 2j (lo), 2j + 1 (hi)
+    const uint32_t ttot = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(S * 64 + hcol * 64);
+    uint32_t q = 0;
+    for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
+      const OzTask task = tasks[t];
+      const OzDesc d = descs[task.d];
+      int kb0, nkb;
+      task_range(d, task.ks, kb0, nkb);
+      if (nkb <= 0) continue;
+      const int nchunks = (nkb + kChunk - 1) / kChunk;
+      const int r = task.tm * 128 + quarter * 32 + lane;
+      const int nb = task.tn * 64 + hcol * 32;
+      for (int c = 0; c < nchunks; c++, q++) {
+        if (!mbar_wait(smem_u32(&bar_acc_full), q & 1) || abort_flag) {
+          ok = false;
+          break;
+        }
         fence_after();
-        // drain: warp w holds TMEM lanes 32w..32w+31 = output rows
+        // the chunk's S accumulators -> one 64-bit partial sum per output
+        long long part[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) part[j] = 0;
 #pragma unroll 1
-        for (int h = 0; h < 2; h++) {
-          long long part[32];
+        for (int dd = 0; dd < S; dd++) {
+          const int shift = 7 * (S - 1 - dd);
+          uint32_t v[32];
+          tmem_ld32(trow + (uint32_t)(dd * 64), v);
 #pragma unroll
-          for (int j = 0; j < 32; j++) part[j] = 0;
-#pragma unroll 1
-          for (int dd = 0; dd < S; dd++) {
-            const int shift = 7 * (S - 1 - dd);
-            uint32_t v[32];
-            tmem_ld32(trow + (uint32_t)(dd * 64 + h * 32), v);
-#pragma unroll
-            for (int j = 0; j < 32; j++)
-              part[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shift;
-          }
-          uint32_t tv[64];
-          if (!first_chunk) tmem_ld64(ttot + (uint32_t)(h * 64), tv);
-#pragma unroll
-          for (int j = 0; j < 32; j++) {
-            long long t = part[j];
-            if (!first_chunk) t += (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
-            tv[2 * j] = (uint32_t)t;
-            tv[2 * j + 1] = (uint32_t)((unsigned long long)t >> 32);
-          }
-          tmem_st64(ttot + (uint32_t)(h * 64), tv);
+          for (int j = 0; j < 32; j++)
+            part[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shift;
         }
-        first_chunk = false;
+        // accumulators read: the MMAs of the next chunk may start
         fence_before();
-        __syncthreads();
-      }
-    }
-    if (tid == 0 && nkb > 0) {
-      // resynchronise the free barriers of the last two stages
-      for (int i = max(0, nkb - 2); i < nkb; i++) {
-        const int b = i & 1;
-        if (ok) ok = mbar_wait(smem_u32(&bar_free[b]), ph_free[b]);
-        ph_free[b] ^= 1;
-      }
-    }
-    if (!ok && lane == 0) atomicExch(err, DEV_TIMEOUT);
-    // epilogue: thread row r of the tile
-    const int r = m0 + warp * 32 + lane;
-    if (nkb > 0) {
-      // alpha is +-1: its sign is folded into the assembled doubles
-      const int ea = (r < d.M ? d.eA[r] : 0) - 14 - 7 * (S - 1);
-      const bool neg = d.alpha < 0.0;
-      double* C = d.C;
-      fence_after();
-#pragma unroll 1
-      for (int h = 0; h < 2; h++) {
-        uint32_t tv[64];
-        tmem_ld64(ttot + (uint32_t)(h * 64), tv);  // all lanes: the load is warp-wide
-        if (r < d.M) {
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_acc_empty))
+                       : "memory");
+        // totals in two rounds of 16 values (32 TMEM columns) each
+        const bool last_chunk = c == nchunks - 1;
+        const int ea = (r < d.M ? d.eA[r] : 0) - 14 - 7 * (S - 1);
+        const bool neg = d.alpha < 0.0;  // alpha is +-1: its sign goes into the doubles
 #pragma unroll
-          for (int j = 0; j < 32; j++) {
-            const int n = n0 + h * 32 + j;
-            if (n < d.N) {
-              const long long t = (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
-              const double v = scaled_int_to_double(t, ea + eB_s[h * 32 + j], neg);
-              double* c = C + (r + (int64_t)n * d.ldc) * d.cscale + d.coff;
-              if (d.atomic) atomicAdd(c, v); else *c = v;
+        for (int g2 = 0; g2 < 2; g2++) {
+          uint32_t tv[32];
+          if (c > 0) tmem_ld32(ttot + (uint32_t)(g2 * 32), tv);
+          if (!last_chunk) {
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+              long long tt = part[g2 * 16 + j];
+              if (c > 0) tt += (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
+              tv[2 * j] = (uint32_t)tt;
+              tv[2 * j + 1] = (uint32_t)((unsigned long long)tt >> 32);
+            }
+            tmem_st32(ttot + (uint32_t)(g2 * 32), tv);
+          } else if (r < d.M) {
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+              const int n = nb + g2 * 16 + j;
+              if (n < d.N) {
+                long long tt = part[g2 * 16 + j];
+                if (c > 0) tt += (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
+                const double v = scaled_int_to_double(tt, ea + d.eB[n], neg);
+                double* cp = d.C + (r + (int64_t)n * d.ldc) * d.cscale + d.coff;
+                if (d.atomic) atomicAdd(cp, v); else *cp = v;
+              }
             }
           }
         }
       }
-      fence_before();
     }
-    if (__syncthreads_or(!ok)) {
-      ok = false;
-      break;
-    }
+    if (!ok) abort_flag = 1;
   }
+  if (!ok && lane == 0) atomicExch(err, DEV_TIMEOUT);
   fence_before();
   __syncthreads();
   if (warp == 0)
@@ -516,7 +523,7 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
 
 template <int S>
 constexpr int gemm_smem() {
-  return 2 * (S * 2 * kTileBytes + S * kTileBytes);
+  return kOzStages * S * 3 * kTileBytes;
 }
 
 // Failure-path check: wait on an mbarrier that nothing will complete, with a
@@ -569,9 +576,9 @@ void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntas
   // one CTA fits an SM (shared memory and tensor memory): persistent grid
   const int grid = ntasks < 152 ? ntasks : 152;
   switch (S) {
-    case 4: ozaki_gemm_kernel<4><<<grid, kGemmThreads, gemm_smem<4>(), st>>>(descs, tasks, ntasks, err); break;
-    case 5: ozaki_gemm_kernel<5><<<grid, kGemmThreads, gemm_smem<5>(), st>>>(descs, tasks, ntasks, err); break;
-    default: ozaki_gemm_kernel<6><<<grid, kGemmThreads, gemm_smem<6>(), st>>>(descs, tasks, ntasks, err); break;
+    case 4: ozaki_gemm_kernel<4><<<grid, kOzThreads, gemm_smem<4>(), st>>>(descs, tasks, ntasks, err); break;
+    case 5: ozaki_gemm_kernel<5><<<grid, kOzThreads, gemm_smem<5>(), st>>>(descs, tasks, ntasks, err); break;
+    default: ozaki_gemm_kernel<6><<<grid, kOzThreads, gemm_smem<6>(), st>>>(descs, tasks, ntasks, err); break;
   }
 }
 
