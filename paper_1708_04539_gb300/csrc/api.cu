@@ -312,9 +312,8 @@ size_t ozaki_norm_bytes(const HostSym& H, int64_t nb, int S, size_t es) {
     size_t b = 512;
     for (int64_t i = H.level_ptr[d]; i < H.level_ptr[d + 1]; i++) {
       const int64_t K = H.level_sn[i], s = H.sn_width[K], c = cK(H, K);
-      if (c == 0) continue;
-      b += 2 * (parts * slice_bytes(c, s, S) + exps_bytes(c) + 512) +
-           2 * (parts * slice_bytes(s, s, S) + exps_bytes(s) + 512) + (size_t)(2 * c + 2 * s) * 8;
+      b += 2 * (parts * slice_bytes(s, s, S) + exps_bytes(s) + 512) + (size_t)(2 * c + 2 * s) * 8;
+      if (c > 0) b += 2 * (parts * slice_bytes(c, s, S) + exps_bytes(c) + 512);
     }
     mx = std::max(mx, b * (size_t)nb + 512);
   }
@@ -674,11 +673,13 @@ struct OzBuilder {
   }
 };
 
-// Split-precision normalisation of one depth level (Algorithm 1 step 2):
-// Lhat = L_{C,K} Linv and Uhat^T = U_{K,C}^T Uinv^T as sliced products (K =
-// s), after the maxima and slicing passes of the four operands.  Linv and
-// Uinv hold exact zeros outside their triangles, so the full products are
-// the triangular ones.  Steps go to the side stream; scratch from `base`.
+// Split-precision normalisation of one depth level (Algorithm 1 step 2 and
+// the diagonal block D_K = U_KK^{-1} L_KK^{-1} that starts Ainv_KK):
+// Lhat = L_{C,K} Linv, Uhat^T = U_{K,C}^T Uinv^T and D_K = Uinv Linv as
+// sliced products (K = s), after the maxima and slicing passes of the four
+// operands (Linv and Uinv serve two products each).  Linv and Uinv hold
+// exact zeros outside their triangles, so the full products are the
+// triangular ones.  Steps go to the side stream; scratch from `base`.
 void add_ozaki_normalize(pselinv_ctx* h, Plan& P, int lev, int64_t nb,
                          const std::vector<int64_t>& wbase, size_t base) {
   const HostSym& H = h->H;
@@ -688,7 +689,7 @@ void add_ozaki_normalize(pselinv_ctx* h, Plan& P, int lev, int64_t nb,
   for (int64_t b = 0; b < nb; b++)
     for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
       const int64_t K = H.level_sn[i];
-      if (cK(H, K) > 0) nmax += 2 * cK(H, K) + 2 * H.sn_width[K];
+      nmax += 2 * cK(H, K) + 2 * H.sn_width[K];
     }
   if (nmax == 0) return;
   unsigned long long* maxbase = (unsigned long long*)ob.take(align256((size_t)nmax * 8 + 8));
@@ -699,24 +700,26 @@ void add_ozaki_normalize(pselinv_ctx* h, Plan& P, int lev, int64_t nb,
     for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
       const int64_t K = H.level_sn[i];
       const int s = (int)H.sn_width[K], c = (int)cK(H, K);
-      if (c == 0) continue;
       const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
       const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
       const char* Linv = h->scratch + (size_t)wbase[b * H.ns + K] * es;
       const char* Uinv = Linv + (size_t)s * s * es;
-      SliceDesc la = ob.slice(h->lu + lo, c, SLICE_ROWS, c, s);  // L_{C,K}(m, k)
-      SliceDesc ua = ob.slice(h->lu + uo, c, SLICE_ROWS, c, s);  // U_{K,C}^T(m, k)
-      SliceDesc lb = ob.slice(Linv, s, SLICE_COLS, s, s);        // Linv(k, n)
-      SliceDesc ub = ob.slice(Uinv, s, SLICE_ROWS, s, s);        // Uinv(n, k)
-      la.maxbits = maxbase + moff;
-      ua.maxbits = maxbase + moff + c;
-      lb.maxbits = maxbase + moff + 2 * c;
-      ub.maxbits = maxbase + moff + 2 * c + s;
-      moff += 2 * c + 2 * s;
-      sl.push_back(la);
-      sl.push_back(ua);
+      SliceDesc lb = ob.slice(Linv, s, SLICE_COLS, s, s);  // Linv(k, n)
+      SliceDesc ub = ob.slice(Uinv, s, SLICE_ROWS, s, s);  // Uinv(n, k) = Uinv(m, k)
+      lb.maxbits = maxbase + moff;
+      ub.maxbits = maxbase + moff + s;
+      moff += 2 * s;
       sl.push_back(lb);
       sl.push_back(ub);
+      ob.product(prods, ub, lb, h->ainv + so, s, s, s, 1.0);  // D_K
+      if (c == 0) continue;
+      SliceDesc la = ob.slice(h->lu + lo, c, SLICE_ROWS, c, s);  // L_{C,K}(m, k)
+      SliceDesc ua = ob.slice(h->lu + uo, c, SLICE_ROWS, c, s);  // U_{K,C}^T(m, k)
+      la.maxbits = maxbase + moff;
+      ua.maxbits = maxbase + moff + c;
+      moff += 2 * c;
+      sl.push_back(la);
+      sl.push_back(ua);
       ob.product(prods, la, lb, h->nf + lo, c, c, s, 1.0);
       ob.product(prods, ua, ub, h->nf + uo, c, c, s, 1.0);
     }
@@ -887,7 +890,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   }
   const size_t norm_base = selinv_main_bytes(H, nb, es);
   bool third_waited = false;
-  // split = true: Lhat and Uhat^T as sliced products (D_K stays FP64)
+  // split = true: Lhat, Uhat^T and D_K as sliced products
   auto add_normalize = [&](int lev, bool split) {
     std::vector<GemmDesc> norm;
     for (int64_t b = 0; b < nb; b++)
@@ -897,10 +900,11 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
         const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
         char* Linv = h->scratch + (size_t)w0 * es;
         char* Uinv = Linv + (size_t)s * s * es;
+        if (split) continue;  // all three as sliced products
         // D_K = Uinv Linv (upper x lower), Lhat = L Linv, Uhat^T = U^T Uinv^T (lower B)
         norm.push_back(make_desc(Uinv, Linv, h->ainv + so, s, s, s, s, s, s, 0, 0, 1.0, 0.0, 0, 1,
                                  GEMM_TRI_UPPER_A | GEMM_TRI_LOWER_B));
-        if (c > 0 && !split) {
+        if (c > 0) {
           const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
           norm.push_back(make_desc(h->lu + lo, Linv, h->nf + lo, c, s, s, c, s, c, 0, 0, 1.0, 0.0,
                                    0, 1, GEMM_TRI_LOWER_B));
