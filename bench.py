@@ -471,9 +471,11 @@ def run_ours(args):
     if args.dump_profile and rank == 0:
         with torch.cuda.stream(stream):
             fprof = h.profile(1, stream=stream)
+            h.profile(2, stream=stream)  # warm the multi-stream timeline once
+            timeline = h.profile(2, stream=stream)
         with open(args.dump_profile, "w") as f:
             json.dump({"precision": args.precision, "size": args.size, "steps": prof,
-                       "factor_steps": fprof}, f)
+                       "factor_steps": fprof, "timeline": timeline}, f)
 
     # end to end through the C ABI with host buffers: H2D values, factor,
     # selected inversion, D2H of the selected entries

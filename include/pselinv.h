@@ -174,6 +174,8 @@ typedef struct pselinv_step_stat {
                      else -1 */
   int32_t side;   /* stream of the launch in a sweep: 0 main, 1 normalisation side stream,
                      2 third stream (triangular inverses of the deeper levels) */
+  double start_ms; /* which = 2: time from the start of the sweep until the launch's stream
+                      reached it (its wait included); else 0 */
 } pselinv_step_stat;
 
 enum pselinv_step_kind {
@@ -184,10 +186,13 @@ enum pselinv_step_kind {
 };
 
 /* Run the selected-inversion plan (which = 0) or the factorisation plan
- * (which = 1) launch by launch, outside any graph, with CUDA events around
- * every launch, and report up to `cap` records in out[] (*count = number of
- * launches).  The results are the same as pselinv_selinv / pselinv_factor
- * produce.  Synchronises `stream`. */
+ * (which = 1) launch by launch, outside any graph and on `stream` alone,
+ * with CUDA events around every launch, and report up to `cap` records in
+ * out[] (*count = number of launches).  which = 2: a timeline of the
+ * selected-inversion plan run on its own streams (normalisation overlapped
+ * as in pselinv_selinv, no graph): ms is each launch's span on its stream
+ * and start_ms when its stream reached it.  The results are the same as
+ * pselinv_selinv / pselinv_factor produce.  Synchronises `stream`. */
 int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out, int64_t cap,
                     int64_t* count);
 

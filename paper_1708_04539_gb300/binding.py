@@ -75,7 +75,7 @@ class TuneRecord(ctypes.Structure):
 class StepStat(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("tasks", ctypes.c_int64),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("ms", ctypes.c_double),
-                ("param", ctypes.c_int32), ("side", ctypes.c_int32)]
+                ("param", ctypes.c_int32), ("side", ctypes.c_int32), ("start_ms", ctypes.c_double)]
 
 
 class Structure(ctypes.Structure):
@@ -276,7 +276,8 @@ class SelInv:
         return out
 
     def profile(self, which=0, stream=None):
-        """Launch-by-launch timing of the selinv (0) or factor (1) plan."""
+        """Launch-by-launch timing of the selinv (0) or factor (1) plan, or the
+        timeline of the selinv plan on its own streams (2)."""
         cap = 1 << 16
         buf = (StepStat * cap)()
         cnt = ctypes.c_int64(0)
@@ -284,7 +285,8 @@ class SelInv:
                                               ctypes.byref(cnt)), "pselinv_profile")
         return [{"kind": STEP_KINDS.get(buf[i].kind, buf[i].kind), "level": buf[i].level,
                  "tasks": buf[i].tasks, "flops": buf[i].flops, "bytes": buf[i].bytes,
-                 "ms": buf[i].ms, "param": buf[i].param, "side": buf[i].side}
+                 "ms": buf[i].ms, "param": buf[i].param, "side": buf[i].side,
+                 "start_ms": buf[i].start_ms}
                 for i in range(min(cnt.value, cap))]
 
     def plan_stats(self):

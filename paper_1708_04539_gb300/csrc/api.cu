@@ -73,7 +73,9 @@ struct Step {
 };
 
 // events of a multi-stream plan
-enum PlanEvent { EV_FORK = 0, EV_SIDE_JOIN = 1, EV_THIRD_JOIN = 2, EV_THIRD_DONE = 3, EV_LEVEL = 4 };
+enum PlanEvent {
+  EV_FORK = 0, EV_SIDE_JOIN = 1, EV_THIRD_JOIN = 2, EV_THIRD_DONE = 3, EV_MAIN_JOIN = 4, EV_LEVEL = 5
+};
 
 struct Plan {
   std::vector<Step> steps;
@@ -139,8 +141,9 @@ struct pselinv_ctx {
   std::map<std::tuple<int, int, int>, int> tuned;
   std::vector<pselinv_tune_record> records;
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t side_stream = nullptr;
-  cudaStream_t third_stream = nullptr;
+  cudaStream_t main_stream = nullptr;   // sweep launches (highest priority)
+  cudaStream_t side_stream = nullptr;   // normalisation one level ahead
+  cudaStream_t third_stream = nullptr;  // triangular inverses of the deeper levels (lowest)
   int64_t last_info = -1;
   int last_status = 0;
 };
@@ -1044,12 +1047,33 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       break;
     case ST_OZGEMM:
       launch_ozaki_gemm(s.cfg, (const OzDesc*)(a + s.descs), (const OzTask*)(a + s.tasks), s.n,
-                        h->derr, st);
+                        h->derr, s.side == 0, st);
       break;
     case ST_ZERO:
       launch_zero((const CopySeg*)(a + s.tasks), s.n, st);
       break;
   }
+}
+
+// The streams of a multi-stream sweep (created on first use): the sweep's
+// own launches at the highest priority, the normalisation one level ahead
+// below it, the triangular inverses of the deeper levels lowest, so that
+// pending CTAs of the critical path are scheduled first.
+struct SweepStreams {
+  cudaStream_t main, side, third;
+};
+int sweep_streams(pselinv_ctx* h, SweepStreams* out) {
+  int least = 0, greatest = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  const int middle = least + (greatest - least) / 2;
+  if (!h->main_stream)
+    CK(cudaStreamCreateWithPriority(&h->main_stream, cudaStreamNonBlocking, greatest));
+  if (!h->side_stream)
+    CK(cudaStreamCreateWithPriority(&h->side_stream, cudaStreamNonBlocking, middle));
+  if (!h->third_stream)
+    CK(cudaStreamCreateWithPriority(&h->third_stream, cudaStreamNonBlocking, least));
+  *out = {h->main_stream, h->side_stream, h->third_stream};
+  return PSELINV_OK;
 }
 
 // Issue the plan on `st`; steps marked `side` go to the side stream, forked
@@ -1060,29 +1084,23 @@ int run_steps(pselinv_ctx* h, Plan& P, cudaStream_t st) {
     CK(cudaGetLastError());
     return PSELINV_OK;
   }
-  if (!h->side_stream) {
-    // lowest priority: pending CTAs of the sweep are scheduled first
-    int lo = 0, hi = 0;
-    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    CK(cudaStreamCreateWithPriority(&h->side_stream, cudaStreamNonBlocking, lo));
-  }
-  if (!h->third_stream) {
-    int lo = 0, hi = 0;
-    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    CK(cudaStreamCreateWithPriority(&h->third_stream, cudaStreamNonBlocking, lo));
-  }
-  cudaStream_t side = h->side_stream, third = h->third_stream;
+  SweepStreams q3;
+  const int rc = sweep_streams(h, &q3);
+  if (rc != PSELINV_OK) return rc;
   CK(cudaEventRecord(P.ev[EV_FORK], st));
-  CK(cudaStreamWaitEvent(side, P.ev[EV_FORK], 0));
-  CK(cudaStreamWaitEvent(third, P.ev[EV_FORK], 0));
+  CK(cudaStreamWaitEvent(q3.main, P.ev[EV_FORK], 0));
+  CK(cudaStreamWaitEvent(q3.side, P.ev[EV_FORK], 0));
+  CK(cudaStreamWaitEvent(q3.third, P.ev[EV_FORK], 0));
   for (const Step& s : P.steps) {
-    cudaStream_t q = s.side == 1 ? side : s.side == 2 ? third : st;
+    cudaStream_t q = s.side == 1 ? q3.side : s.side == 2 ? q3.third : q3.main;
     if (s.wait >= 0) CK(cudaStreamWaitEvent(q, P.ev[s.wait], 0));
     launch_step(h, P, s, q);
     if (s.signal >= 0) CK(cudaEventRecord(P.ev[s.signal], q));
   }
-  CK(cudaEventRecord(P.ev[EV_SIDE_JOIN], side));
-  CK(cudaEventRecord(P.ev[EV_THIRD_JOIN], third));
+  CK(cudaEventRecord(P.ev[EV_MAIN_JOIN], q3.main));
+  CK(cudaEventRecord(P.ev[EV_SIDE_JOIN], q3.side));
+  CK(cudaEventRecord(P.ev[EV_THIRD_JOIN], q3.third));
+  CK(cudaStreamWaitEvent(st, P.ev[EV_MAIN_JOIN], 0));
   CK(cudaStreamWaitEvent(st, P.ev[EV_SIDE_JOIN], 0));
   CK(cudaStreamWaitEvent(st, P.ev[EV_THIRD_JOIN], 0));
   CK(cudaGetLastError());
@@ -1109,7 +1127,8 @@ int run_plan(pselinv_ctx* h, Plan& P, cudaStream_t st, bool graph) {
       return cuda_status(e);
     }
     P.graph = g;
-    CK(cudaGraphInstantiate(&P.exec, g, 0));
+    // launches keep the priority of the stream they were captured from
+    CK(cudaGraphInstantiate(&P.exec, g, cudaGraphInstantiateFlagUseNodePriority));
   }
   CK(cudaGraphLaunch(P.exec, st));
   return PSELINV_OK;
@@ -1339,31 +1358,70 @@ int pselinv_get_structure(pselinv_t h, pselinv_structure* o) {
 
 int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out, int64_t cap,
                     int64_t* count) {
-  if (!h || (which != 0 && which != 1) || !count || (cap > 0 && !out)) return PSELINV_ERR_ARG;
-  if (which == 0 ? !h->factored : h->nbatch == 0) return PSELINV_ERR_ARG;
+  if (!h || which < 0 || which > 2 || !count || (cap > 0 && !out)) return PSELINV_ERR_ARG;
+  if (which != 1 ? !h->factored : h->nbatch == 0) return PSELINV_ERR_ARG;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
   const int prec = h->last_precision;
-  if (which == 0 && !h->selinv_plan[prec][sched].built) {
+  if (which != 1 && !h->selinv_plan[prec][sched].built) {
     const int rc = build_selinv_plan(h, sched, prec);
     if (rc != PSELINV_OK) return rc;
   }
-  Plan& P = which == 0 ? h->selinv_plan[prec][sched] : h->factor_plan;
+  Plan& P = which != 1 ? h->selinv_plan[prec][sched] : h->factor_plan;
   const size_t ns = P.steps.size();
-  std::vector<cudaEvent_t> ev(ns + 1);
+  // which 0/1: serialised, ev[i] .. ev[i + 1] around launch i;
+  // which 2: the plan's own streams, ev[2i + 1] before and ev[2i + 2] after
+  //   launch i on its stream, ev[0] at the start
+  std::vector<cudaEvent_t> ev(which == 2 ? 2 * ns + 1 : ns + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(ev[0], st));
-  for (size_t i = 0; i < ns; i++) {
-    launch_step(h, P, P.steps[i], st);
-    CK(cudaEventRecord(ev[i + 1], st));
+  if (which == 2 && P.two_streams) {
+    SweepStreams q3;
+    const int rc = sweep_streams(h, &q3);
+    if (rc != PSELINV_OK) return rc;
+    CK(cudaStreamWaitEvent(q3.main, ev[0], 0));
+    CK(cudaStreamWaitEvent(q3.side, ev[0], 0));
+    CK(cudaStreamWaitEvent(q3.third, ev[0], 0));
+    for (size_t i = 0; i < ns; i++) {
+      const Step& s = P.steps[i];
+      cudaStream_t q = s.side == 1 ? q3.side : s.side == 2 ? q3.third : q3.main;
+      if (s.wait >= 0) CK(cudaStreamWaitEvent(q, P.ev[s.wait], 0));
+      CK(cudaEventRecord(ev[2 * i + 1], q));
+      launch_step(h, P, s, q);
+      CK(cudaEventRecord(ev[2 * i + 2], q));
+      if (s.signal >= 0) CK(cudaEventRecord(P.ev[s.signal], q));
+    }
+    CK(cudaEventRecord(P.ev[EV_MAIN_JOIN], q3.main));
+    CK(cudaEventRecord(P.ev[EV_SIDE_JOIN], q3.side));
+    CK(cudaEventRecord(P.ev[EV_THIRD_JOIN], q3.third));
+    CK(cudaStreamWaitEvent(st, P.ev[EV_MAIN_JOIN], 0));
+    CK(cudaStreamWaitEvent(st, P.ev[EV_SIDE_JOIN], 0));
+    CK(cudaStreamWaitEvent(st, P.ev[EV_THIRD_JOIN], 0));
+  } else if (which == 2) {
+    for (size_t i = 0; i < ns; i++) {
+      CK(cudaEventRecord(ev[2 * i + 1], st));
+      launch_step(h, P, P.steps[i], st);
+      CK(cudaEventRecord(ev[2 * i + 2], st));
+    }
+  } else {
+    for (size_t i = 0; i < ns; i++) {
+      launch_step(h, P, P.steps[i], st);
+      CK(cudaEventRecord(ev[i + 1], st));
+    }
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   *count = (int64_t)ns;
   for (size_t i = 0; i < ns && (int64_t)i < cap; i++) {
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+    float ms = 0, t0 = 0;
+    if (which == 2) {
+      CK(cudaEventElapsedTime(&t0, ev[0], ev[2 * i + 1]));
+      CK(cudaEventElapsedTime(&ms, ev[2 * i + 1], ev[2 * i + 2]));
+    } else {
+      CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+    }
+    out[i].start_ms = t0;
     const Step& s = P.steps[i];
     static const int kinds[] = {PSELINV_STEP_GEMM,    PSELINV_STEP_TRI_INV,    PSELINV_STEP_DIAG_LU,
                                 PSELINV_STEP_GATHER,  PSELINV_STEP_SCATTER_SUB, PSELINV_STEP_COPY,
@@ -1381,7 +1439,7 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
     out[i].side = s.side;
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  if (which == 0) h->inverted = true;
+  if (which != 1) h->inverted = true;
   return read_device_error(h, st);
 }
 
@@ -1693,6 +1751,7 @@ void pselinv_free(pselinv_t h) {
     cudaSetDevice(h->device);
     free_numeric(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->main_stream) cudaStreamDestroy(h->main_stream);
     if (h->side_stream) cudaStreamDestroy(h->side_stream);
     if (h->third_stream) cudaStreamDestroy(h->third_stream);
     cudaFree(h->dsym);

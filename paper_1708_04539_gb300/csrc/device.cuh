@@ -191,7 +191,7 @@ cudaError_t prepare_ozaki_kernels();
 void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bool maxima,
                   cudaStream_t st);
 void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
-                       cudaStream_t st);
+                       bool persistent, cudaStream_t st);
 void launch_zero(const CopySeg* segs, int nseg, cudaStream_t st);
 // a kernel whose only wait never completes: it gives up after budget_ns and
 // records DEV_TIMEOUT in err[0]

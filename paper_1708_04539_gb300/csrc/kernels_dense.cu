@@ -350,10 +350,11 @@ void launch_tri_inv(int dtype, const SymDev& S, const void* store, void* out,
                     const int64_t* wofs, const SnTask* tasks, int ntasks, int, int small,
                     cudaStream_t st) {
   if (ntasks <= 0) return;
+  // one task (or one warp's task) per CTA: the launches often run on a
+  // low-priority stream, and short CTAs let the sweep's CTAs in between
   if (small) {
     const int warps = kThreads / 32;
-    const int blocks = (ntasks + warps - 1) / warps;
-    const int grid = blocks < 152 * 8 ? blocks : 152 * 8;
+    const int grid = (ntasks + warps - 1) / warps;
     if (dtype == DT_F64)
       tri_inv_small_kernel<double><<<grid, kThreads, 0, st>>>(S, (const double*)store,
                                                               (double*)out, wofs, tasks, ntasks);
@@ -362,7 +363,7 @@ void launch_tri_inv(int dtype, const SymDev& S, const void* store, void* out,
                                                                (cdouble*)out, wofs, tasks, ntasks);
     return;
   }
-  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  const int grid = ntasks;
   if (dtype == DT_F64)
     tri_inv_kernel<double><<<grid, kThreads, 0, st>>>(S, (const double*)store, (double*)out, wofs,
                                                       tasks, ntasks);

@@ -571,10 +571,12 @@ void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bo
 }
 
 void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
-                       cudaStream_t st) {
+                       bool persistent, cudaStream_t st) {
   if (ntasks <= 0) return;
-  // one CTA fits an SM (shared memory and tensor memory): persistent grid
-  const int grid = ntasks < 152 ? ntasks : 152;
+  // one CTA fits an SM (shared memory and tensor memory): a persistent grid
+  // on the sweep's stream; one task per CTA on the normalisation stream, so
+  // that its CTAs leave SMs to the sweep between tasks
+  const int grid = persistent && ntasks > 152 ? 152 : ntasks;
   switch (S) {
     case 4: ozaki_gemm_kernel<4><<<grid, kOzThreads, gemm_smem<4>(), st>>>(descs, tasks, ntasks, err); break;
     case 5: ozaki_gemm_kernel<5><<<grid, kOzThreads, gemm_smem<5>(), st>>>(descs, tasks, ntasks, err); break;
