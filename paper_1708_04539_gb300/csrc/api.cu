@@ -42,7 +42,6 @@ int cuda_status(cudaError_t e) {
 enum StepKind {
   ST_GEMM,
   ST_TRI_INV,
-  ST_DIAG_LU,
   ST_GATHER,
   ST_SCATTER_SUB,
   ST_COPY,
@@ -50,7 +49,8 @@ enum StepKind {
   ST_SCATTER_VALUES,
   ST_SLICE,
   ST_OZGEMM,
-  ST_ZERO
+  ST_ZERO,
+  ST_LU_PANEL
 };
 
 struct Step {
@@ -498,12 +498,39 @@ int build_factor_plan(pselinv_ctx* h) {
           }
         segs.push_back({TL, Lp, 2 * c * s});
       }
-    Step d;
-    d.kind = ST_DIAG_LU;
-    d.n = (int)diag.size();
-    d.tasks = P.push(diag);
-    d.level = (int)lev;
-    P.steps.push_back(d);
+    // blocked LU of the diagonal blocks: panels of 32 columns, each a panel
+    // launch (pivot block, L21 rows, U12 columns) and a trailing-update GEMM,
+    // batched over the level's supernodes
+    int64_t smax = 0;
+    for (const SnTask& t : diag) smax = std::max<int64_t>(smax, H.sn_width[t.K]);
+    for (int64_t j0 = 0; j0 < smax; j0 += 32) {
+      std::vector<SnTask> piv, pan;
+      std::vector<GemmDesc> upd;
+      for (const SnTask& t : diag) {
+        const int64_t s = H.sn_width[t.K];
+        if (s <= j0) continue;
+        const int64_t w = std::min<int64_t>(32, s - j0), rest = s - j0 - w;
+        const int nbk = (int)ceil_div(rest, 32);
+        piv.push_back({t.inst, t.K, (int)j0, 0});
+        for (int blk = 1; blk <= 2 * nbk; blk++) pan.push_back({t.inst, t.K, (int)j0, blk});
+        if (rest > 0) {
+          char* D = h->lu + ((size_t)t.inst * H.storage + H.sn_offset[t.K]) * es;
+          upd.push_back(make_desc(D + (size_t)(j0 + w + j0 * s) * es, D + (size_t)(j0 + (j0 + w) * s) * es,
+                                  D + (size_t)((j0 + w) + (j0 + w) * s) * es, (int)rest, (int)rest,
+                                  (int)w, (int)s, (int)s, (int)s, 0, 0, -1.0, 1.0));
+        }
+      }
+      for (const auto* list : {&piv, &pan}) {
+        if (list->empty()) continue;
+        Step d;
+        d.kind = ST_LU_PANEL;
+        d.n = (int)list->size();
+        d.tasks = P.push(*list);
+        d.level = (int)lev;
+        P.steps.push_back(d);
+      }
+      add_gemm_step(P, dt, GEMM_32x32, upd, (int)lev);
+    }
     add_tri_step(P, H, tri, (int)lev, 0);
     add_gemm_step(P, dt, cfg, trsm, (int)lev);
     add_gemm_step(P, dt, cfg, schur, (int)lev);
@@ -1019,8 +1046,8 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       launch_tri_inv(h->dtype, h->S, h->lu, h->scratch, (const int64_t*)(a + s.offs),
                      (const SnTask*)(a + s.tasks), s.n, h->max_width, s.cfg, st);
       break;
-    case ST_DIAG_LU:
-      launch_diag_lu(h->dtype, h->S, h->lu, (const SnTask*)(a + s.tasks), s.n, st);
+    case ST_LU_PANEL:
+      launch_lu_panel(h->dtype, h->S, h->lu, (const SnTask*)(a + s.tasks), s.n, st);
       break;
     case ST_GATHER:
       launch_gather(h->dtype, h->S, h->ainv, h->scratch, (const int64_t*)(a + s.offs),
@@ -1272,7 +1299,7 @@ int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, v
   if (h->H.nnz > 0)
     CK(cudaMemcpyAsync(h->staging, values, (size_t)nbatch * h->H.nnz * es, cudaMemcpyDefault, st));
   CK(cudaMemsetAsync(h->derr, 0, 4 * sizeof(int), st));
-  int rc = run_plan(h, h->factor_plan, st, false);
+  int rc = run_plan(h, h->factor_plan, st, h->opts.use_graph != 0);
   if (rc != PSELINV_OK) return rc;
   rc = read_device_error(h, st);
   if (rc != PSELINV_OK) return rc;
@@ -1423,10 +1450,11 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
     }
     out[i].start_ms = t0;
     const Step& s = P.steps[i];
-    static const int kinds[] = {PSELINV_STEP_GEMM,    PSELINV_STEP_TRI_INV,    PSELINV_STEP_DIAG_LU,
+    static const int kinds[] = {PSELINV_STEP_GEMM,    PSELINV_STEP_TRI_INV,
                                 PSELINV_STEP_GATHER,  PSELINV_STEP_SCATTER_SUB, PSELINV_STEP_COPY,
                                 PSELINV_STEP_MEMSET,  PSELINV_STEP_SCATTER_VALUES,
-                                PSELINV_STEP_SLICE,   PSELINV_STEP_OZAKI_GEMM, PSELINV_STEP_MEMSET};
+                                PSELINV_STEP_SLICE,   PSELINV_STEP_OZAKI_GEMM, PSELINV_STEP_MEMSET,
+                                PSELINV_STEP_DIAG_LU};
     out[i].kind = kinds[s.kind];
     out[i].level = s.level;
     out[i].tasks = s.n;

@@ -212,9 +212,10 @@ int gemm_tile_n(int dtype, int cfg);
 // value scatter (A's entries into the storage of every instance)
 void launch_scatter_values(int dtype, const SymDev& S, const void* values, void* store,
                            int nbatch, cudaStream_t st);
-// in-place LU of the diagonal blocks (no pivoting); tasks: {inst, K}
-void launch_diag_lu(int dtype, const SymDev& S, void* store, const SnTask* tasks, int ntasks,
-                    cudaStream_t st);
+// one panel step of the blocked diagonal LU: tasks {inst, K, j0, blk}
+// (blk 0: pivot block, 1..nb: rows of L21, nb+1..2nb: columns of U12)
+void launch_lu_panel(int dtype, const SymDev& S, void* store, const SnTask* tasks, int ntasks,
+                     cudaStream_t st);
 // triangular inverses of the diagonal blocks of `store`:
 // tasks {inst, K, which (0 = L unit lower, 1 = U upper), first column of a
 // panel of 8 columns}; small = 1: blocks of width <= 32, one task per

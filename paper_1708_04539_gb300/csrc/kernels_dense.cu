@@ -1,7 +1,7 @@
 // Dense block kernels in FP64 / complex128:
 //   * a batched, persistent GEMM over a task list (the block products of
 //     Algorithm 1 steps 2-5 and of the supernodal LU),
-//   * the in-place LU without pivoting of diagonal blocks,
+//   * the panel steps of the blocked LU without pivoting of diagonal blocks,
 //   * triangular inverses of the diagonal blocks (one warp per column).
 //
 // On GB300 the FP64 rate is the same for DFMA and the FP64 MMA path (about
@@ -106,32 +106,104 @@ gemm_kernel(const GemmDesc* __restrict__ descs, const GemmTask* __restrict__ tas
   }
 }
 
-// In-place LU without pivoting of the s x s diagonal block of supernode K
-// (right-looking, one CTA per block): L_KK unit lower below the diagonal,
-// U_KK on and above it.
+// Panel step of the blocked LU without pivoting of the s x s diagonal
+// block of a supernode (right-looking, panels of 32 columns; the trailing
+// update A22 -= L21 U12 is a GEMM launch of its own).  Task {inst, K, j0,
+// blk} with w = min(32, s - j0) and nb = number of 32-blocks below the
+// pivot block: blk = 0 factors the w x w pivot block at (j0, j0) in shared
+// memory and writes it back (a launch of its own, before the others read
+// it); blk in [1, nb] solves the 32 rows j0 + w + 32 (blk - 1) .. of
+// L21 = A21 U11^{-1}, blk in [nb + 1, 2 nb] the 32 columns of
+// U12 = L11^{-1} A12.  One division per pivot and CTA.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-diag_lu_kernel(SymDev S, T* store, const SnTask* __restrict__ tasks, int ntasks) {
+lu_panel_kernel(SymDev S, T* store, const SnTask* __restrict__ tasks, int ntasks) {
+  __shared__ T Dd[32][33];
+  __shared__ T R[32];
+  __shared__ T X[32][33];
+  const int tid = threadIdx.x;
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const SnTask task = tasks[t];
     const int K = task.K;
     const int s = S.sn_width[K];
+    const int j0 = task.a, blk = task.b;
+    const int w = min(32, s - j0);
     T* D = store + (int64_t)task.inst * S.storage + S.sn_off[K];
-    for (int k = 0; k < s; k++) {
-      const T piv = D[k + (int64_t)k * s];
-      if (is_zero(piv)) {
-        if (threadIdx.x == 0) set_error(S.err, DEV_ZERO_PIVOT, S.sn_first[K] + k);
-        break;  // uniform across the block: every thread read the same pivot
+    for (int e = tid; e < w * w; e += kThreads) {
+      const int i = e % w, j = e / w;
+      Dd[i][j] = D[(j0 + i) + (int64_t)(j0 + j) * s];
+    }
+    __syncthreads();
+    const int nb = (s - j0 - w + 31) / 32;
+    if (blk == 0) {
+      for (int k = 0; k < w; k++) {
+        if (tid == 0) {
+          const T piv = Dd[k][k];
+          if (is_zero(piv)) set_error(S.err, DEV_ZERO_PIVOT, S.sn_first[K] + j0 + k);
+          R[k] = div_s(sc_one(T()), piv);
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < w; i += kThreads) Dd[i][k] = mul_s(Dd[i][k], R[k]);
+        __syncthreads();
+        const int m = w - k - 1;
+        for (int e = tid; e < m * m; e += kThreads) {
+          const int i = k + 1 + e % m, j = k + 1 + e / m;
+          Dd[i][j] = sub_s(Dd[i][j], mul_s(Dd[i][k], Dd[k][j]));
+        }
+        __syncthreads();
       }
-      for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x)
-        D[i + (int64_t)k * s] = div_s(D[i + (int64_t)k * s], piv);
-      __syncthreads();
-      const int m = s - k - 1;
-      for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-        const int i = k + 1 + idx % m, j = k + 1 + idx / m;
-        D[i + (int64_t)j * s] = sub_s(D[i + (int64_t)j * s], mul_s(D[i + (int64_t)k * s], D[k + (int64_t)j * s]));
+      for (int e = tid; e < w * w; e += kThreads) {
+        const int i = e % w, j = e / w;
+        D[(j0 + i) + (int64_t)(j0 + j) * s] = Dd[i][j];
       }
       __syncthreads();
+      continue;
+    }
+    // the pivot block is factored already: L11 below, U11 on and above
+    if (tid < w) R[tid] = div_s(sc_one(T()), Dd[tid][tid]);
+    __syncthreads();
+    if (blk <= nb) {
+      // rows of L21: X U11 = A21, one column of X at a time
+      const int r0 = j0 + w + 32 * (blk - 1), nr = min(32, s - r0);
+      for (int e = tid; e < nr * w; e += kThreads) {
+        const int i = e % nr, j = e / nr;
+        X[i][j] = D[(r0 + i) + (int64_t)(j0 + j) * s];
+      }
+      __syncthreads();
+      for (int j = 0; j < w; j++) {
+        for (int i = tid; i < nr; i += kThreads) X[i][j] = mul_s(X[i][j], R[j]);
+        __syncthreads();
+        const int m = w - j - 1;
+        for (int e = tid; e < nr * m; e += kThreads) {
+          const int i = e % nr, kk = j + 1 + e / nr;
+          X[i][kk] = sub_s(X[i][kk], mul_s(X[i][j], Dd[j][kk]));
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < nr * w; e += kThreads) {
+        const int i = e % nr, j = e / nr;
+        D[(r0 + i) + (int64_t)(j0 + j) * s] = X[i][j];
+      }
+    } else {
+      // columns of U12: L11 Y = A12 (unit lower), one row of Y at a time
+      const int c0 = j0 + w + 32 * (blk - nb - 1), nc = min(32, s - c0);
+      for (int e = tid; e < w * nc; e += kThreads) {
+        const int i = e % w, j = e / w;
+        X[i][j] = D[(j0 + i) + (int64_t)(c0 + j) * s];
+      }
+      __syncthreads();
+      for (int k = 0; k < w - 1; k++) {
+        const int m = w - k - 1;
+        for (int e = tid; e < m * nc; e += kThreads) {
+          const int i = k + 1 + e % m, j = e / m;
+          X[i][j] = sub_s(X[i][j], mul_s(Dd[i][k], X[k][j]));
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < w * nc; e += kThreads) {
+        const int i = e % w, j = e / w;
+        D[(j0 + i) + (int64_t)(c0 + j) * s] = X[i][j];
+      }
     }
     __syncthreads();
   }
@@ -334,14 +406,13 @@ void launch_gemm(int dtype, int cfg, const GemmDesc* descs, const GemmTask* task
   }
 }
 
-void launch_diag_lu(int dtype, const SymDev& S, void* store, const SnTask* tasks, int ntasks,
-                    cudaStream_t st) {
+void launch_lu_panel(int dtype, const SymDev& S, void* store, const SnTask* tasks, int ntasks,
+                     cudaStream_t st) {
   if (ntasks <= 0) return;
-  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
   if (dtype == DT_F64)
-    diag_lu_kernel<double><<<grid, kThreads, 0, st>>>(S, (double*)store, tasks, ntasks);
+    lu_panel_kernel<double><<<ntasks, kThreads, 0, st>>>(S, (double*)store, tasks, ntasks);
   else
-    diag_lu_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (cdouble*)store, tasks, ntasks);
+    lu_panel_kernel<cdouble><<<ntasks, kThreads, 0, st>>>(S, (cdouble*)store, tasks, ntasks);
 }
 
 cudaError_t prepare_dense_kernels(int, int) { return cudaSuccess; }
