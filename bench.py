@@ -64,6 +64,8 @@ def parse():
                          "(profiling runs: timings under a profiler would mislead the tuner)")
     ap.add_argument("--dump-profile", default=None,
                     help="write the launch-by-launch profile (JSON) to this path")
+    ap.add_argument("--split-normalise", action="store_true",
+                    help="also slice the normalisation and D_K (by default they stay FP64)")
     ap.add_argument("--size", type=int, default=40,
                     help="grid side (40 = the benchmark workload; smaller for profiling captures)")
     return ap.parse_args()
@@ -403,7 +405,8 @@ def run_ours(args):
     workload = WORKLOAD if args.size == 40 else WORKLOAD.replace(
         "40^3 (n=64000)", f"{args.size}^3 (n={args.size ** 3})")
     sched = ps.SCHED_PER_SUPERNODE if args.schedule == "per_supernode" else ps.SCHED_LEVEL
-    h = ps.SelInv.from_problem(p, relax_pct=20, schedule=sched, use_graph=not args.no_graph)
+    h = ps.SelInv.from_problem(p, relax_pct=20, schedule=sched, use_graph=not args.no_graph,
+                               split_normalise=args.split_normalise)
     st = h.structure()
     flops = float(st["flops_selinv_exact"])
     stream = torch.cuda.Stream()
@@ -516,6 +519,7 @@ def run_ours(args):
                    "supernodes": int(st["nsuper"]), "levels": int(st["nlevels"]),
                    "flops_per_matrix": flops, "flops_relaxed_structure": st["flops_selinv"],
                    "schedule": args.schedule, "cuda_graph": not args.no_graph,
+                   "normalisation": "split" if args.split_normalise else "fp64",
                    "tuning": tuning, "tuning_seconds": tune_s,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.0f MB of factors read per step)"

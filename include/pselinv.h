@@ -83,7 +83,12 @@ typedef struct pselinv_opts {
   int32_t tile_plan;     /* 0 = built-in heuristic, 1 = tuned plan (pselinv_tune), 2 = learned model */
   int32_t host_only;     /* 1: pselinv_analyze makes no CUDA call (structure inspection only;
                             the handle then refuses pselinv_factor) */
-  int32_t reserved[7];
+  int32_t split_normalise; /* PREC_OZAKI_FP16 only.  0 (default): the normalisation (Lhat,
+                            Uhat^T, Algorithm 1 step 2) and D_K = U_KK^{-1} L_KK^{-1} stay in
+                            FP64 like the triangular inverses and the final Ainv_KK
+                            combination; 1: in split levels they are sliced products too
+                            (faster, one more rounding stage) */
+  int32_t reserved[6];
 } pselinv_opts;
 
 typedef struct pselinv_ctx* pselinv_t;

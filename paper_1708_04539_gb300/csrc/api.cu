@@ -971,7 +971,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       mode = tuned_value(h, precision, (int)lev, 3, lf < 2e8 ? 1 : 0);
     }
     const bool split_level = precision == PSELINV_PREC_OZAKI_FP16 && mode == 0;
-    add_normalize((int)lev, split_level);
+    add_normalize((int)lev, split_level && h->opts.split_normalise != 0);
     const size_t first_main = P.steps.size();
     // groups: the whole level, or one supernode at a time
     std::vector<std::vector<int64_t>> groups;
@@ -1218,6 +1218,7 @@ void pselinv_default_opts(pselinv_opts* o) {
   o->check_level = 0;
   o->tile_plan = 0;
   o->host_only = 0;
+  o->split_normalise = 0;
 }
 
 const char* pselinv_error_string(int status) {

@@ -24,10 +24,20 @@ def torch():
     return _t
 
 
-def run_split(torch, p, slices=0, **kw):
+def force_split(h):
+    """Every level on the sliced products (the default keeps small levels in
+    FP64), so that the small test matrices exercise the tensor-core path."""
+    import paper_1708_04539_gb300 as ps
+    nlev = h.structure()["nlevels"]
+    h.plan_set([(lev, 3, 0) for lev in range(nlev)], ps.PREC_OZAKI_FP16)
+
+
+def run_split(torch, p, slices=0, all_levels=True, **kw):
     import paper_1708_04539_gb300 as ps
     h = ps.SelInv.from_problem(p, slices=slices, **kw)
     h.factor(torch.from_numpy(np.ascontiguousarray(p.values)).cuda())
+    if all_levels:
+        force_split(h)
     h.selinv(precision=ps.PREC_OZAKI_FP16)
     st = h.structure()
     sn = h.get_selected(layout=ps.LAYOUT_SUPERNODAL)
@@ -57,6 +67,22 @@ def test_split_matches_oracle(torch, name, maker):
     # and the FP64 path of the same handle
     scale = np.abs(sn64).max()
     assert np.abs(sn - sn64).max() <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("name,maker", CASES[1:4], ids=[c[0] for c in CASES[1:4]])
+def test_split_normalise_option_matches_oracle(torch, name, maker):
+    """Option: Lhat, Uhat^T and D_K as sliced products as well."""
+    p = maker()
+    st, sn, pa, sn64 = run_split(torch, p, split_normalise=True)
+    compare_full(p, st, sn, 0, 20, tol=TOL_SPLIT)
+    assert np.abs(sn - sn64).max() <= 1e-9 * np.abs(sn64).max()
+
+
+def test_default_level_mix_matches_oracle(torch):
+    """The default per-level choice (small levels in FP64, the rest split)."""
+    p = gen.upwind_3d(20, 72, max_sn=256)
+    st, sn, pa, sn64 = run_split(torch, p, all_levels=False)
+    compare_full(p, st, sn, 0, 20, tol=TOL_SPLIT)
 
 
 @pytest.mark.parametrize("slices,bound", [(5, 1e-8), (4, 1e-6)])
@@ -97,6 +123,7 @@ def test_split_complex_shift_batch(torch):
     p = gen.shifted_family(7, 71, nshift=4, max_sn=64)
     h = ps.SelInv.from_problem(p)
     h.factor(torch.from_numpy(p.values).cuda())
+    force_split(h)
     h.selinv(precision=ps.PREC_OZAKI_FP16)
     st = h.structure()
     for b in range(p.nbatch):
@@ -108,7 +135,7 @@ def test_split_complex_shift_batch(torch):
 @pytest.mark.slow
 def test_split_config2_full_size(torch):
     p = gen.make_config(2)
-    st, sn, pa, sn64 = run_split(torch, p)
+    st, sn, pa, sn64 = run_split(torch, p, all_levels=False)
     from paper_1708_04539_gb300.binding import supernodal_coordinates
     from helpers import selected_error
     rows, cols = supernodal_coordinates(st)
