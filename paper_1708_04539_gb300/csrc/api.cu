@@ -623,7 +623,7 @@ void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool
                      int ks, int slot) {
   if (descs.empty()) return;
   std::vector<OzTask> tasks;
-  double flops = 0;
+  double flops = 0, bytes = 0;
   for (size_t d = 0; d < descs.size(); d++) {
     OzDesc& g = descs[d];
     g.ksplit = std::max(min_ozaki_ksplit(g), std::min(ks, std::max(1, ceil_div(g.K32, kOzChunkBlocks))));
@@ -632,10 +632,15 @@ void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool
       for (int tn = 0; tn < ceil_div(g.N, 64); tn++)
         for (int tm = 0; tm < ceil_div(g.M, 128); tm++) tasks.push_back({(int)d, tm, tn, k});
     flops += 2.0 * g.M * g.N * (double)g.K32 * 32;
+    // slices of both operands read once, the FP64 result written (read too
+    // when accumulated)
+    bytes += 2.0 * S * ((double)g.M + g.N) * g.K32 * 32 +
+             8.0 * g.M * g.N * (g.atomic ? 2.0 : 1.0) * g.cscale;
   }
   Step st;
   st.kind = ST_OZGEMM;
   st.cfg = S;
+  st.bytes = (size_t)bytes;
   st.n = (int)tasks.size();
   st.descs = P.push(descs);
   st.tasks = P.push(tasks);
