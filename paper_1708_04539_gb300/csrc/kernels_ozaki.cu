@@ -291,7 +291,7 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 // ---------------------------------------------------------------------------
 // sliced GEMM: one 128 x 64 output tile (and one K range) per task,
 // persistent CTAs with three roles
-//   warp 8 (one lane): bulk copies of the slice tiles into a 3-stage ring,
+//   warp 8 (one lane): bulk copies of the slice tiles into a 2-stage ring,
 //   warp 9 (one lane): the tcgen05 MMAs of every stage into the S
 //     accumulators; a commit frees the stage, another marks a chunk done,
 //   warps 0-7: drain each finished chunk (warp w owns TMEM lanes = output
@@ -300,7 +300,7 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 //     after the last chunk, write the outputs while the MMAs of the next
 //     task already run.
 // ---------------------------------------------------------------------------
-constexpr int kOzStages = 3;
+constexpr int kOzStages = 2;
 constexpr int kOzDrainWarps = 8;
 constexpr int kOzThreads = (kOzDrainWarps + 2) * 32;
 
