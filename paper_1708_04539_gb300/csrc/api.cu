@@ -619,15 +619,28 @@ int choose_ozaki_ksplit(const std::vector<OzDesc>& descs) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, kmax));
 }
 
+// K split of each product: the requested one, but at least enough to keep
+// every task within kOzMaxChunks exact chunks; a split product accumulates
+// with atomics.  Returns whether any product accumulates (then its output
+// must hold zeros or the value it accumulates onto before the launch).
+bool set_ozaki_ksplit(std::vector<OzDesc>& descs, int ks, bool force_atomic) {
+  bool any = false;
+  for (OzDesc& g : descs) {
+    g.ksplit = std::max(min_ozaki_ksplit(g), std::min(ks, std::max(1, ceil_div(g.K32, kOzChunkBlocks))));
+    g.atomic = (force_atomic || g.ksplit > 1) ? 1 : 0;
+    any = any || g.atomic;
+  }
+  return any;
+}
+
 void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool force_atomic,
                      int ks, int slot) {
   if (descs.empty()) return;
   std::vector<OzTask> tasks;
   double flops = 0, bytes = 0;
+  set_ozaki_ksplit(descs, ks, force_atomic);
   for (size_t d = 0; d < descs.size(); d++) {
     OzDesc& g = descs[d];
-    g.ksplit = std::max(min_ozaki_ksplit(g), std::min(ks, std::max(1, ceil_div(g.K32, kOzChunkBlocks))));
-    g.atomic = (force_atomic || g.ksplit > 1) ? 1 : 0;
     for (int k = 0; k < g.ksplit; k++)
       for (int tn = 0; tn < ceil_div(g.N, 64); tn++)
         for (int tm = 0; tm < ceil_div(g.M, 128); tm++) tasks.push_back({(int)d, tm, tn, k});
@@ -870,7 +883,9 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   const int ks_diag = tuned_value(h, prec, lev, 2, choose_ozaki_ksplit(dg));
   add_slice_step(P, mx1, lev, true);
   add_slice_step(P, sl1, lev, false);
-  if (ks_main > 1) add_zero_step(P, zero, lev);
+  // outputs of products split along K (requested, or forced by the exact
+  // chunk limit) are accumulated: zero them first
+  if (set_ozaki_ksplit(main, ks_main, false)) add_zero_step(P, zero, lev);
   add_ozgemm_step(P, main, S, lev, false, ks_main, 1);
   add_slice_step(P, sl2, lev, true);
   add_slice_step(P, sl2, lev, false);
