@@ -34,6 +34,14 @@ METRIC = "selinv_fp64_equiv_gflops"
 UNIT = "GFLOP/s"
 WORKLOAD = ("3D 7-point upwind convection-diffusion 40^3 (n=64000), FP64, nested dissection, "
             "max supernode 256, relaxed supernodes (<=20% explicit zeros)")
+OTHER_WORKLOADS = {
+    3: "3D 27-point complex operator A = H - zS + 0.2N on a {m}^3 grid (n={n}), complex128, "
+       "nested dissection, max supernode 256",
+    4: "pole-expansion batch: 40 complex shifts of a 3D 7-point {m}^3 operator (n={n}), "
+       "complex128, one sweep for all shifts, max supernode 256",
+    5: "block-sparse DG operator: {m}^3 elements x 64 unknowns (n={n}), dense element and "
+       "upwind face blocks, FP64, nested dissection on the element grid, max supernode 256",
+}
 # FP64 DFMA pipe of GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz max SM clock
 FP64_ALU_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 SAMPLE_TARGET_N = 4000  # unknowns of the leading nested-dissection subdomain timed on the CPU
@@ -66,8 +74,12 @@ def parse():
                     help="write the launch-by-launch profile (JSON) to this path")
     ap.add_argument("--split-normalise", action="store_true",
                     help="also slice the normalisation and D_K (by default they stay FP64)")
-    ap.add_argument("--size", type=int, default=40,
-                    help="grid side (40 = the benchmark workload; smaller for profiling captures)")
+    ap.add_argument("--size", type=int, default=None,
+                    help="grid side (default: the configuration's own; 40 for the benchmark "
+                         "workload; smaller for profiling captures)")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
+                    help="2: 40^3 upwind (the benchmark workload); 3: 60^3 complex 27-point; "
+                         "4: 40 complex shifts of a 32^3 operator; 5: 16^3 x 64 DG operator")
     return ap.parse_args()
 
 
@@ -304,11 +316,23 @@ def comparison(p, h, stream, out_dev, flops):
         g.factor(torch.from_numpy(p.values).cuda(), stream=stream)
     per_sn_ms = time_steps(g, ps.PREC_FP64, stream, 2, out_dev)
     g.close()
+    # option: normalisation and D_K as sliced products too
+    q = ps.SelInv.from_problem(p, relax_pct=20, split_normalise=True)
+    with torch.cuda.stream(stream):
+        q.factor(torch.from_numpy(p.values).cuda(), stream=stream)
+        q.tune(precision=ps.PREC_OZAKI_FP16, mode=ps.TUNE_EXHAUSTIVE, stream=stream)
+    sn_ms = time_steps(q, ps.PREC_OZAKI_FP16, stream, 5, out_dev)
+    sn_err = selected_error(q.get_selected(layout=ps.LAYOUT_SUPERNODAL, stream=stream), ref,
+                            rows, cols, p.n)
+    q.close()
     return {"fp64_level_batched_ms": fp64_level_ms,
             "fp64_level_batched_gflops": flops / (fp64_level_ms * 1e-3) / 1e9,
             "fp64_per_supernode_ms": per_sn_ms,
             "fp64_per_supernode_gflops": flops / (per_sn_ms * 1e-3) / 1e9,
             "split_vs_fp64_selected_error": err, "split_vs_fp64_normwise_error": normwise,
+            "split_normalise_option_ms": sn_ms,
+            "split_normalise_option_gflops": flops / (sn_ms * 1e-3) / 1e9,
+            "split_normalise_option_error": sn_err,
             "error_metric": "max |x - r| / max(max_k |r_ik|, max_k |r_kj|) over every entry "
                             "of the pattern of L+U; r = FP64 GPU result"}
 
@@ -401,17 +425,28 @@ def run_ours(args):
         dist.barrier()
     ps.load_library()
 
-    p = gen.make_config(2, size=args.size)
-    workload = WORKLOAD if args.size == 40 else WORKLOAD.replace(
-        "40^3 (n=64000)", f"{args.size}^3 (n={args.size ** 3})")
+    p = gen.make_config(args.config, size=args.size)
+    if args.config == 4:
+        p = p[0]  # the shift family (the uneven grids are a parity case)
+    size = args.size or {2: 40, 3: 60, 4: 32, 5: 16}[args.config]
+    if args.config == 2:
+        workload = WORKLOAD if size == 40 else WORKLOAD.replace(
+            "40^3 (n=64000)", f"{size}^3 (n={size ** 3})")
+    else:
+        workload = OTHER_WORKLOADS[args.config].format(m=size, n=p.n)
+    cplx = np.iscomplexobj(p.values)
+    nbatch = p.nbatch
+    headline = args.config == 2
     sched = ps.SCHED_PER_SUPERNODE if args.schedule == "per_supernode" else ps.SCHED_LEVEL
     h = ps.SelInv.from_problem(p, relax_pct=20, schedule=sched, use_graph=not args.no_graph,
                                split_normalise=args.split_normalise)
     st = h.structure()
-    flops = float(st["flops_selinv_exact"])
+    # FP64-equivalent flops of one sweep over every instance (x4 for complex)
+    flops = float(st["flops_selinv_exact"]) * (4.0 if cplx else 1.0) * nbatch
     stream = torch.cuda.Stream()
     vals_dev = torch.from_numpy(p.values).cuda()
-    out_dev = torch.zeros(p.nnz, dtype=torch.float64, device="cuda")
+    odt = torch.complex128 if cplx else torch.float64
+    out_dev = torch.zeros((nbatch, p.nnz), dtype=odt, device="cuda")
 
     # factorisation (timed separately)
     with torch.cuda.stream(stream):
@@ -438,12 +473,13 @@ def run_ours(args):
         tune_s = time.perf_counter() - t0
     if args.plan_out:
         with open(args.plan_out, "w") as f:
-            json.dump({"precision": args.precision, "size": args.size,
+            json.dump({"precision": args.precision, "config": args.config, "size": size,
                        "triples": h.plan_get(prec)}, f)
 
     def step():
         h.selinv(precision=prec, stream=stream)
-        h.get_selected(out_dev, stream=stream)
+        for b in range(nbatch):
+            h.get_selected(out_dev[b], batch=b, stream=stream)
 
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
@@ -477,7 +513,7 @@ def run_ours(args):
             h.profile(2, stream=stream)  # warm the multi-stream timeline once
             timeline = h.profile(2, stream=stream)
         with open(args.dump_profile, "w") as f:
-            json.dump({"precision": args.precision, "size": args.size, "steps": prof,
+            json.dump({"precision": args.precision, "config": args.config, "size": size, "steps": prof,
                        "factor_steps": fprof, "timeline": timeline}, f)
 
     # end to end through the C ABI with host buffers: H2D values, factor,
@@ -485,24 +521,28 @@ def run_ours(args):
     e2e = None
     if args.e2e_steps > 0:
         vals_host = torch.from_numpy(p.values.copy()).pin_memory()
-        out_host = torch.zeros(p.nnz, dtype=torch.float64).pin_memory()
-        with torch.cuda.stream(stream):
+        out_host = torch.zeros((nbatch, p.nnz), dtype=odt).pin_memory()
+
+        def e2e_step():
             h.factor(vals_host, stream=stream)
             h.selinv(precision=prec, stream=stream)
-            h.get_selected(out_host, stream=stream)
+            for b in range(nbatch):
+                h.get_selected(out_host[b], batch=b, stream=stream)
+
+        with torch.cuda.stream(stream):
+            e2e_step()
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             for _ in range(args.e2e_steps):
-                h.factor(vals_host, stream=stream)
-                h.selinv(precision=prec, stream=stream)
-                h.get_selected(out_host, stream=stream)
+                e2e_step()
         torch.cuda.synchronize()
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, "cuda")
+        io_bytes = int(p.nnz * nbatch * (16 if cplx else 8))
         e2e = {"value": world * flops / e2e_s / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(p.nnz * 8), "d2h_bytes_per_step": int(p.nnz * 8),
+               "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
                "ms_per_step": e2e_s * 1e3,
                "includes": "H2D values, factor, selinv, extract, D2H"}
 
@@ -512,19 +552,20 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+f16-slices",
+        "dtype": ("c128" if cplx else "f64") + ("" if args.precision == "fp64" else "+f16-slices"),
         "data": "synthetic (seeded generator, nested dissection)",
         "precision": args.precision,
-        "config": {"workload": workload, "n": p.n, "nnz": p.nnz,
+        "config": {"workload": workload, "n": p.n, "nnz": p.nnz, "instances": nbatch,
                    "supernodes": int(st["nsuper"]), "levels": int(st["nlevels"]),
-                   "flops_per_matrix": flops, "flops_relaxed_structure": st["flops_selinv"],
+                   "flops_per_matrix": flops / nbatch,
+                   "flops_relaxed_structure": st["flops_selinv"] * (4.0 if cplx else 1.0),
                    "schedule": args.schedule, "cuda_graph": not args.no_graph,
                    "normalisation": "split" if args.split_normalise else "fp64",
                    "tuning": tuning, "tuning_seconds": tune_s,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.0f MB of factors read per step)"
                          % (st["storage_size"] * 8 / 1e6)},
-        "time_per_matrix_ms": ms_per_step,
+        "time_per_matrix_ms": ms_per_step / nbatch,
         "factor_ms": factor_ms,
         "e2e": e2e,
         "gpu_launches": int((nl + 1) * args.steps),
@@ -535,10 +576,10 @@ def run_ours(args):
     }
     if not prof:
         line["roofline"] = None
-    if not args.no_compare and args.precision == "ozaki" and rank == 0:
-        line["comparison"] = comparison(p, h, stream, out_dev, flops)
+    if not args.no_compare and args.precision == "ozaki" and rank == 0 and headline:
+        line["comparison"] = comparison(p, h, stream, out_dev[0], flops)
     h.close()
-    if rank == 0 and world == 1 and not args.skip_cpu_baseline and args.size == 40:
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline and headline and size == 40:
         line["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:
         print(json.dumps(line))
