@@ -48,28 +48,48 @@ gemm_kernel(const GemmDesc* __restrict__ descs, const GemmTask* __restrict__ tas
     for (int i = 0; i < TM; i++)
 #pragma unroll
       for (int j = 0; j < TN; j++) acc[i][j] = sc_zero(T());
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-      // A tile: BM x BK of op(A)
-      for (int e = tid; e < BM * BK; e += kThreads) {
+    // the next K tile is loaded into registers while the current one is
+    // used from shared memory
+    constexpr int NA = BM * BK / kThreads, NB = BK * BN / kThreads;
+    T ra[NA], rb[NB];
+    auto load_tiles = [&](int k0) {
+#pragma unroll
+      for (int q = 0; q < NA; q++) {
+        const int e = tid + q * kThreads;
         int mm, kk;
         if (d.transA) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
         const int m = m0 + mm, k = k0 + kk;
         T v = sc_zero(T());
         if (m < d.M && k < ke)
           v = d.transA ? A[k + (int64_t)m * d.lda] : A[m + (int64_t)k * d.lda];
-        sm.a[kk][mm] = v;
+        ra[q] = v;
       }
-      // B tile: BK x BN of op(B)
-      for (int e = tid; e < BK * BN; e += kThreads) {
+#pragma unroll
+      for (int q = 0; q < NB; q++) {
+        const int e = tid + q * kThreads;
         int kk, nn;
         if (d.transB) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
         const int n = n0 + nn, k = k0 + kk;
         T v = sc_zero(T());
         if (n < d.N && k < ke)
           v = d.transB ? B[n + (int64_t)k * d.ldb] : B[k + (int64_t)n * d.ldb];
-        sm.b[kk][nn] = v;
+        rb[q] = v;
+      }
+    };
+    if (kb < ke) load_tiles(kb);
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+      for (int q = 0; q < NA; q++) {
+        const int e = tid + q * kThreads;
+        if (d.transA) sm.a[e % BK][e / BK] = ra[q]; else sm.a[e / BM][e % BM] = ra[q];
+      }
+#pragma unroll
+      for (int q = 0; q < NB; q++) {
+        const int e = tid + q * kThreads;
+        if (d.transB) sm.b[e / BN][e % BN] = rb[q]; else sm.b[e % BK][e / BK] = rb[q];
       }
       __syncthreads();
+      if (k0 + BK < ke) load_tiles(k0 + BK);
 #pragma unroll
       for (int kk = 0; kk < BK; kk++) {
         T av[TM], bv[TN];
