@@ -80,7 +80,6 @@ typedef struct pselinv_opts {
   int32_t schedule;      /* pselinv_schedule; default PSELINV_SCHED_LEVEL */
   int32_t use_graph;     /* 1: record the selinv sweep once in a CUDA graph and replay it */
   int32_t check_level;   /* 1: bounds-check every index-map read on the device */
-  int32_t tile_plan;     /* 0 = built-in heuristic, 1 = tuned plan (pselinv_tune), 2 = learned model */
   int32_t host_only;     /* 1: pselinv_analyze makes no CUDA call (structure inspection only;
                             the handle then refuses pselinv_factor) */
   int32_t split_normalise; /* PREC_OZAKI_FP16 only.  0 (default): the normalisation (Lhat,
@@ -88,7 +87,7 @@ typedef struct pselinv_opts {
                             FP64 like the triangular inverses and the final Ainv_KK
                             combination; 1: in split levels they are sliced products too
                             (faster, one more rounding stage) */
-  int32_t reserved[6];
+  int32_t reserved[7];
 } pselinv_opts;
 
 typedef struct pselinv_ctx* pselinv_t;

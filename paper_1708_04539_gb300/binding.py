@@ -59,9 +59,9 @@ class Opts(ctypes.Structure):
     _fields_ = [("max_supernode", ctypes.c_int32), ("relax_pct", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("slices", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("check_level", ctypes.c_int32), ("tile_plan", ctypes.c_int32),
+                ("check_level", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("split_normalise", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 _P64 = ctypes.POINTER(ctypes.c_int64)
@@ -212,7 +212,7 @@ class SelInv:
 
     def __init__(self, n, colptr, rowind, perm=None, max_supernode=256, relax_pct=20,
                  schedule=SCHED_LEVEL, use_graph=True, check_level=0, precision=PREC_FP64,
-                 slices=0, tile_plan=0, host_only=False, split_normalise=False):
+                 slices=0, host_only=False, split_normalise=False):
         lib = load_library()
         self._lib = lib
         opts = Opts()
@@ -224,7 +224,6 @@ class SelInv:
         opts.check_level = int(check_level)
         opts.precision = int(precision)
         opts.slices = int(slices)
-        opts.tile_plan = int(tile_plan)
         opts.host_only = 1 if host_only else 0
         opts.split_normalise = 1 if split_normalise else 0
         self._colptr = np.ascontiguousarray(colptr, dtype=np.int64)

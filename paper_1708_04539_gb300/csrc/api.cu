@@ -357,7 +357,9 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
                   selinv_main_bytes(H, nb, es) + ozaki_norm_bytes(H, nb, 6, es));
 }
 
-int choose_cfg(int dtype) { return dtype == DT_F64 ? GEMM_64x64 : GEMM_64x64; }
+// default FP64 tile config before tuning: 32 x 32 tiles (what the tuner
+// keeps for the normalisation and the FP64 levels of the 40^3 sweep)
+int choose_cfg(int dtype) { return dtype == DT_F64 ? GEMM_32x32 : GEMM_64x64; }
 
 int tuned_value(const pselinv_ctx* h, int prec, int level, int slot, int dflt) {
   auto it = h->tuned.find(std::make_tuple(prec, level, slot));
@@ -461,7 +463,7 @@ int build_factor_plan(pselinv_ctx* h) {
   Step sv;
   sv.kind = ST_SCATTER_VALUES;
   P.steps.push_back(sv);
-  const int cfg = choose_cfg(dt);
+  const int cfg = GEMM_64x64;  // the factor's panel and Schur products are large
   for (size_t lev = 0; lev + 1 < H.hlevel_ptr.size(); lev++) {
     std::vector<SnTask> diag, gt;
     std::vector<TriBlock> tri;
@@ -1236,7 +1238,6 @@ void pselinv_default_opts(pselinv_opts* o) {
   o->schedule = PSELINV_SCHED_LEVEL;
   o->use_graph = 1;
   o->check_level = 0;
-  o->tile_plan = 0;
   o->host_only = 0;
   o->split_normalise = 0;
 }
