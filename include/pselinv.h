@@ -307,6 +307,22 @@ int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int
 int pselinv_plan_get(pselinv_t h, int precision, int32_t* out, int64_t cap, int64_t* count);
 int pselinv_plan_set(pselinv_t h, int precision, const int32_t* in, int64_t count);
 
+/* Pole-expansion consumers of a batch of selected inverses (the use of
+ * selected inversion that motivates the method, Section 1: a density matrix
+ * or an observable as a weighted sum over shifted matrices).  weights: host
+ * array of nbatch scalars of the factored dtype (w_l; complex: interleaved).
+ * Require pselinv_selinv to have run.
+ *   weighted_sum: out[p] = sum_l w_l (A_l^{-1})_{rowind[p], j} for entry p of
+ *     column j of the input pattern (CSC order; out: host or device, nnz
+ *     scalars).
+ *   trace: *out = sum_l w_l Tr[B A_l^{-1}] = sum_l w_l sum_p B[p] (A_l^{-1})_{j, rowind[p]}
+ *     for B on the input pattern (B: nnz scalars in CSC order, host or
+ *     device; out: one scalar, host or device).  The reduction runs in a
+ *     fixed order (the result does not depend on timing).
+ * Host output waits for the stream. */
+int pselinv_weighted_sum(pselinv_t h, const void* weights, void* out, void* stream);
+int pselinv_trace(pselinv_t h, const void* weights, const void* B, void* out, void* stream);
+
 /* Exercise the bounded-wait failure path (not from the paper): launch a
  * kernel whose only wait (on a tensor-core completion barrier) can never
  * complete, with a budget of budget_us microseconds (1 .. 2e6).  Every wait

@@ -30,6 +30,7 @@ _EXPORTS = [
     "pselinv_sync", "pselinv_last_info", "pselinv_error_string", "pselinv_free",
     "pselinv_block_inverse_noalloc", "pselinv_tune", "pselinv_tune_records",
     "pselinv_plan_get", "pselinv_plan_set", "pselinv_wait_selftest",
+    "pselinv_weighted_sum", "pselinv_trace",
     "pselinv_model_create", "pselinv_model_train", "pselinv_model_gradients",
     "pselinv_model_predict", "pselinv_model_get_params", "pselinv_model_set_params",
     "pselinv_model_encode", "pselinv_model_free",
@@ -145,6 +146,10 @@ def load_library():
     lib.pselinv_plan_get.restype = ctypes.c_int
     lib.pselinv_plan_set.argtypes = [P, ctypes.c_int, P, I64]
     lib.pselinv_plan_set.restype = ctypes.c_int
+    lib.pselinv_weighted_sum.argtypes = [P, P, P, P]
+    lib.pselinv_weighted_sum.restype = ctypes.c_int
+    lib.pselinv_trace.argtypes = [P, P, P, P, P]
+    lib.pselinv_trace.restype = ctypes.c_int
     lib.pselinv_model_create.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(P)]
     lib.pselinv_model_create.restype = ctypes.c_int
     lib.pselinv_model_train.argtypes = [P, RP, I64, ctypes.c_int32, ctypes.c_float, P,
@@ -327,6 +332,32 @@ class SelInv:
         buf = (ctypes.c_int32 * max(3, len(flat)))(*flat)
         self._check(self._lib.pselinv_plan_set(self._h, int(precision), buf, len(flat) // 3),
                     "pselinv_plan_set")
+
+    def _weights(self, weights):
+        cplx = self.dtype == C128
+        w = np.ascontiguousarray(weights, dtype=np.complex128 if cplx else np.float64)
+        if w.size != self.nbatch:
+            raise ValueError(f"{w.size} weights for {self.nbatch} instances")
+        return w
+
+    def weighted_sum(self, weights, out=None, stream=None):
+        """sum_l w_l A_l^{-1} on pattern(A), CSC order (a pole-expansion sum)."""
+        w = self._weights(weights)
+        if out is None:
+            out = np.zeros(self.nnz, dtype=w.dtype)
+        self._check(self._lib.pselinv_weighted_sum(self._h, _ptr(w), _ptr(out), _stream(stream)),
+                    "pselinv_weighted_sum")
+        return out
+
+    def trace(self, weights, B, stream=None):
+        """sum_l w_l Tr[B A_l^{-1}] for B given on pattern(A) in CSC order."""
+        w = self._weights(weights)
+        if isinstance(B, np.ndarray):
+            B = np.ascontiguousarray(B, dtype=w.dtype)
+        res = np.zeros(1, dtype=w.dtype)
+        self._check(self._lib.pselinv_trace(self._h, _ptr(w), _ptr(B), _ptr(res), _stream(stream)),
+                    "pselinv_trace")
+        return res[0]
 
     def sync(self, stream=None):
         self._check(self._lib.pselinv_sync(self._h, _stream(stream)), "pselinv_sync")

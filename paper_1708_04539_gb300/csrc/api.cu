@@ -132,6 +132,12 @@ struct pselinv_ctx {
   size_t scratch_bytes = 0;
   char* staging = nullptr;  // nbatch * nnz values
   char* outstage = nullptr; // nnz values
+  // pole-expansion consumers: the input pattern (for transposed entries),
+  // the storage slot of the transposed entry of every input entry, and a
+  // buffer for weights, B and partial sums
+  std::vector<int64_t> colptr_h, rowind_h;
+  int64_t* tslot = nullptr;
+  char* cbuf = nullptr;
   bool factored = false, inverted = false;
   Plan factor_plan;
   Plan selinv_plan[2][2];  // [precision][schedule]
@@ -1193,7 +1199,8 @@ void free_numeric(pselinv_ctx* h) {
   cudaFree(h->scratch);
   cudaFree(h->staging);
   cudaFree(h->outstage);
-  h->lu = h->nf = h->ainv = h->scratch = h->staging = h->outstage = nullptr;
+  cudaFree(h->cbuf);
+  h->lu = h->nf = h->ainv = h->scratch = h->staging = h->outstage = h->cbuf = nullptr;
   h->dtype = 0;
   h->nbatch = 0;
   h->factored = h->inverted = false;
@@ -1274,6 +1281,8 @@ int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind, con
     return rc;
   }
   for (int64_t k = 0; k < h->H.ns; k++) h->max_width = std::max<int>(h->max_width, (int)h->H.sn_width[k]);
+  h->colptr_h.assign(colptr, colptr + n + 1);
+  h->rowind_h.assign(rowind, rowind + colptr[n]);
   if (!h->opts.host_only) {
     if (cudaGetDevice(&h->device) != cudaSuccess) {
       (void)cudaGetLastError();
@@ -1734,6 +1743,74 @@ int pselinv_wait_selftest(void* stream, int64_t budget_us) {
   return herr[0] == DEV_TIMEOUT ? PSELINV_ERR_TIMEOUT : PSELINV_OK;
 }
 
+// weights (host) and, for the trace, B (host or device) into the consumer
+// buffer: [weights: nbatch scalars | B: nnz scalars | partial sums | result]
+static int consumer_stage(pselinv_ctx* h, const void* weights, const void* B, cudaStream_t st) {
+  const size_t es = h->esize, nb = (size_t)h->nbatch, nnz = (size_t)h->H.nnz;
+  if (!h->cbuf) CK(cudaMalloc(&h->cbuf, align256(nb * es) + align256(nnz * es) + trace_partial_bytes() + 256));
+  CK(cudaMemcpyAsync(h->cbuf, weights, nb * es, cudaMemcpyHostToDevice, st));
+  if (B) CK(cudaMemcpyAsync(h->cbuf + align256(nb * es), B, nnz * es, cudaMemcpyDefault, st));
+  return PSELINV_OK;
+}
+
+int pselinv_weighted_sum(pselinv_t h, const void* weights, void* out, void* stream) {
+  if (!h || !weights || !out || !h->inverted) return PSELINV_ERR_ARG;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = consumer_stage(h, weights, nullptr, st);
+  if (rc != PSELINV_OK) return rc;
+  const bool dev = is_device_ptr(out);
+  void* dst = dev ? out : (void*)h->outstage;
+  launch_weighted_sum(h->dtype, h->S, h->ainv, (int)h->nbatch, h->cbuf, dst, st);
+  CK(cudaGetLastError());
+  if (!dev) {
+    CK(cudaMemcpyAsync(out, h->outstage, (size_t)h->H.nnz * h->esize, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return PSELINV_OK;
+}
+
+int pselinv_trace(pselinv_t h, const void* weights, const void* B, void* out, void* stream) {
+  if (!h || !weights || !B || !out || !h->inverted) return PSELINV_ERR_ARG;
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = (int64_t)h->colptr_h.size() - 1, nnz = h->H.nnz;
+  if (!h->tslot) {
+    // transposed entry of every input entry (the pattern is structurally
+    // symmetric), then its storage slot
+    std::vector<int64_t> col(nnz), order(nnz), tslot(nnz);
+    for (int64_t j = 0; j < n; j++)
+      for (int64_t q = h->colptr_h[j]; q < h->colptr_h[j + 1]; q++) col[q] = j;
+    for (int64_t q = 0; q < nnz; q++) order[q] = q;
+    auto key = [&](int64_t q) { return h->rowind_h[q] * n + col[q]; };  // (i, j) -> row-major
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+    for (int64_t q = 0; q < nnz; q++) {
+      // entry q = (i, j): find (j, i), i.e. row-major key j * n + i
+      const int64_t want = col[q] * n + h->rowind_h[q];
+      int64_t lo = 0, hi = nnz;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (key(order[mid]) < want) lo = mid + 1; else hi = mid;
+      }
+      if (lo >= nnz || key(order[lo]) != want) return PSELINV_ERR_NOT_STRUCT_SYM;
+      tslot[q] = h->H.value_map[order[lo]];
+    }
+    CK(cudaMalloc(&h->tslot, (size_t)std::max<int64_t>(nnz, 1) * 8));
+    CK(cudaMemcpy(h->tslot, tslot.data(), (size_t)nnz * 8, cudaMemcpyHostToDevice));
+  }
+  int rc = consumer_stage(h, weights, B, st);
+  if (rc != PSELINV_OK) return rc;
+  const size_t es = h->esize, nb = (size_t)h->nbatch;
+  char* bdev = h->cbuf + align256(nb * es);
+  char* partial = bdev + align256((size_t)nnz * es);
+  char* res = partial + trace_partial_bytes();
+  launch_trace(h->dtype, h->S, h->ainv, (int)h->nbatch, h->cbuf, bdev, h->tslot, partial, res, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, res, es, cudaMemcpyDefault, st));
+  if (!is_device_ptr(out)) CK(cudaStreamSynchronize(st));
+  return PSELINV_OK;
+}
+
 int pselinv_plan_get(pselinv_t h, int precision, int32_t* out, int64_t cap, int64_t* count) {
   if (!h || !count || (cap > 0 && !out) ||
       (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16))
@@ -1806,6 +1883,7 @@ void pselinv_free(pselinv_t h) {
     if (h->third_stream) cudaStreamDestroy(h->third_stream);
     cudaFree(h->dsym);
     cudaFree(h->derr);
+    cudaFree(h->tslot);
   }
   delete h;
 }

@@ -209,6 +209,14 @@ void launch_gemm(int dtype, int cfg, const GemmDesc* descs, const GemmTask* task
 int gemm_tile_m(int dtype, int cfg);
 int gemm_tile_n(int dtype, int cfg);
 
+// out[p] = sum_b w[b] Ainv_b at entry p of pattern(A) (w: nb device scalars)
+void launch_weighted_sum(int dtype, const SymDev& S, const void* store, int nb, const void* w,
+                         void* out, cudaStream_t st);
+// *out = sum_b w[b] sum_p B[p] Ainv_b at tslot[p] (two launches, fixed reduction
+// order; partial: trace_partial_bytes() of device scratch)
+void launch_trace(int dtype, const SymDev& S, const void* store, int nb, const void* w,
+                  const void* B, const int64_t* tslot, void* partial, void* out, cudaStream_t st);
+size_t trace_partial_bytes();
 // value scatter (A's entries into the storage of every instance)
 void launch_scatter_values(int dtype, const SymDev& S, const void* values, void* store,
                            int nbatch, cudaStream_t st);

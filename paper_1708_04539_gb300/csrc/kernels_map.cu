@@ -155,6 +155,61 @@ extract_kernel(SymDev S, const T* __restrict__ store, T* out) {
     out[p] = store[S.value_map[p]];
 }
 
+// Pole-expansion consumers (a weighted sum over the instances of a batch).
+// out[p] = sum_b w_b Ainv_b at entry p of pattern(A).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+weighted_sum_kernel(SymDev S, const T* __restrict__ store, int nb, const T* __restrict__ w,
+                    T* out) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < S.nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t slot = S.value_map[p];
+    T acc = sc_zero(T());
+    for (int b = 0; b < nb; b++) acc = add_s(acc, mul_s(w[b], store[b * S.storage + slot]));
+    out[p] = acc;
+  }
+}
+
+// Partial sums of sum_b w_b sum_p B[p] Ainv_b(j, i) for entry p = (i, j) of
+// pattern(A) (tslot[p] = storage slot of the transposed entry): a fixed grid
+// and a fixed reduction order, so the result does not depend on timing.
+constexpr int kTraceBlocks = 1024;
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+trace_partial_kernel(SymDev S, const T* __restrict__ store, int nb, const T* __restrict__ w,
+                     const T* __restrict__ B, const int64_t* __restrict__ tslot, T* partial) {
+  __shared__ T red[kThreads];
+  T acc = sc_zero(T());
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < S.nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t slot = tslot[p];
+    T x = sc_zero(T());
+    for (int b = 0; b < nb; b++) x = add_s(x, mul_s(w[b], store[b * S.storage + slot]));
+    acc = add_s(acc, mul_s(B[p], x));
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = add_s(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) trace_final_kernel(const T* __restrict__ partial, T* out) {
+  __shared__ T red[kThreads];
+  T acc = sc_zero(T());
+  for (int i = threadIdx.x; i < kTraceBlocks; i += kThreads) acc = add_s(acc, partial[i]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = add_s(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 int grid_for(int64_t n) {
   const int64_t g = (n + kThreads - 1) / kThreads;
   return (int)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
@@ -218,5 +273,32 @@ void launch_extract(int dtype, const SymDev& S, const void* store, int inst, voi
     extract_kernel<cdouble><<<grid_for(S.nnz), kThreads, 0, st>>>(
         S, (const cdouble*)store + (int64_t)inst * S.storage, (cdouble*)out);
 }
+
+void launch_weighted_sum(int dtype, const SymDev& S, const void* store, int nb, const void* w,
+                         void* out, cudaStream_t st) {
+  if (S.nnz == 0) return;
+  if (dtype == DT_F64)
+    weighted_sum_kernel<double><<<grid_for(S.nnz), kThreads, 0, st>>>(
+        S, (const double*)store, nb, (const double*)w, (double*)out);
+  else
+    weighted_sum_kernel<cdouble><<<grid_for(S.nnz), kThreads, 0, st>>>(
+        S, (const cdouble*)store, nb, (const cdouble*)w, (cdouble*)out);
+}
+
+void launch_trace(int dtype, const SymDev& S, const void* store, int nb, const void* w,
+                  const void* B, const int64_t* tslot, void* partial, void* out, cudaStream_t st) {
+  if (dtype == DT_F64) {
+    trace_partial_kernel<double><<<kTraceBlocks, kThreads, 0, st>>>(
+        S, (const double*)store, nb, (const double*)w, (const double*)B, tslot, (double*)partial);
+    trace_final_kernel<double><<<1, kThreads, 0, st>>>((const double*)partial, (double*)out);
+  } else {
+    trace_partial_kernel<cdouble><<<kTraceBlocks, kThreads, 0, st>>>(
+        S, (const cdouble*)store, nb, (const cdouble*)w, (const cdouble*)B, tslot,
+        (cdouble*)partial);
+    trace_final_kernel<cdouble><<<1, kThreads, 0, st>>>((const cdouble*)partial, (cdouble*)out);
+  }
+}
+
+size_t trace_partial_bytes() { return (size_t)kTraceBlocks * 16; }
 
 }  // namespace pselinv
