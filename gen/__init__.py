@@ -18,6 +18,7 @@ from .problems import (  # noqa: F401
     SEED_BASE,
     nd_perm,
     conv_diff_2d,
+    sym_diffusion_3d,
     upwind_3d,
     stencil27_complex,
     shifted_family,

@@ -244,6 +244,39 @@ def upwind_3d(m: int, seed: int, shift: float = 0.1, max_sn: int = 256,
                    nd_perm(dims, max_sn), max_sn, dims)
 
 
+def sym_diffusion_3d(m: int, seed: int, shift: float = 0.1, max_sn: int = 256,
+                     name: str | None = None) -> Problem:
+    """3D 7-point diffusion with symmetric random coefficients (real, A = A^T).
+
+    Each grid edge (i, i + e_d) gets a_{i,i+e_d} = a_{i+e_d,i} = -(1 + u), u ~ U(0,1)
+    drawn per edge; a_ii = sum of |off-diagonals| + shift.
+    """
+    dims = (m, m, m)
+    idx, coords = _coords(dims)
+    n = idx.size
+    rng = _rng(seed, 3)
+    rows, cols, vals = [], [], []
+    offsum = np.zeros(n)
+    for d in range(3):
+        off = [0, 0, 0]
+        off[d] = 1
+        mask, j = _neighbour(dims, coords, off)
+        i = idx[mask]
+        jj = j[mask]
+        w = -(1.0 + rng.uniform(0.0, 1.0, size=i.size))
+        rows += [i, jj]
+        cols += [jj, i]
+        vals += [w, w]
+        np.add.at(offsum, i, np.abs(w))
+        np.add.at(offsum, jj, np.abs(w))
+    rows.append(idx)
+    cols.append(idx)
+    vals.append(offsum + shift)
+    colptr, rowind, v = _to_csc(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+    return Problem(name or f"sym_diffusion_3d_{m}", n, colptr, rowind, v,
+                   nd_perm(dims, max_sn), max_sn, dims)
+
+
 def stencil27_complex(m: int, seed: int, z: complex = 0.5 + 0.1j, eps: float = 0.2,
                       max_sn: int = 256, name: str | None = None) -> Problem:
     """3D 27-point complex operator A = H - z S + eps N on an m^3 grid.

@@ -87,7 +87,13 @@ typedef struct pselinv_opts {
                             FP64 like the triangular inverses and the final Ainv_KK
                             combination; 1: in split levels they are sliced products too
                             (faster, one more rounding stage) */
-  int32_t reserved[7];
+  int32_t symmetric;     /* 1: the values satisfy A = A^T (real symmetric or complex
+                            symmetric, not Hermitian).  Then Uhat = Lhat^T and
+                            Ainv(K, C) = Ainv(C, K)^T: the sweep skips the normalisation
+                            of U, step 5's product (a copy) and the column slicing of G
+                            (the symmetric variant of Algorithm 1).  Not checked: values
+                            that are not symmetric give a wrong result.  Default 0. */
+  int32_t reserved[6];
 } pselinv_opts;
 
 typedef struct pselinv_ctx* pselinv_t;

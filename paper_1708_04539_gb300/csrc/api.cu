@@ -584,6 +584,19 @@ void add_zero_step(Plan& P, const std::vector<CopySeg>& segs, int level) {
   P.steps.push_back(z);
 }
 
+void add_copy_step(Plan& P, const std::vector<CopySeg>& segs, int level, size_t es) {
+  if (segs.empty()) return;
+  Step cp;
+  cp.kind = ST_COPY;
+  cp.n = (int)segs.size();
+  cp.tasks = P.push(segs);
+  cp.level = level;
+  double bytes = 0;
+  for (const CopySeg& g : segs) bytes += 2.0 * (double)g.count * (double)es;  // read + write
+  cp.bytes = (size_t)bytes;
+  P.steps.push_back(cp);
+}
+
 void add_slice_step(Plan& P, const std::vector<SliceDesc>& descs, int level, bool maxima) {
   if (descs.empty()) return;
   std::vector<SliceTask> tasks;
@@ -770,14 +783,16 @@ void add_ozaki_normalize(pselinv_ctx* h, Plan& P, int lev, int64_t nb,
       ob.product(prods, ub, lb, h->ainv + so, s, s, s, 1.0);  // D_K
       if (c == 0) continue;
       SliceDesc la = ob.slice(h->lu + lo, c, SLICE_ROWS, c, s);  // L_{C,K}(m, k)
-      SliceDesc ua = ob.slice(h->lu + uo, c, SLICE_ROWS, c, s);  // U_{K,C}^T(m, k)
       la.maxbits = maxbase + moff;
-      ua.maxbits = maxbase + moff + c;
-      moff += 2 * c;
       sl.push_back(la);
-      sl.push_back(ua);
       ob.product(prods, la, lb, h->nf + lo, c, c, s, 1.0);
-      ob.product(prods, ua, ub, h->nf + uo, c, c, s, 1.0);
+      if (!h->opts.symmetric) {  // symmetric A: Uhat = Lhat^T, not needed
+        SliceDesc ua = ob.slice(h->lu + uo, c, SLICE_ROWS, c, s);  // U_{K,C}^T(m, k)
+        ua.maxbits = maxbase + moff + c;
+        sl.push_back(ua);
+        ob.product(prods, ua, ub, h->nf + uo, c, c, s, 1.0);
+      }
+      moff += 2 * c;
     }
   const size_t first = P.steps.size();
   Step ms;
@@ -806,7 +821,8 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   std::vector<int64_t> gofs, mofs;
   std::vector<SliceDesc> sl1, sl2, mx1;
   std::vector<OzDesc> main, dg;
-  std::vector<CopySeg> zero;
+  std::vector<CopySeg> zero, mirror;
+  const bool sym = h->opts.symmetric != 0;
   OzBuilder ob(h, (size_t)gbase_scalars * es);
   auto take = [&](size_t bytes) { return ob.take(bytes); };
   // row and column maxima of every G and panel of the level, zeroed by one memset
@@ -840,30 +856,38 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
         }
       const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
       const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
+      // symmetric A: G is symmetric and Uhat = Lhat^T, so step 5's product is
+      // the transpose of step 3's (a copy) and step 4 uses Lhat
       SliceDesc gr = slice_desc((const double*)G, c, SLICE_ROWS, c, c);
-      SliceDesc gc = slice_desc((const double*)G, c, SLICE_COLS, c, c);
-      gr.maxbits = maxbase + m0;      // row maxima of G (from the gather for real data)
-      gc.maxbits = maxbase + m0 + c;  // column maxima of G
+      gr.maxbits = maxbase + m0;  // row maxima of G (from the gather for real data)
       SliceDesc lh = slice_desc((const double*)(h->nf + lo), c, SLICE_COLS, s, c);
-      SliceDesc uh = slice_desc((const double*)(h->nf + uo), c, SLICE_COLS, s, c);
-      SliceDesc ak = slice_desc((const double*)(h->ainv + lo), c, SLICE_COLS, s, c);
       lh.maxbits = maxbase + m0 + 2 * c;
-      uh.maxbits = maxbase + m0 + 2 * c + s;
+      SliceDesc gc = gr, uh = lh;
+      if (!sym) {
+        gc = slice_desc((const double*)G, c, SLICE_COLS, c, c);
+        gc.maxbits = maxbase + m0 + c;  // column maxima of G
+        uh = slice_desc((const double*)(h->nf + uo), c, SLICE_COLS, s, c);
+        uh.maxbits = maxbase + m0 + 2 * c + s;
+      }
+      SliceDesc ak = slice_desc((const double*)(h->ainv + lo), c, SLICE_COLS, s, c);
       ak.maxbits = maxbase + m0 + 2 * c + 2 * s;
       sl1.push_back(gr);
-      sl1.push_back(gc);
       sl1.push_back(lh);
-      sl1.push_back(uh);
+      if (!sym) {
+        sl1.push_back(gc);
+        sl1.push_back(uh);
+      }
       if (cplx) {
         mx1.push_back(gr);
-        mx1.push_back(gc);
+        if (!sym) mx1.push_back(gc);
       }
       mx1.push_back(lh);
-      mx1.push_back(uh);
+      if (!sym) mx1.push_back(uh);
       sl2.push_back(ak);
       // step 3: Ainv(C,K) = -G Lhat;  step 5: Ainv(K,C)^T = -G^T Uhat^T
       push_product(main, gr, lh, h->ainv + lo, c, c, s);
-      push_product(main, gc, uh, h->ainv + uo, c, c, s);
+      if (!sym) push_product(main, gc, uh, h->ainv + uo, c, c, s);
+      else mirror.push_back({h->ainv + lo, h->ainv + uo, (int64_t)c * s});
       // step 4: Ainv(K,K) = D_K - Uhat Ainv(C,K)
       push_product(dg, uh, ak, h->ainv + so, s, s, s);
       zero.push_back({nullptr, h->ainv + lo, (int64_t)2 * c * s * (cplx ? 2 : 1)});
@@ -895,6 +919,7 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   // chunk limit) are accumulated: zero them first
   if (set_ozaki_ksplit(main, ks_main, false)) add_zero_step(P, zero, lev);
   add_ozgemm_step(P, main, S, lev, false, ks_main, 1);
+  add_copy_step(P, mirror, lev, es);
   add_slice_step(P, sl2, lev, true);
   add_slice_step(P, sl2, lev, false);
   add_ozgemm_step(P, dg, S, lev, true, ks_diag, 2);
@@ -902,6 +927,7 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
 
 int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   const HostSym& H = h->H;
+  const bool sym = h->opts.symmetric != 0;
   Plan& P = h->selinv_plan[precision][schedule];
   P.release();
   const size_t es = h->esize;
@@ -966,8 +992,9 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
           const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
           norm.push_back(make_desc(h->lu + lo, Linv, h->nf + lo, c, s, s, c, s, c, 0, 0, 1.0, 0.0,
                                    0, 1, GEMM_TRI_LOWER_B));
-          norm.push_back(make_desc(h->lu + uo, Uinv, h->nf + uo, c, s, s, c, s, c, 0, 1, 1.0, 0.0,
-                                   0, 1, GEMM_TRI_LOWER_B));
+          if (!h->opts.symmetric)  // symmetric A: Uhat = Lhat^T, not needed
+            norm.push_back(make_desc(h->lu + uo, Uinv, h->nf + uo, c, s, s, c, s, c, 0, 1, 1.0, 0.0,
+                                     0, 1, GEMM_TRI_LOWER_B));
         }
       }
     const size_t first = P.steps.size();
@@ -1020,6 +1047,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       std::vector<SnTask> gt;
       std::vector<int64_t> gofs;
       std::vector<GemmDesc> main, dg;
+      std::vector<CopySeg> mirror;
       int64_t goff = gbase;
       for (int64_t b = 0; b < nb; b++)
         for (int64_t K : grp) {
@@ -1036,10 +1064,14 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
           const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
           char* G = h->scratch + (size_t)g0 * es;
           main.push_back(make_desc(G, h->nf + lo, h->ainv + lo, c, s, c, c, c, c, 0, 0, -1.0, 0.0));
-          main.push_back(make_desc(G, h->nf + uo, h->ainv + uo, c, s, c, c, c, c, 1, 0, -1.0, 0.0));
+          // symmetric A: step 5 is the transpose of step 3 and Uhat = Lhat^T
+          if (sym)
+            mirror.push_back({h->ainv + lo, h->ainv + uo, c * s});
+          else
+            main.push_back(make_desc(G, h->nf + uo, h->ainv + uo, c, s, c, c, c, c, 1, 0, -1.0, 0.0));
           const int ksplit = std::max(1, (int)std::min<int64_t>(c / 256, 64));
-          dg.push_back(make_desc(h->nf + uo, h->ainv + lo, h->ainv + so, s, s, c, c, c, s, 1, 0,
-                                 -1.0, 1.0, 1, ksplit));
+          dg.push_back(make_desc(h->nf + (sym ? lo : uo), h->ainv + lo, h->ainv + so, s, s, c, c, c,
+                                 s, 1, 0, -1.0, 1.0, 1, ksplit));
         }
       if (gt.empty()) continue;
       Step g;
@@ -1052,6 +1084,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       P.steps.push_back(g);
       add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_main, cfg), main, (int)lev,
                     slot_main);
+      add_copy_step(P, mirror, (int)lev, es);
       add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_diag, cfg), dg, (int)lev,
                     slot_diag);
     }
@@ -1247,6 +1280,7 @@ void pselinv_default_opts(pselinv_opts* o) {
   o->check_level = 0;
   o->host_only = 0;
   o->split_normalise = 0;
+  o->symmetric = 0;
 }
 
 const char* pselinv_error_string(int status) {
