@@ -24,6 +24,7 @@ def _check_csc(p):
     lambda s: gen.dg_blocks(2, 5, s),
     lambda s: gen.shifted_family(4, s, nshift=3),
     lambda s: gen.random_struct_sym(40, 0.1, s),
+    lambda s: gen.sym_diffusion_3d(4, s),
 ])
 def test_generators_valid_and_deterministic(maker):
     a, b, c = maker(5), maker(5), maker(6)
@@ -34,6 +35,13 @@ def test_generators_valid_and_deterministic(maker):
         d = a.dense(k)
         off = np.abs(d).sum(axis=1) - np.abs(np.diag(d))
         assert np.all(np.abs(np.diag(d)) > off - 1e-12)  # diagonally dominant by rows
+
+
+def test_symmetric_generators_are_symmetric():
+    for p in (gen.sym_diffusion_3d(5, 3), gen.stencil27_complex(4, 3, eps=0.0),
+              gen.random_struct_sym(50, 0.1, 3, symmetric_values=True)):
+        d = p.dense(0)
+        assert np.array_equal(d, d.T)
 
 
 def test_conv_diff_values_follow_recipe():
