@@ -241,11 +241,15 @@ def roofline_from_profile(prof, slices):
     peaks = measured_peaks()
     if top == "gemm":
         achieved = k["flops"] / sec / 1e12
-        tile = GEMM_TEMPLATES.get(main_param, "?")
-        rec = {"bound": "alu", "kernel": f"gemm_kernel<double,{tile}> (FP64 DFMA)",
+        if main_param == 3:  # row panels of the products with a triangular B
+            name, tkey = "tri_rows_kernel<double> (FP64 DFMA)", "tri_rows_kernel_f64"
+        else:
+            tile = GEMM_TEMPLATES.get(main_param, "?")
+            name, tkey = f"gemm_kernel<double,{tile}> (FP64 DFMA)", "gemm_kernel_f64"
+        rec = {"bound": "alu", "kernel": name,
                "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
-               "traffic": traffic_from_profiles("gemm_kernel_f64")}
+               "traffic": traffic_from_profiles(tkey)}
     elif top == "ozaki_gemm":
         pairs = slices * (slices + 1) // 2
         achieved = pairs * k["flops"] / sec / 1e12

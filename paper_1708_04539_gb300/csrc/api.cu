@@ -227,15 +227,33 @@ void gemm_features<GemmDesc>(Step& st, const std::vector<GemmDesc>& descs, doubl
 void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& descs, int level,
                    int slot = -1) {
   if (descs.empty()) return;
-  const int bm = gemm_tile_m(dtype, cfg), bn = gemm_tile_n(dtype, cfg);
+  if (cfg == GEMM_TRI_ROWS)
+    for (const GemmDesc& g : descs)
+      if (!tri_rows_eligible(g)) cfg = GEMM_32x32;  // not a triangular product
   std::vector<GemmTask> tasks;
+  std::vector<double> work;  // GEMM_TRI_ROWS: FMAs per task, for the launch order
   double flops = 0, bytes = 0;
   for (size_t d = 0; d < descs.size(); d++) {
     const GemmDesc& g = descs[d];
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) continue;
-    for (int ks = 0; ks < g.ksplit; ks++)
-      for (int tn = 0; tn < ceil_div(g.N, bn); tn++)
-        for (int tm = 0; tm < ceil_div(g.M, bm); tm++) tasks.push_back({(int)d, tm, tn, ks});
+    if (cfg == GEMM_TRI_ROWS) {
+      const int ch = tri_rows_chunk(dtype);
+      const bool lower = (g.tri & GEMM_TRI_LOWER_B) != 0;
+      for (int tn = 0; tn < ceil_div(g.N, ch); tn++) {
+        const int j0 = tn * ch, w = std::min(ch, g.N - j0);
+        const int nw = w <= 4 ? 4 : w <= 8 ? 8 : 16;
+        const double kw = lower ? g.K - j0 : j0 + w;
+        for (int tm = 0; tm < ceil_div(g.M, kTriRowsBlock); tm++) {
+          tasks.push_back({(int)d, tm, tn, nw});
+          work.push_back(kw * nw * std::min(kTriRowsBlock, g.M - tm * kTriRowsBlock));
+        }
+      }
+    } else {
+      const int bm = gemm_tile_m(dtype, cfg), bn = gemm_tile_n(dtype, cfg);
+      for (int ks = 0; ks < g.ksplit; ks++)
+        for (int tn = 0; tn < ceil_div(g.N, bn); tn++)
+          for (int tm = 0; tm < ceil_div(g.M, bm); tm++) tasks.push_back({(int)d, tm, tn, ks});
+    }
     double f = 2.0 * g.M * g.N * g.K;
     if (g.tri == GEMM_TRI_LOWER_B || g.tri == GEMM_TRI_UPPER_B) f = (double)g.M * g.N * (g.N + 1);
     if (g.tri == (GEMM_TRI_UPPER_A | GEMM_TRI_LOWER_B)) f = 2.0 * g.N * (double)g.N * g.N / 3.0;
@@ -245,6 +263,15 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
                    (double)g.M * g.N * ((g.atomic || g.beta != 0.0) ? 2.0 : 1.0));
   }
   if (tasks.empty()) return;
+  if (cfg == GEMM_TRI_ROWS) {  // longest tasks first: CTAs start in task order
+    std::vector<size_t> order(tasks.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return work[a] > work[b]; });
+    std::vector<GemmTask> sorted(tasks.size());
+    for (size_t i = 0; i < order.size(); i++) sorted[i] = tasks[order[i]];
+    tasks.swap(sorted);
+  }
   Step s;
   s.bytes = (size_t)bytes;
   s.kind = ST_GEMM;
@@ -540,7 +567,7 @@ int build_factor_plan(pselinv_ctx* h) {
       add_gemm_step(P, dt, GEMM_32x32, upd, (int)lev);
     }
     add_tri_step(P, H, tri, (int)lev, 0);
-    add_gemm_step(P, dt, cfg, trsm, (int)lev);
+    add_gemm_step(P, dt, GEMM_TRI_ROWS, trsm, (int)lev);
     add_gemm_step(P, dt, cfg, schur, (int)lev);
     if (!gt.empty()) {
       Step sc;
@@ -998,7 +1025,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
         }
       }
     const size_t first = P.steps.size();
-    add_gemm_step(P, dt, tuned_value(h, precision, lev, 0, cfg), norm, lev, 0);
+    add_gemm_step(P, dt, tuned_value(h, precision, lev, 0, GEMM_TRI_ROWS), norm, lev, 0);
     if (split) add_ozaki_normalize(h, P, lev, nb, wbase, norm_base);
     for (size_t i = first; i < P.steps.size(); i++) P.steps[i].side = 1;
     if (P.steps.size() > first) {
@@ -1558,7 +1585,8 @@ int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_
 template <class RB>
 static int model_tune(pselinv_ctx* h, Plan& P0, int precision, pselinv_model_t model, RB rebuild) {
   if (!model) return PSELINV_ERR_ARG;
-  static const int gemm_cands[3] = {GEMM_64x64, GEMM_32x32, GEMM_128x64};
+  // the normalisation's products (slot 0) have triangular B: one candidate more
+  static const int gemm_cands[4] = {GEMM_64x64, GEMM_32x32, GEMM_128x64, GEMM_TRI_ROWS};
   static const int ks_cands[5] = {1, 2, 4, 8, 16};
   std::vector<std::tuple<int, int, int>> keys;
   std::vector<pselinv_tune_record> q;
@@ -1567,7 +1595,7 @@ static int model_tune(pselinv_ctx* h, Plan& P0, int precision, pselinv_model_t m
     const auto key = std::make_tuple(s.level, s.slot, (int)s.kind);
     if (std::find(keys.begin(), keys.end(), key) != keys.end()) continue;
     keys.push_back(key);
-    const int nc = s.kind == ST_GEMM ? 3 : 5;
+    const int nc = s.kind == ST_GEMM ? (s.slot == 0 ? 4 : 3) : 5;
     for (int v = 0; v < nc; v++) {
       pselinv_tune_record r{};
       r.precision = precision;
@@ -1619,7 +1647,8 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
   if (mode == PSELINV_TUNE_MODEL) return model_tune(h, P0, precision, model, rebuild);
   if (mode != PSELINV_TUNE_EXHAUSTIVE) return PSELINV_ERR_ARG;
 
-  static const int gemm_cands[3] = {GEMM_64x64, GEMM_32x32, GEMM_128x64};
+  // the normalisation's products (slot 0) have triangular B: one candidate more
+  static const int gemm_cands[4] = {GEMM_64x64, GEMM_32x32, GEMM_128x64, GEMM_TRI_ROWS};
   static const int ks_cands[5] = {1, 2, 4, 8, 16};
   struct Key {
     int level, slot, kind;
@@ -1678,8 +1707,10 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
   };
   const int nlev = (int)h->H.level_ptr.size() - 1;
   if (precision == PSELINV_PREC_FP64) {
-    for (int v = 0; v < 3; v++) {
-      for (const Key& k : keys) h->tuned[std::make_tuple(precision, k.level, k.slot)] = gemm_cands[v];
+    for (int v = 0; v < 4; v++) {
+      for (const Key& k : keys)
+        h->tuned[std::make_tuple(precision, k.level, k.slot)] =
+            k.slot == 0 || v < 3 ? gemm_cands[v] : GEMM_32x32;
       rc = measure(-1);
       if (rc != PSELINV_OK) return rc;
     }
@@ -1690,7 +1721,7 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
         h->tuned[std::make_tuple(precision, l, 3)] = 0;
         h->tuned[std::make_tuple(precision, l, 1)] = ks_cands[v];
         h->tuned[std::make_tuple(precision, l, 2)] = ks_cands[v];
-        h->tuned[std::make_tuple(precision, l, 0)] = gemm_cands[v % 3];
+        h->tuned[std::make_tuple(precision, l, 0)] = gemm_cands[(v + 3) % 4];
       }
       rc = measure(0);
       if (rc != PSELINV_OK) return rc;
@@ -1872,14 +1903,14 @@ int pselinv_plan_set(pselinv_t h, int precision, const int32_t* in, int64_t coun
   for (int64_t i = 0; i < count; i++) {
     const int lev = in[3 * i], slot = in[3 * i + 1], v = in[3 * i + 2];
     bool ok = lev >= 0 && lev < nlev && slot >= 0 && slot <= 5;
-    if (ok && precision == PSELINV_PREC_FP64) ok = slot <= 2 && v >= 0 && v <= 2;
+    if (ok && precision == PSELINV_PREC_FP64) ok = slot <= 2 && v >= 0 && v <= (slot == 0 ? 3 : 2);
     if (ok && precision == PSELINV_PREC_OZAKI_FP16) {
       if (slot == 1 || slot == 2)
         ok = v == 1 || v == 2 || v == 4 || v == 8 || v == 16;
       else if (slot == 3)
         ok = v == 0 || v == 1;
       else
-        ok = v >= 0 && v <= 2;
+        ok = v >= 0 && v <= (slot == 0 ? 3 : 2);
     }
     if (!ok) return PSELINV_ERR_ARG;
     entries.push_back({std::make_tuple(precision, lev, slot), v});

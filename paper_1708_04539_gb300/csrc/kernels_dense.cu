@@ -389,6 +389,97 @@ tri_inv_small_kernel(SymDev S, const T* store, T* out, const int64_t* __restrict
   }
 }
 
+// Product with a square triangular op(B): C(m, n) = alpha sum_k A(m, k)
+// op(B)(k, n) (+ beta C), one thread per row m, columns j0 .. j0 + NW - 1.
+// A lower op(B) is zero for k < n, an upper one for k > n: in the diagonal
+// block (k in [j0, j0 + NW)) only the triangle is multiplied, the other
+// k run over all NW columns.  An upper A (GEMM_TRI_UPPER_A, lower op(B)
+// only) starts every warp at its first row.  Lanes past M read row M - 1
+// and columns past N read column N - 1 (in bounds; never stored).  FP64
+// throughput is the bound: the loads of op(B) are warp-uniform, the loads
+// of A coalesced along m.
+template <typename T, int NW, bool LOWER>
+__device__ __forceinline__ void tri_rows_task(const GemmDesc& d, int m, int warp_m0, int j0) {
+  const T* __restrict__ B = (const T*)d.B;
+  const T* __restrict__ Ar = (const T*)d.A + min(m, d.M - 1);
+  const int K = d.K, nlast = d.N - 1;
+  const int64_t sk = d.transB ? d.ldb : 1, sn = d.transB ? 1 : d.ldb;
+  auto bval = [&](int k, int q) { return B[(int64_t)k * sk + (int64_t)min(j0 + q, nlast) * sn]; };
+  T acc[NW];
+#pragma unroll
+  for (int q = 0; q < NW; q++) acc[q] = sc_zero(T());
+  if (LOWER) {
+    const int kstart = (d.tri & GEMM_TRI_UPPER_A) ? max(j0, warp_m0) : j0;
+#pragma unroll
+    for (int kk = 0; kk < NW; kk++) {
+      const int k = j0 + kk;
+      if (k < kstart || k >= K) continue;
+      const T a = Ar[(int64_t)k * d.lda];
+#pragma unroll
+      for (int q = 0; q <= kk; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);
+    }
+    for (int k = max(j0 + NW, kstart); k < K; k++) {
+      const T a = Ar[(int64_t)k * d.lda];
+#pragma unroll
+      for (int q = 0; q < NW; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);
+    }
+  } else {
+    for (int k = 0; k < j0; k++) {
+      const T a = Ar[(int64_t)k * d.lda];
+#pragma unroll
+      for (int q = 0; q < NW; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);
+    }
+#pragma unroll
+    for (int kk = 0; kk < NW; kk++) {
+      const int k = j0 + kk;
+      if (k >= K) break;
+      const T a = Ar[(int64_t)k * d.lda];
+#pragma unroll
+      for (int q = kk; q < NW; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);
+    }
+  }
+  if (m >= d.M) return;
+  T* __restrict__ C = (T*)d.C + m;
+#pragma unroll
+  for (int q = 0; q < NW; q++) {
+    const int n = j0 + q;
+    if (n >= d.N) break;
+    T v = scale_s(acc[q], d.alpha);
+    if (d.beta != 0.0) v = add_s(v, scale_s(C[(int64_t)n * d.ldc], d.beta));
+    C[(int64_t)n * d.ldc] = v;
+  }
+}
+
+template <typename T, bool LOWER>
+__device__ __forceinline__ void tri_rows_dispatch(const GemmDesc& d, int nw, int m, int warp_m0,
+                                                  int j0) {
+  switch (nw) {
+    case 4: tri_rows_task<T, 4, LOWER>(d, m, warp_m0, j0); break;
+    case 8: tri_rows_task<T, 8, LOWER>(d, m, warp_m0, j0); break;
+    default:
+      if constexpr (sizeof(T) == 8) tri_rows_task<T, 16, LOWER>(d, m, warp_m0, j0);
+      break;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTriRowsBlock)
+tri_rows_kernel(const GemmDesc* __restrict__ descs, const GemmTask* __restrict__ tasks, int ntasks) {
+  const int chunk = sizeof(T) == 8 ? 16 : 8;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const GemmTask task = tasks[t];
+    const GemmDesc d = descs[task.d];
+    const int m = task.tm * kTriRowsBlock + (int)threadIdx.x;
+    const int warp_m0 = m & ~31;
+    if (warp_m0 >= d.M) continue;  // whole warp past the last row
+    const int j0 = task.tn * chunk;
+    if (d.tri & GEMM_TRI_LOWER_B)
+      tri_rows_dispatch<T, true>(d, task.ks, m, warp_m0, j0);
+    else
+      tri_rows_dispatch<T, false>(d, task.ks, m, warp_m0, j0);
+  }
+}
+
 template <typename T, int BM, int BN, int BK>
 void gemm_launch_t(const GemmDesc* descs, const GemmTask* tasks, int ntasks, int grid,
                    cudaStream_t st) {
@@ -411,6 +502,14 @@ int gemm_tile_n(int dtype, int cfg) {
 
 void launch_gemm(int dtype, int cfg, const GemmDesc* descs, const GemmTask* tasks, int ntasks,
                  int grid, cudaStream_t st) {
+  if (cfg == GEMM_TRI_ROWS) {
+    if (ntasks <= 0) return;
+    if (dtype == DT_F64)
+      tri_rows_kernel<double><<<grid, kTriRowsBlock, 0, st>>>(descs, tasks, ntasks);
+    else
+      tri_rows_kernel<cdouble><<<grid, kTriRowsBlock, 0, st>>>(descs, tasks, ntasks);
+    return;
+  }
   if (dtype == DT_F64) {
     switch (cfg) {
       case GEMM_32x32: gemm_launch_t<double, 32, 32, 16>(descs, tasks, ntasks, grid, st); break;
