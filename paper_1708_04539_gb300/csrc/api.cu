@@ -230,6 +230,7 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
   if (cfg == GEMM_TRI_ROWS)
     for (const GemmDesc& g : descs)
       if (!tri_rows_eligible(g)) cfg = GEMM_32x32;  // not a triangular product
+  const int rblock = kTriRowsBlock;
   std::vector<GemmTask> tasks;
   std::vector<double> work;  // GEMM_TRI_ROWS: FMAs per task, for the launch order
   double flops = 0, bytes = 0;
@@ -241,11 +242,11 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
       const bool lower = (g.tri & GEMM_TRI_LOWER_B) != 0;
       for (int tn = 0; tn < ceil_div(g.N, ch); tn++) {
         const int j0 = tn * ch, w = std::min(ch, g.N - j0);
-        const int nw = w <= 4 ? 4 : w <= 8 ? 8 : 16;
+        const int nw = w <= 4 ? 4 : 8;
         const double kw = lower ? g.K - j0 : j0 + w;
-        for (int tm = 0; tm < ceil_div(g.M, kTriRowsBlock); tm++) {
+        for (int tm = 0; tm < ceil_div(g.M, rblock); tm++) {
           tasks.push_back({(int)d, tm, tn, nw});
-          work.push_back(kw * nw * std::min(kTriRowsBlock, g.M - tm * kTriRowsBlock));
+          work.push_back(kw * nw * std::min(rblock, g.M - tm * rblock));
         }
       }
     } else {

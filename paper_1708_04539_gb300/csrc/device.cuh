@@ -208,10 +208,12 @@ enum DType { DT_F64 = 1, DT_C128 = 2 };
 // one thread per row of C and a chunk of columns per task, the zero
 // triangle of the diagonal block skipped exactly.  Its tasks are {d, row
 // block of kTriRowsBlock rows, chunk of tri_rows_chunk() columns, width
-// NW in {4, 8, 16} that the kernel computes for the chunk}.
+// NW in {4, 8} that the kernel computes for the chunk}.  Short tasks
+// (64 rows x 8 columns) let the CTAs of a concurrent stream in sooner.
 enum GemmCfg { GEMM_64x64 = 0, GEMM_32x32 = 1, GEMM_128x64 = 2, GEMM_TRI_ROWS = 3, GEMM_NCFG = 4 };
-constexpr int kTriRowsBlock = 128;
-inline int tri_rows_chunk(int dtype) { return dtype == DT_F64 ? 16 : 8; }
+constexpr int kTriRowsBlock = 64;
+constexpr int kTriRowsChunk = 8;
+inline int tri_rows_chunk(int) { return kTriRowsChunk; }
 inline bool tri_rows_eligible(const GemmDesc& d) {
   const int t = d.tri & (GEMM_TRI_LOWER_B | GEMM_TRI_UPPER_B);
   return (t == GEMM_TRI_LOWER_B || t == GEMM_TRI_UPPER_B) && d.transA == 0 && d.atomic == 0 &&

@@ -408,6 +408,27 @@ __device__ __forceinline__ void tri_rows_task(const GemmDesc& d, int m, int warp
   T acc[NW];
 #pragma unroll
   for (int q = 0; q < NW; q++) acc[q] = sc_zero(T());
+  // k in [kb, ke) over all NW columns, the operands of k + 1 loaded while
+  // those of k are multiplied (a warp alone on its FP64 unit stays busy)
+  auto full_range = [&](int kb, int ke) {
+    if (kb >= ke) return;
+    T an = Ar[(int64_t)kb * d.lda], bn[NW];
+#pragma unroll
+    for (int q = 0; q < NW; q++) bn[q] = bval(kb, q);
+    for (int k = kb; k < ke; k++) {
+      const T a = an;
+      T b[NW];
+#pragma unroll
+      for (int q = 0; q < NW; q++) b[q] = bn[q];
+      if (k + 1 < ke) {
+        an = Ar[(int64_t)(k + 1) * d.lda];
+#pragma unroll
+        for (int q = 0; q < NW; q++) bn[q] = bval(k + 1, q);
+      }
+#pragma unroll
+      for (int q = 0; q < NW; q++) acc[q] = fma_s(a, b[q], acc[q]);
+    }
+  };
   if (LOWER) {
     const int kstart = (d.tri & GEMM_TRI_UPPER_A) ? max(j0, warp_m0) : j0;
 #pragma unroll
@@ -418,17 +439,9 @@ __device__ __forceinline__ void tri_rows_task(const GemmDesc& d, int m, int warp
 #pragma unroll
       for (int q = 0; q <= kk; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);
     }
-    for (int k = max(j0 + NW, kstart); k < K; k++) {
-      const T a = Ar[(int64_t)k * d.lda];
-#pragma unroll
-      for (int q = 0; q < NW; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);
-    }
+    full_range(max(j0 + NW, kstart), K);
   } else {
-    for (int k = 0; k < j0; k++) {
-      const T a = Ar[(int64_t)k * d.lda];
-#pragma unroll
-      for (int q = 0; q < NW; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);
-    }
+    full_range(0, j0);
 #pragma unroll
     for (int kk = 0; kk < NW; kk++) {
       const int k = j0 + kk;
@@ -453,26 +466,22 @@ __device__ __forceinline__ void tri_rows_task(const GemmDesc& d, int m, int warp
 template <typename T, bool LOWER>
 __device__ __forceinline__ void tri_rows_dispatch(const GemmDesc& d, int nw, int m, int warp_m0,
                                                   int j0) {
-  switch (nw) {
-    case 4: tri_rows_task<T, 4, LOWER>(d, m, warp_m0, j0); break;
-    case 8: tri_rows_task<T, 8, LOWER>(d, m, warp_m0, j0); break;
-    default:
-      if constexpr (sizeof(T) == 8) tri_rows_task<T, 16, LOWER>(d, m, warp_m0, j0);
-      break;
-  }
+  if (nw == 4)
+    tri_rows_task<T, 4, LOWER>(d, m, warp_m0, j0);
+  else
+    tri_rows_task<T, 8, LOWER>(d, m, warp_m0, j0);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kTriRowsBlock)
 tri_rows_kernel(const GemmDesc* __restrict__ descs, const GemmTask* __restrict__ tasks, int ntasks) {
-  const int chunk = sizeof(T) == 8 ? 16 : 8;
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const GemmTask task = tasks[t];
     const GemmDesc d = descs[task.d];
     const int m = task.tm * kTriRowsBlock + (int)threadIdx.x;
     const int warp_m0 = m & ~31;
     if (warp_m0 >= d.M) continue;  // whole warp past the last row
-    const int j0 = task.tn * chunk;
+    const int j0 = task.tn * kTriRowsChunk;
     if (d.tri & GEMM_TRI_LOWER_B)
       tri_rows_dispatch<T, true>(d, task.ks, m, warp_m0, j0);
     else

@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 import gen
-from test_gpu_parity import compare_full, gpu_run
+from test_gpu_parity import TOL_FP64, compare_full, gpu_run, oracle_coo
+from helpers import selected_error
 
 pytestmark = pytest.mark.gpu
 
@@ -141,3 +142,33 @@ def test_split_config2_full_size(torch):
     rows, cols = supernodal_coordinates(st)
     err = selected_error(sn, sn64, rows, cols, p.n)
     assert err < TOL_SPLIT, err
+
+
+@pytest.mark.parametrize("name,make", [CASES[2], CASES[3], ("upwind12_c", lambda: gen.stencil27_complex(8, 66, max_sn=64))],
+                         ids=["upwind16_wide", "dg", "stencil27_c"])
+@pytest.mark.parametrize("norm_cfg", [1, 3], ids=["tiles32", "rows"])
+def test_normalisation_kernels_match_oracle(torch, name, make, norm_cfg):
+    """The normalisation's triangular products (Lhat, Uhat^T, D_K) through
+    each of their kernels -- 32 x 32 tiles and row panels with exact
+    triangles -- in both plans, over two sweeps of one handle."""
+    import paper_1708_04539_gb300 as ps
+    from paper_1708_04539_gb300.binding import supernodal_coordinates
+    p = make()
+    h = ps.SelInv.from_problem(p)
+    h.factor(torch.from_numpy(np.ascontiguousarray(p.values)).cuda())
+    nlev = h.structure()["nlevels"]
+    st = h.structure()
+    h.plan_set([(lev, 0, norm_cfg) for lev in range(nlev)], ps.PREC_FP64)
+    h.plan_set([(lev, 0, norm_cfg) for lev in range(nlev)] + [(lev, 3, 0) for lev in range(nlev)],
+               ps.PREC_OZAKI_FP16)
+    _, orows, ocols, ovals = oracle_coo(p, 0, 20)
+    grows, gcols = supernodal_coordinates(st)
+    gi, oi = np.argsort(grows * p.n + gcols), np.argsort(orows * p.n + ocols)
+    for rep in range(2):
+        for prec, tol in ((ps.PREC_FP64, TOL_FP64), (ps.PREC_OZAKI_FP16, TOL_SPLIT)):
+            h.selinv(precision=prec)
+            sn = h.get_selected(layout=ps.LAYOUT_SUPERNODAL)
+            err = selected_error(sn[gi], ovals[oi], orows[oi], ocols[oi], p.n)
+            assert err < tol, (rep, prec, err)
+    h.sync()
+    h.close()
