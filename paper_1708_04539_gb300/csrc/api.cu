@@ -130,6 +130,7 @@ struct pselinv_ctx {
   char* ainv = nullptr;
   char* scratch = nullptr;
   size_t scratch_bytes = 0;
+  size_t scratch_high = 0;  // plan building: highest scratch byte a step uses
   char* staging = nullptr;  // nbatch * nnz values
   char* outstage = nullptr; // nnz values
   // pole-expansion consumers: the input pattern (for transposed entries),
@@ -375,8 +376,19 @@ size_t selinv_main_bytes(const HostSym& H, int64_t nb, size_t es) {
                            (size_t)(w * nb) * es + ozaki_level_bytes(H, nb, 6, es) + 4096));
 }
 
+// row and column maxima of the split levels' operands, a region of their
+// own for the whole sweep (zeroed once per sweep): an upper bound with one
+// group per supernode
+size_t maxima_bytes(const HostSym& H, int64_t nb) {
+  size_t b = 0;
+  for (int64_t K = 0; K < H.ns; K++)
+    if (cK(H, K) > 0) b += align256((size_t)(2 * cK(H, K) + 3 * H.sn_width[K]) * 8 * nb + 8);
+  return b;
+}
+
 // scratch needed (bytes) by the factor and selected-inversion plans; the
-// split normalisation (side stream) has its own region after the sweep's
+// split normalisation (side stream) has its own region after the sweep's,
+// the maxima theirs after that
 size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
   int64_t fmax = 0;
   for (size_t d = 0; d + 1 < H.hlevel_ptr.size(); d++) {
@@ -388,7 +400,8 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
     fmax = std::max(fmax, f);
   }
   return std::max((size_t)(fmax * nb) * es + 256,
-                  selinv_main_bytes(H, nb, es) + ozaki_norm_bytes(H, nb, 6, es));
+                  selinv_main_bytes(H, nb, es) + ozaki_norm_bytes(H, nb, 6, es) +
+                      maxima_bytes(H, nb));
 }
 
 // default FP64 tile config before tuning: 32 x 32 tiles (what the tuner
@@ -725,6 +738,7 @@ struct OzBuilder {
     off = align256(off);
     const size_t o = off;
     off += bytes;
+    h->scratch_high = std::max(h->scratch_high, off);
     return h->scratch + o;
   }
   // slice set of the R x Kd operand X: X(r, k) = src[r + k ld] (SLICE_ROWS)
@@ -840,7 +854,7 @@ void add_ozaki_normalize(pselinv_ctx* h, Plan& P, int lev, int64_t nb,
 // steps 3 and 5, slice Ainv(C,K), sliced product for step 4 accumulated onto
 // D_K.  Scratch layout after the W region (byte offsets).
 void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, int64_t nb,
-                     int64_t gbase_scalars, int lev) {
+                     int64_t gbase_scalars, int lev, size_t& max_cursor) {
   const HostSym& H = h->H;
   const int S = h->slices;
   const size_t es = h->esize;
@@ -853,13 +867,17 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   const bool sym = h->opts.symmetric != 0;
   OzBuilder ob(h, (size_t)gbase_scalars * es);
   auto take = [&](size_t bytes) { return ob.take(bytes); };
-  // row and column maxima of every G and panel of the level, zeroed by one memset
+  // row and column maxima of every G and panel of the level (the sweep's
+  // maxima region, zeroed at its start)
   int64_t nmax = 0;
   for (int64_t b = 0; b < nb; b++)
     for (int64_t K : grp)
       if (H.rows_ptr[K + 1] > H.rows_ptr[K])
         nmax += 2 * (H.rows_ptr[K + 1] - H.rows_ptr[K]) + 3 * H.sn_width[K];
-  unsigned long long* maxbase = (unsigned long long*)take(align256((size_t)nmax * 8 + 8));
+  if (nmax == 0) return;  // roots only (c = 0): nothing after D_K
+  unsigned long long* maxbase = (unsigned long long*)(h->scratch + max_cursor);
+  max_cursor += align256((size_t)nmax * 8 + 8);
+  h->scratch_high = std::max(h->scratch_high, max_cursor);
   int64_t moff = 0;
   auto slice_desc = [&](const double* src, int ld, int mode, int R, int Kd) {
     return ob.slice(src, ld, mode, R, Kd);
@@ -921,12 +939,6 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
       zero.push_back({nullptr, h->ainv + lo, (int64_t)2 * c * s * (cplx ? 2 : 1)});
     }
   if (gt.empty()) return;
-  Step ms;
-  ms.kind = ST_MEMSET;
-  ms.ptr = maxbase;
-  ms.bytes = (size_t)nmax * 8;
-  ms.level = lev;
-  P.steps.push_back(ms);
   Step g;
   g.kind = ST_GATHER;
   g.n = (int)gt.size();
@@ -958,6 +970,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   const bool sym = h->opts.symmetric != 0;
   Plan& P = h->selinv_plan[precision][schedule];
   P.release();
+  h->scratch_high = 0;
   const size_t es = h->esize;
   const int dt = h->dtype;
   const int64_t nb = h->nbatch;
@@ -1001,6 +1014,8 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
     if (!tb.empty()) P.steps.back().signal = EV_THIRD_DONE;
   }
   const size_t norm_base = selinv_main_bytes(H, nb, es);
+  const size_t max_base = norm_base + ozaki_norm_bytes(H, nb, 6, es);
+  size_t max_cursor = max_base;
   bool third_waited = false;
   // split = true: Lhat, Uhat^T and D_K as sliced products
   auto add_normalize = [&](int lev, bool split) {
@@ -1069,7 +1084,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
     const int slot_diag = precision == PSELINV_PREC_OZAKI_FP16 ? 5 : 2;
     for (const auto& grp : groups) {
       if (split_level) {
-        add_ozaki_level(h, P, grp, nb, gbase, (int)lev);
+        add_ozaki_level(h, P, grp, nb, gbase, (int)lev, max_cursor);
         continue;
       }
       std::vector<SnTask> gt;
@@ -1083,6 +1098,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
           if (c == 0) continue;
           const int64_t g0 = goff;
           goff += c * c;
+          h->scratch_high = std::max(h->scratch_high, (size_t)goff * es);
           for (int tq = 0; tq < ceil_div(c, 32); tq++)
             for (int tp = 0; tp < ceil_div(c, 32); tp++) {
               gt.push_back({(int)b, (int)K, tp, tq});
@@ -1117,6 +1133,15 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
                     slot_diag);
     }
     if (P.steps.size() > first_main) P.steps[first_main].wait = EV_LEVEL + (int)lev;
+  }
+  // the scratch sizes above bound every region the steps use
+  if (h->scratch_high > h->scratch_bytes) return PSELINV_ERR_CHECK;
+  if (max_cursor > max_base) {  // one memset of every split level's maxima, first on the sweep
+    Step ms;
+    ms.kind = ST_MEMSET;
+    ms.ptr = h->scratch + max_base;
+    ms.bytes = max_cursor - max_base;
+    P.steps.insert(P.steps.begin(), ms);
   }
   CK(cudaMalloc(&P.arena, P.host.size() + 256));
   CK(cudaMemcpy(P.arena, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
