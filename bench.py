@@ -213,7 +213,7 @@ def measured_peaks():
         return {}
 
 
-GEMM_TEMPLATES = {0: "64,64,16", 1: "32,32,16", 2: "128,64,8"}  # tile config -> BM,BN,BK
+GEMM_TEMPLATES = {0: "64,64,16", 1: "32,32,16", 2: "128,64,8"}  # tile config -> BM,BN,BK (3: row panels)
 
 
 def roofline_from_profile(prof, slices):
@@ -241,8 +241,8 @@ def roofline_from_profile(prof, slices):
     peaks = measured_peaks()
     if top == "gemm":
         achieved = k["flops"] / sec / 1e12
-        if main_param == 3:  # row panels of the products with a triangular B
-            name, tkey = "tri_rows_kernel<double> (FP64 DFMA)", "tri_rows_kernel_f64"
+        if main_param == 3:  # row panels (the normalisation's triangular products)
+            name, tkey = "rows_gemm_kernel<double> (FP64 DFMA)", "rows_gemm_kernel_f64"
         else:
             tile = GEMM_TEMPLATES.get(main_param, "?")
             name, tkey = f"gemm_kernel<double,{tile}> (FP64 DFMA)", "gemm_kernel_f64"

@@ -228,26 +228,29 @@ void gemm_features<GemmDesc>(Step& st, const std::vector<GemmDesc>& descs, doubl
 void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& descs, int level,
                    int slot = -1) {
   if (descs.empty()) return;
-  if (cfg == GEMM_TRI_ROWS)
+  if (cfg == GEMM_ROWS)
     for (const GemmDesc& g : descs)
-      if (!tri_rows_eligible(g)) cfg = GEMM_32x32;  // not a triangular product
-  const int rblock = kTriRowsBlock;
+      if (!rows_eligible(g)) cfg = GEMM_32x32;
   std::vector<GemmTask> tasks;
-  std::vector<double> work;  // GEMM_TRI_ROWS: FMAs per task, for the launch order
+  std::vector<double> work;  // GEMM_ROWS: FMAs per task, for the launch order
   double flops = 0, bytes = 0;
   for (size_t d = 0; d < descs.size(); d++) {
     const GemmDesc& g = descs[d];
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) continue;
-    if (cfg == GEMM_TRI_ROWS) {
-      const int ch = tri_rows_chunk(dtype);
-      const bool lower = (g.tri & GEMM_TRI_LOWER_B) != 0;
-      for (int tn = 0; tn < ceil_div(g.N, ch); tn++) {
-        const int j0 = tn * ch, w = std::min(ch, g.N - j0);
+    if (cfg == GEMM_ROWS) {
+      const int tri = g.tri & (GEMM_TRI_LOWER_B | GEMM_TRI_UPPER_B);
+      const int kchunk = ceil_div(g.K, g.ksplit);
+      for (int tn = 0; tn < ceil_div(g.N, kRowsChunk); tn++) {
+        const int j0 = tn * kRowsChunk, w = std::min(kRowsChunk, g.N - j0);
         const int nw = w <= 4 ? 4 : 8;
-        const double kw = lower ? g.K - j0 : j0 + w;
-        for (int tm = 0; tm < ceil_div(g.M, rblock); tm++) {
-          tasks.push_back({(int)d, tm, tn, nw});
-          work.push_back(kw * nw * std::min(rblock, g.M - tm * rblock));
+        for (int ks = 0; ks < g.ksplit; ks++) {
+          const int kb = ks * kchunk, ke = std::min(g.K, kb + kchunk);
+          if (kb >= ke) continue;
+          const double kw = tri == GEMM_TRI_LOWER_B ? g.K - j0 : tri == GEMM_TRI_UPPER_B ? j0 + w : ke - kb;
+          for (int tm = 0; tm < ceil_div(g.M, kRowsBlock); tm++) {
+            tasks.push_back({(int)d, tm, tn, nw + 16 * ks});
+            work.push_back(kw * nw * std::min(kRowsBlock, g.M - tm * kRowsBlock));
+          }
         }
       }
     } else {
@@ -265,7 +268,7 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
                    (double)g.M * g.N * ((g.atomic || g.beta != 0.0) ? 2.0 : 1.0));
   }
   if (tasks.empty()) return;
-  if (cfg == GEMM_TRI_ROWS) {  // longest tasks first: CTAs start in task order
+  if (cfg == GEMM_ROWS) {  // longest tasks first: CTAs start in task order
     std::vector<size_t> order(tasks.size());
     for (size_t i = 0; i < order.size(); i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
@@ -581,7 +584,7 @@ int build_factor_plan(pselinv_ctx* h) {
       add_gemm_step(P, dt, GEMM_32x32, upd, (int)lev);
     }
     add_tri_step(P, H, tri, (int)lev, 0);
-    add_gemm_step(P, dt, GEMM_TRI_ROWS, trsm, (int)lev);
+    add_gemm_step(P, dt, GEMM_ROWS, trsm, (int)lev);
     add_gemm_step(P, dt, cfg, schur, (int)lev);
     if (!gt.empty()) {
       Step sc;
@@ -712,6 +715,15 @@ void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool
     bytes += 2.0 * S * ((double)g.M + g.N) * g.K32 * 32 +
              8.0 * g.M * g.N * (g.atomic ? 2.0 : 1.0) * g.cscale;
   }
+  // longest tasks (most K blocks) first
+  auto kblocks = [&](const OzTask& t) {
+    const OzDesc& g = descs[t.d];
+    int per = (g.K32 + g.ksplit - 1) / g.ksplit;
+    per = (per + kOzChunkBlocks - 1) / kOzChunkBlocks * kOzChunkBlocks;
+    return std::min(g.K32, (t.ks + 1) * per) - t.ks * per;
+  };
+  std::stable_sort(tasks.begin(), tasks.end(),
+                   [&](const OzTask& a, const OzTask& b) { return kblocks(a) > kblocks(b); });
   Step st;
   st.kind = ST_OZGEMM;
   st.cfg = S;
@@ -1041,7 +1053,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
         }
       }
     const size_t first = P.steps.size();
-    add_gemm_step(P, dt, tuned_value(h, precision, lev, 0, GEMM_TRI_ROWS), norm, lev, 0);
+    add_gemm_step(P, dt, tuned_value(h, precision, lev, 0, GEMM_ROWS), norm, lev, 0);
     if (split) add_ozaki_normalize(h, P, lev, nb, wbase, norm_base);
     for (size_t i = first; i < P.steps.size(); i++) P.steps[i].side = 1;
     if (P.steps.size() > first) {
@@ -1082,6 +1094,11 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
     }
     const int slot_main = precision == PSELINV_PREC_OZAKI_FP16 ? 4 : 1;
     const int slot_diag = precision == PSELINV_PREC_OZAKI_FP16 ? 5 : 2;
+    // FP64 products of narrow supernodes (N = s): row panels, else tiles
+    int64_t smax = 0;
+    for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++)
+      smax = std::max<int64_t>(smax, H.sn_width[H.level_sn[i]]);
+    const int cfg_lev = smax <= 16 ? GEMM_ROWS : cfg;
     for (const auto& grp : groups) {
       if (split_level) {
         add_ozaki_level(h, P, grp, nb, gbase, (int)lev, max_cursor);
@@ -1126,10 +1143,10 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       g.offs = P.push(gofs);
       g.level = (int)lev;
       P.steps.push_back(g);
-      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_main, cfg), main, (int)lev,
+      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_main, cfg_lev), main, (int)lev,
                     slot_main);
       add_copy_step(P, mirror, (int)lev, es);
-      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_diag, cfg), dg, (int)lev,
+      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_diag, cfg_lev), dg, (int)lev,
                     slot_diag);
     }
     if (P.steps.size() > first_main) P.steps[first_main].wait = EV_LEVEL + (int)lev;
@@ -1611,8 +1628,7 @@ int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_
 template <class RB>
 static int model_tune(pselinv_ctx* h, Plan& P0, int precision, pselinv_model_t model, RB rebuild) {
   if (!model) return PSELINV_ERR_ARG;
-  // the normalisation's products (slot 0) have triangular B: one candidate more
-  static const int gemm_cands[4] = {GEMM_64x64, GEMM_32x32, GEMM_128x64, GEMM_TRI_ROWS};
+  static const int gemm_cands[4] = {GEMM_64x64, GEMM_32x32, GEMM_128x64, GEMM_ROWS};
   static const int ks_cands[5] = {1, 2, 4, 8, 16};
   std::vector<std::tuple<int, int, int>> keys;
   std::vector<pselinv_tune_record> q;
@@ -1621,7 +1637,7 @@ static int model_tune(pselinv_ctx* h, Plan& P0, int precision, pselinv_model_t m
     const auto key = std::make_tuple(s.level, s.slot, (int)s.kind);
     if (std::find(keys.begin(), keys.end(), key) != keys.end()) continue;
     keys.push_back(key);
-    const int nc = s.kind == ST_GEMM ? (s.slot == 0 ? 4 : 3) : 5;
+    const int nc = s.kind == ST_GEMM ? 4 : 5;
     for (int v = 0; v < nc; v++) {
       pselinv_tune_record r{};
       r.precision = precision;
@@ -1673,8 +1689,7 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
   if (mode == PSELINV_TUNE_MODEL) return model_tune(h, P0, precision, model, rebuild);
   if (mode != PSELINV_TUNE_EXHAUSTIVE) return PSELINV_ERR_ARG;
 
-  // the normalisation's products (slot 0) have triangular B: one candidate more
-  static const int gemm_cands[4] = {GEMM_64x64, GEMM_32x32, GEMM_128x64, GEMM_TRI_ROWS};
+  static const int gemm_cands[4] = {GEMM_64x64, GEMM_32x32, GEMM_128x64, GEMM_ROWS};
   static const int ks_cands[5] = {1, 2, 4, 8, 16};
   struct Key {
     int level, slot, kind;
@@ -1734,9 +1749,7 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
   const int nlev = (int)h->H.level_ptr.size() - 1;
   if (precision == PSELINV_PREC_FP64) {
     for (int v = 0; v < 4; v++) {
-      for (const Key& k : keys)
-        h->tuned[std::make_tuple(precision, k.level, k.slot)] =
-            k.slot == 0 || v < 3 ? gemm_cands[v] : GEMM_32x32;
+      for (const Key& k : keys) h->tuned[std::make_tuple(precision, k.level, k.slot)] = gemm_cands[v];
       rc = measure(-1);
       if (rc != PSELINV_OK) return rc;
     }
@@ -1752,8 +1765,8 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
       rc = measure(0);
       if (rc != PSELINV_OK) return rc;
     }
-    // phase B: every level FP64, tile shapes
-    for (int v = 0; v < 3; v++) {
+    // phase B: every level FP64, tile shapes and row panels
+    for (int v = 0; v < 4; v++) {
       for (int l = 0; l < nlev; l++) {
         h->tuned[std::make_tuple(precision, l, 3)] = 1;
         h->tuned[std::make_tuple(precision, l, 4)] = gemm_cands[v];
@@ -1929,14 +1942,14 @@ int pselinv_plan_set(pselinv_t h, int precision, const int32_t* in, int64_t coun
   for (int64_t i = 0; i < count; i++) {
     const int lev = in[3 * i], slot = in[3 * i + 1], v = in[3 * i + 2];
     bool ok = lev >= 0 && lev < nlev && slot >= 0 && slot <= 5;
-    if (ok && precision == PSELINV_PREC_FP64) ok = slot <= 2 && v >= 0 && v <= (slot == 0 ? 3 : 2);
+    if (ok && precision == PSELINV_PREC_FP64) ok = slot <= 2 && v >= 0 && v <= 3;
     if (ok && precision == PSELINV_PREC_OZAKI_FP16) {
       if (slot == 1 || slot == 2)
         ok = v == 1 || v == 2 || v == 4 || v == 8 || v == 16;
       else if (slot == 3)
         ok = v == 0 || v == 1;
       else
-        ok = v >= 0 && v <= (slot == 0 ? 3 : 2);
+        ok = v >= 0 && v <= 3;
     }
     if (!ok) return PSELINV_ERR_ARG;
     entries.push_back({std::make_tuple(precision, lev, slot), v});

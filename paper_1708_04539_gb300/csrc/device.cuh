@@ -202,22 +202,22 @@ void launch_wait_selftest(int* err, unsigned long long budget_ns, cudaStream_t s
 // ---------------------------------------------------------------------------
 enum DType { DT_F64 = 1, DT_C128 = 2 };
 
-// GEMM tile configurations (rows x cols of C per CTA).  GEMM_TRI_ROWS is
-// the product with a square triangular op(B) (exactly one of
-// GEMM_TRI_LOWER_B / GEMM_TRI_UPPER_B; transA = 0, no atomics, no K split):
-// one thread per row of C and a chunk of columns per task, the zero
-// triangle of the diagonal block skipped exactly.  Its tasks are {d, row
-// block of kTriRowsBlock rows, chunk of tri_rows_chunk() columns, width
-// NW in {4, 8} that the kernel computes for the chunk}.  Short tasks
-// (64 rows x 8 columns) let the CTAs of a concurrent stream in sooner.
-enum GemmCfg { GEMM_64x64 = 0, GEMM_32x32 = 1, GEMM_128x64 = 2, GEMM_TRI_ROWS = 3, GEMM_NCFG = 4 };
-constexpr int kTriRowsBlock = 64;
-constexpr int kTriRowsChunk = 8;
-inline int tri_rows_chunk(int) { return kTriRowsChunk; }
-inline bool tri_rows_eligible(const GemmDesc& d) {
+// GEMM configurations: tiles (rows x cols of C per CTA) or GEMM_ROWS, row
+// panels: one thread per row of C and a chunk of kRowsChunk columns per
+// task (64 rows x 8 columns: short tasks, no padding of narrow products,
+// and the zero triangle of a triangular op(B) skipped exactly).  Its tasks
+// are {d, row block, column chunk, NW + 16 x K chunk}, NW in {4, 8} the
+// width the kernel computes for the chunk.
+enum GemmCfg { GEMM_64x64 = 0, GEMM_32x32 = 1, GEMM_128x64 = 2, GEMM_ROWS = 3, GEMM_NCFG = 4 };
+constexpr int kRowsBlock = 64;
+constexpr int kRowsChunk = 8;
+// a triangular op(B) (at most one of LOWER_B / UPPER_B) must be square and
+// unsplit; an upper op(A) only goes with a lower op(B)
+inline bool rows_eligible(const GemmDesc& d) {
   const int t = d.tri & (GEMM_TRI_LOWER_B | GEMM_TRI_UPPER_B);
-  return (t == GEMM_TRI_LOWER_B || t == GEMM_TRI_UPPER_B) && d.transA == 0 && d.atomic == 0 &&
-         d.ksplit == 1 && d.N == d.K && !((d.tri & GEMM_TRI_UPPER_A) && t == GEMM_TRI_UPPER_B);
+  if (t == (GEMM_TRI_LOWER_B | GEMM_TRI_UPPER_B)) return false;
+  if (t != 0 && (d.N != d.K || d.ksplit != 1)) return false;
+  return !(d.tri & GEMM_TRI_UPPER_A) || t == GEMM_TRI_LOWER_B;
 }
 void launch_gemm(int dtype, int cfg, const GemmDesc* descs, const GemmTask* tasks, int ntasks,
                  int grid, cudaStream_t st);

@@ -389,39 +389,43 @@ tri_inv_small_kernel(SymDev S, const T* store, T* out, const int64_t* __restrict
   }
 }
 
-// Product with a square triangular op(B): C(m, n) = alpha sum_k A(m, k)
-// op(B)(k, n) (+ beta C), one thread per row m, columns j0 .. j0 + NW - 1.
-// A lower op(B) is zero for k < n, an upper one for k > n: in the diagonal
-// block (k in [j0, j0 + NW)) only the triangle is multiplied, the other
-// k run over all NW columns.  An upper A (GEMM_TRI_UPPER_A, lower op(B)
-// only) starts every warp at its first row.  Lanes past M read row M - 1
-// and columns past N read column N - 1 (in bounds; never stored).  FP64
-// throughput is the bound: the loads of op(B) are warp-uniform, the loads
-// of A coalesced along m.
-template <typename T, int NW, bool LOWER>
-__device__ __forceinline__ void tri_rows_task(const GemmDesc& d, int m, int warp_m0, int j0) {
+// Row-panel product C(m, n) = alpha sum_k op(A)(m, k) op(B)(k, n) (+ beta
+// C, or atomically added), one thread per row m and columns j0 .. j0 +
+// NW - 1, k over the task's K chunk.  TRI = 1 (op(B) lower triangular, zero
+// for k < n) or 2 (upper, zero for k > n): square op(B), one K chunk; in the
+// diagonal block (k in [j0, j0 + NW)) only the triangle is multiplied, the
+// other k run over all NW columns.  An upper op(A) (GEMM_TRI_UPPER_A, with a
+// lower op(B)) starts every warp at its first row.  Lanes past M read row
+// M - 1 and columns past N read column N - 1 (in bounds; never stored).
+// FP64 throughput is the bound: the loads of op(B) are warp-uniform, those
+// of A coalesced along m (or, transposed, one row per lane reused from L1).
+template <typename T, int NW, int TRI>
+__device__ __forceinline__ void rows_task(const GemmDesc& d, int m, int warp_m0, int j0, int kb,
+                                          int ke) {
   const T* __restrict__ B = (const T*)d.B;
-  const T* __restrict__ Ar = (const T*)d.A + min(m, d.M - 1);
-  const int K = d.K, nlast = d.N - 1;
+  const int mm = min(m, d.M - 1);
+  const T* __restrict__ Ar = (const T*)d.A + (d.transA ? (int64_t)mm * d.lda : (int64_t)mm);
+  const int64_t ak = d.transA ? 1 : d.lda;
+  const int nlast = d.N - 1;
   const int64_t sk = d.transB ? d.ldb : 1, sn = d.transB ? 1 : d.ldb;
   auto bval = [&](int k, int q) { return B[(int64_t)k * sk + (int64_t)min(j0 + q, nlast) * sn]; };
   T acc[NW];
 #pragma unroll
   for (int q = 0; q < NW; q++) acc[q] = sc_zero(T());
-  // k in [kb, ke) over all NW columns, the operands of k + 1 loaded while
+  // k in [k0, k1) over all NW columns, the operands of k + 1 loaded while
   // those of k are multiplied (a warp alone on its FP64 unit stays busy)
-  auto full_range = [&](int kb, int ke) {
-    if (kb >= ke) return;
-    T an = Ar[(int64_t)kb * d.lda], bn[NW];
+  auto full_range = [&](int k0, int k1) {
+    if (k0 >= k1) return;
+    T an = Ar[(int64_t)k0 * ak], bn[NW];
 #pragma unroll
-    for (int q = 0; q < NW; q++) bn[q] = bval(kb, q);
-    for (int k = kb; k < ke; k++) {
+    for (int q = 0; q < NW; q++) bn[q] = bval(k0, q);
+    for (int k = k0; k < k1; k++) {
       const T a = an;
       T b[NW];
 #pragma unroll
       for (int q = 0; q < NW; q++) b[q] = bn[q];
-      if (k + 1 < ke) {
-        an = Ar[(int64_t)(k + 1) * d.lda];
+      if (k + 1 < k1) {
+        an = Ar[(int64_t)(k + 1) * ak];
 #pragma unroll
         for (int q = 0; q < NW; q++) bn[q] = bval(k + 1, q);
       }
@@ -429,27 +433,29 @@ __device__ __forceinline__ void tri_rows_task(const GemmDesc& d, int m, int warp
       for (int q = 0; q < NW; q++) acc[q] = fma_s(a, b[q], acc[q]);
     }
   };
-  if (LOWER) {
+  if (TRI == 1) {
     const int kstart = (d.tri & GEMM_TRI_UPPER_A) ? max(j0, warp_m0) : j0;
 #pragma unroll
     for (int kk = 0; kk < NW; kk++) {
       const int k = j0 + kk;
-      if (k < kstart || k >= K) continue;
-      const T a = Ar[(int64_t)k * d.lda];
+      if (k < kstart || k >= ke) continue;
+      const T a = Ar[(int64_t)k * ak];
 #pragma unroll
       for (int q = 0; q <= kk; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);
     }
-    full_range(max(j0 + NW, kstart), K);
-  } else {
+    full_range(max(j0 + NW, kstart), ke);
+  } else if (TRI == 2) {
     full_range(0, j0);
 #pragma unroll
     for (int kk = 0; kk < NW; kk++) {
       const int k = j0 + kk;
-      if (k >= K) break;
-      const T a = Ar[(int64_t)k * d.lda];
+      if (k >= ke) break;
+      const T a = Ar[(int64_t)k * ak];
 #pragma unroll
       for (int q = kk; q < NW; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);
     }
+  } else {
+    full_range(kb, ke);
   }
   if (m >= d.M) return;
   T* __restrict__ C = (T*)d.C + m;
@@ -458,34 +464,43 @@ __device__ __forceinline__ void tri_rows_task(const GemmDesc& d, int m, int warp
     const int n = j0 + q;
     if (n >= d.N) break;
     T v = scale_s(acc[q], d.alpha);
+    if (d.atomic) {
+      atomic_add_s(C + (int64_t)n * d.ldc, v);
+      continue;
+    }
     if (d.beta != 0.0) v = add_s(v, scale_s(C[(int64_t)n * d.ldc], d.beta));
     C[(int64_t)n * d.ldc] = v;
   }
 }
 
-template <typename T, bool LOWER>
-__device__ __forceinline__ void tri_rows_dispatch(const GemmDesc& d, int nw, int m, int warp_m0,
-                                                  int j0) {
+template <typename T, int TRI>
+__device__ __forceinline__ void rows_dispatch(const GemmDesc& d, int nw, int m, int warp_m0, int j0,
+                                              int kb, int ke) {
   if (nw == 4)
-    tri_rows_task<T, 4, LOWER>(d, m, warp_m0, j0);
+    rows_task<T, 4, TRI>(d, m, warp_m0, j0, kb, ke);
   else
-    tri_rows_task<T, 8, LOWER>(d, m, warp_m0, j0);
+    rows_task<T, 8, TRI>(d, m, warp_m0, j0, kb, ke);
 }
 
+// Tasks {d, row block, column chunk, NW + 16 x K chunk index}
 template <typename T>
-__global__ void __launch_bounds__(kTriRowsBlock)
-tri_rows_kernel(const GemmDesc* __restrict__ descs, const GemmTask* __restrict__ tasks, int ntasks) {
+__global__ void __launch_bounds__(kRowsBlock)
+rows_gemm_kernel(const GemmDesc* __restrict__ descs, const GemmTask* __restrict__ tasks, int ntasks) {
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const GemmTask task = tasks[t];
     const GemmDesc d = descs[task.d];
-    const int m = task.tm * kTriRowsBlock + (int)threadIdx.x;
+    const int m = task.tm * kRowsBlock + (int)threadIdx.x;
     const int warp_m0 = m & ~31;
     if (warp_m0 >= d.M) continue;  // whole warp past the last row
-    const int j0 = task.tn * kTriRowsChunk;
+    const int j0 = task.tn * kRowsChunk, nw = task.ks & 15, kc = task.ks >> 4;
+    const int kchunk = (d.K + d.ksplit - 1) / d.ksplit;
+    const int kb = kc * kchunk, ke = min(d.K, kb + kchunk);
     if (d.tri & GEMM_TRI_LOWER_B)
-      tri_rows_dispatch<T, true>(d, task.ks, m, warp_m0, j0);
+      rows_dispatch<T, 1>(d, nw, m, warp_m0, j0, kb, ke);
+    else if (d.tri & GEMM_TRI_UPPER_B)
+      rows_dispatch<T, 2>(d, nw, m, warp_m0, j0, kb, ke);
     else
-      tri_rows_dispatch<T, false>(d, task.ks, m, warp_m0, j0);
+      rows_dispatch<T, 0>(d, nw, m, warp_m0, j0, kb, ke);
   }
 }
 
@@ -511,12 +526,12 @@ int gemm_tile_n(int dtype, int cfg) {
 
 void launch_gemm(int dtype, int cfg, const GemmDesc* descs, const GemmTask* tasks, int ntasks,
                  int grid, cudaStream_t st) {
-  if (cfg == GEMM_TRI_ROWS) {
+  if (cfg == GEMM_ROWS) {
     if (ntasks <= 0) return;
     if (dtype == DT_F64)
-      tri_rows_kernel<double><<<grid, kTriRowsBlock, 0, st>>>(descs, tasks, ntasks);
+      rows_gemm_kernel<double><<<grid, kRowsBlock, 0, st>>>(descs, tasks, ntasks);
     else
-      tri_rows_kernel<cdouble><<<grid, kTriRowsBlock, 0, st>>>(descs, tasks, ntasks);
+      rows_gemm_kernel<cdouble><<<grid, kRowsBlock, 0, st>>>(descs, tasks, ntasks);
     return;
   }
   if (dtype == DT_F64) {

@@ -137,15 +137,16 @@ def test_plan_cache_round_trip_host_only():
     h.plan_set(triples, ps.PREC_OZAKI_FP16)
     assert h.plan_get(ps.PREC_OZAKI_FP16) == sorted(triples)
     assert h.plan_get(ps.PREC_FP64) == []
-    h.plan_set(triples + [(1, 0, 3)], ps.PREC_OZAKI_FP16)  # row panels: slot 0 only
-    assert h.plan_get(ps.PREC_OZAKI_FP16) == sorted(triples + [(1, 0, 3)])
+    rows = [(1, 0, 3), (1, 4, 3), (1, 5, 3)]  # row panels in the GEMM slots
+    h.plan_set(triples + rows, ps.PREC_OZAKI_FP16)
+    assert h.plan_get(ps.PREC_OZAKI_FP16) == sorted(triples + rows)
     h.plan_set(triples, ps.PREC_OZAKI_FP16)
-    for bad in [(nlev, 0, 0), (-1, 0, 0), (0, 6, 0), (0, 1, 3), (0, 3, 2), (0, 4, 3),
-                (0, 0, 4), (0, 5, 3)]:
+    for bad in [(nlev, 0, 0), (-1, 0, 0), (0, 6, 0), (0, 1, 3), (0, 3, 2), (0, 4, 4),
+                (0, 0, 4), (0, 5, -1)]:
         with pytest.raises(ps.PselinvError):
             h.plan_set(triples + [bad], ps.PREC_OZAKI_FP16)
         assert h.plan_get(ps.PREC_OZAKI_FP16) == sorted(triples)
-    for bad in [(0, 3, 0), (0, 1, 3), (0, 0, 4)]:  # no precision slot in the FP64 plan
+    for bad in [(0, 3, 0), (0, 1, 4), (0, 0, 4)]:  # no precision slot in the FP64 plan
         with pytest.raises(ps.PselinvError):
             h.plan_set([bad], ps.PREC_FP64)
     h.plan_set([(0, 0, 3)], ps.PREC_FP64)

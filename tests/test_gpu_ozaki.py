@@ -146,11 +146,13 @@ def test_split_config2_full_size(torch):
 
 @pytest.mark.parametrize("name,make", [CASES[2], CASES[3], ("upwind12_c", lambda: gen.stencil27_complex(8, 66, max_sn=64))],
                          ids=["upwind16_wide", "dg", "stencil27_c"])
-@pytest.mark.parametrize("norm_cfg", [1, 3], ids=["tiles32", "rows"])
-def test_normalisation_kernels_match_oracle(torch, name, make, norm_cfg):
-    """The normalisation's triangular products (Lhat, Uhat^T, D_K) through
-    each of their kernels -- 32 x 32 tiles and row panels with exact
-    triangles -- in both plans, over two sweeps of one handle."""
+@pytest.mark.parametrize("cfg", [1, 3], ids=["tiles32", "rows"])
+def test_fp64_product_kernels_match_oracle(torch, name, make, cfg):
+    """Every FP64 product of the sweep through one kernel -- 32 x 32 tiles or
+    row panels (exact triangles for the normalisation's Lhat, Uhat^T and
+    D_K; transposed G for step 5; atomic K chunks for step 4): the FP64 plan,
+    and the split plan with every other level in FP64, over two sweeps of
+    one handle."""
     import paper_1708_04539_gb300 as ps
     from paper_1708_04539_gb300.binding import supernodal_coordinates
     p = make()
@@ -158,9 +160,9 @@ def test_normalisation_kernels_match_oracle(torch, name, make, norm_cfg):
     h.factor(torch.from_numpy(np.ascontiguousarray(p.values)).cuda())
     nlev = h.structure()["nlevels"]
     st = h.structure()
-    h.plan_set([(lev, 0, norm_cfg) for lev in range(nlev)], ps.PREC_FP64)
-    h.plan_set([(lev, 0, norm_cfg) for lev in range(nlev)] + [(lev, 3, 0) for lev in range(nlev)],
-               ps.PREC_OZAKI_FP16)
+    h.plan_set([(lev, slot, cfg) for lev in range(nlev) for slot in (0, 1, 2)], ps.PREC_FP64)
+    h.plan_set([(lev, slot, cfg) for lev in range(nlev) for slot in (0, 4, 5)] +
+               [(lev, 3, lev % 2) for lev in range(nlev)], ps.PREC_OZAKI_FP16)
     _, orows, ocols, ovals = oracle_coo(p, 0, 20)
     grows, gcols = supernodal_coordinates(st)
     gi, oi = np.argsort(grows * p.n + gcols), np.argsort(orows * p.n + ocols)
