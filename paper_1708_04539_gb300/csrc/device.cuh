@@ -259,7 +259,8 @@ void launch_gather(int dtype, const SymDev& S, const void* store, void* out,
 // store(R_K, R_K) -= Sc_K (atomic) from src + sofs[task]; tasks as for gather
 void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src,
                         const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st);
-void launch_copy(int dtype, const CopySeg* segs, int nseg, cudaStream_t st);
+// per_seg CTAs per segment (the plan sizes it by the longest segment)
+void launch_copy(int dtype, const CopySeg* segs, int nseg, int per_seg, cudaStream_t st);
 // out[p] = store[inst * storage + value_map[p]]
 void launch_extract(int dtype, const SymDev& S, const void* store, int inst, void* out,
                     cudaStream_t st);

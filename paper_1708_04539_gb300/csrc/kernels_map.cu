@@ -254,9 +254,9 @@ void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src
                                                            (const cdouble*)src, sofs, tasks, ntasks);
 }
 
-void launch_copy(int dtype, const CopySeg* segs, int nseg, cudaStream_t st) {
+void launch_copy(int dtype, const CopySeg* segs, int nseg, int per_seg, cudaStream_t st) {
   if (nseg <= 0) return;
-  dim3 grid(8, nseg < 65535 ? nseg : 65535);
+  dim3 grid(per_seg > 0 ? per_seg : 8, nseg < 65535 ? nseg : 65535);
   if (dtype == DT_F64)
     copy_kernel<double><<<grid, kThreads, 0, st>>>(segs, nseg);
   else
