@@ -407,9 +407,14 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
                       maxima_bytes(H, nb));
 }
 
-// default FP64 tile config before tuning: 32 x 32 tiles (what the tuner
-// keeps for the normalisation and the FP64 levels of the 40^3 sweep)
-int choose_cfg(int dtype) { return dtype == DT_F64 ? GEMM_32x32 : GEMM_64x64; }
+// default FP64 kernel before tuning: row panels for level launches (what
+// the tuner keeps for most FP64 launches of the 40^3 sweep, and faster than
+// tiles on the factorisation's Schur products); 32 x 32 tiles for launches
+// of one supernode's products, where more, smaller tasks fill the GPU
+// better (40^3 per-supernode sweep 274 vs 318 ms)
+int choose_cfg(int schedule) {
+  return schedule == PSELINV_SCHED_PER_SUPERNODE ? GEMM_32x32 : GEMM_ROWS;
+}
 
 int tuned_value(const pselinv_ctx* h, int prec, int level, int slot, int dflt) {
   auto it = h->tuned.find(std::make_tuple(prec, level, slot));
@@ -992,7 +997,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   const size_t es = h->esize;
   const int dt = h->dtype;
   const int64_t nb = h->nbatch;
-  const int cfg = choose_cfg(dt);
+  const int cfg = choose_cfg(schedule);
   // W region: Linv | Uinv per (instance, supernode)
   std::vector<int64_t> wbase((size_t)(nb * H.ns));
   int64_t off = 0;
@@ -1100,11 +1105,6 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
     }
     const int slot_main = precision == PSELINV_PREC_OZAKI_FP16 ? 4 : 1;
     const int slot_diag = precision == PSELINV_PREC_OZAKI_FP16 ? 5 : 2;
-    // FP64 products of narrow supernodes (N = s): row panels, else tiles
-    int64_t smax = 0;
-    for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++)
-      smax = std::max<int64_t>(smax, H.sn_width[H.level_sn[i]]);
-    const int cfg_lev = smax <= 16 ? GEMM_ROWS : cfg;
     for (const auto& grp : groups) {
       if (split_level) {
         add_ozaki_level(h, P, grp, nb, gbase, (int)lev, max_cursor);
@@ -1149,10 +1149,10 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       g.offs = P.push(gofs);
       g.level = (int)lev;
       P.steps.push_back(g);
-      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_main, cfg_lev), main, (int)lev,
+      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_main, cfg), main, (int)lev,
                     slot_main);
       add_copy_step(P, mirror, (int)lev, es);
-      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_diag, cfg_lev), dg, (int)lev,
+      add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_diag, cfg), dg, (int)lev,
                     slot_diag);
     }
     if (P.steps.size() > first_main) P.steps[first_main].wait = EV_LEVEL + (int)lev;
