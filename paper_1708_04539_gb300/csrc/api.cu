@@ -244,9 +244,11 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
         const int j0 = tn * kRowsChunk, w = std::min(kRowsChunk, g.N - j0);
         const int nw = w <= 4 ? 4 : 8;
         for (int ks = 0; ks < g.ksplit; ks++) {
-          const int kb = ks * kchunk, ke = std::min(g.K, kb + kchunk);
+          int kb = ks * kchunk, ke = std::min(g.K, kb + kchunk);
+          if (tri == GEMM_TRI_LOWER_B) kb = std::max(kb, j0);       // op(B)(k, n) = 0 for k < n
+          if (tri == GEMM_TRI_UPPER_B) ke = std::min(ke, j0 + w);   // op(B)(k, n) = 0 for k > n
           if (kb >= ke) continue;
-          const double kw = tri == GEMM_TRI_LOWER_B ? g.K - j0 : tri == GEMM_TRI_UPPER_B ? j0 + w : ke - kb;
+          const double kw = ke - kb;
           for (int tm = 0; tm < ceil_div(g.M, kRowsBlock); tm++) {
             tasks.push_back({(int)d, tm, tn, nw + 16 * ks});
             work.push_back(kw * nw * std::min(kRowsBlock, g.M - tm * kRowsBlock));
@@ -627,6 +629,9 @@ void add_zero_step(Plan& P, const std::vector<CopySeg>& segs, int level) {
   if (segs.empty()) return;
   Step z;
   z.kind = ST_ZERO;
+  int64_t longest = 0;
+  for (const CopySeg& g : segs) longest = std::max(longest, g.count);
+  z.grid = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (longest + 2047) / 2048));
   z.n = (int)segs.size();
   z.tasks = P.push(segs);
   z.level = level;
@@ -988,6 +993,9 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   add_ozgemm_step(P, dg, S, lev, true, ks_diag, 2);
 }
 
+// largest K split of the normalisation's products
+constexpr int kNormMaxKsplit = 8;
+
 int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   const HostSym& H = h->H;
   const bool sym = h->opts.symmetric != 0;
@@ -1064,6 +1072,25 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
         }
       }
     const size_t first = P.steps.size();
+    // levels of few wide supernodes (near the roots): split K so that the
+    // launch has tasks for every SM, its K loops being the level's latency;
+    // the outputs are then zeroed and accumulated
+    int64_t ntask = 0, kmax = 0;
+    for (const GemmDesc& g : norm) {
+      ntask += (int64_t)ceil_div(g.M, kRowsBlock) * ceil_div(g.N, kRowsChunk);
+      kmax = std::max<int64_t>(kmax, g.K);
+    }
+    int ks = 1;
+    while (ks < kNormMaxKsplit && ntask * ks < 152 * 8 && kmax / (2 * ks) >= 32) ks *= 2;
+    if (ks > 1) {
+      std::vector<CopySeg> zero;
+      for (GemmDesc& g : norm) {
+        g.ksplit = ks;
+        g.atomic = 1;
+        zero.push_back({nullptr, g.C, (int64_t)g.M * g.N * (int64_t)(es / 8)});
+      }
+      add_zero_step(P, zero, lev);
+    }
     add_gemm_step(P, dt, tuned_value(h, precision, lev, 0, GEMM_ROWS), norm, lev, 0);
     if (split) add_ozaki_normalize(h, P, lev, nb, wbase, norm_base);
     for (size_t i = first; i < P.steps.size(); i++) P.steps[i].side = 1;
@@ -1214,7 +1241,7 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
                         h->derr, s.side == 0, st);
       break;
     case ST_ZERO:
-      launch_zero((const CopySeg*)(a + s.tasks), s.n, st);
+      launch_zero((const CopySeg*)(a + s.tasks), s.n, s.grid, st);
       break;
   }
 }

@@ -192,7 +192,7 @@ void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bo
                   cudaStream_t st);
 void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
                        bool persistent, cudaStream_t st);
-void launch_zero(const CopySeg* segs, int nseg, cudaStream_t st);
+void launch_zero(const CopySeg* segs, int nseg, int per_seg, cudaStream_t st);
 // a kernel whose only wait never completes: it gives up after budget_ns and
 // records DEV_TIMEOUT in err[0]
 void launch_wait_selftest(int* err, unsigned long long budget_ns, cudaStream_t st);
@@ -211,12 +211,12 @@ enum DType { DT_F64 = 1, DT_C128 = 2 };
 enum GemmCfg { GEMM_64x64 = 0, GEMM_32x32 = 1, GEMM_128x64 = 2, GEMM_ROWS = 3, GEMM_NCFG = 4 };
 constexpr int kRowsBlock = 64;
 constexpr int kRowsChunk = 8;
-// a triangular op(B) (at most one of LOWER_B / UPPER_B) must be square and
-// unsplit; an upper op(A) only goes with a lower op(B)
+// a triangular op(B) (at most one of LOWER_B / UPPER_B) must be square; an
+// upper op(A) only goes with a lower op(B)
 inline bool rows_eligible(const GemmDesc& d) {
   const int t = d.tri & (GEMM_TRI_LOWER_B | GEMM_TRI_UPPER_B);
   if (t == (GEMM_TRI_LOWER_B | GEMM_TRI_UPPER_B)) return false;
-  if (t != 0 && (d.N != d.K || d.ksplit != 1)) return false;
+  if (t != 0 && d.N != d.K) return false;
   return !(d.tri & GEMM_TRI_UPPER_A) || t == GEMM_TRI_LOWER_B;
 }
 void launch_gemm(int dtype, int cfg, const GemmDesc* descs, const GemmTask* tasks, int ntasks,

@@ -391,10 +391,10 @@ tri_inv_small_kernel(SymDev S, const T* store, T* out, const int64_t* __restrict
 
 // Row-panel product C(m, n) = alpha sum_k op(A)(m, k) op(B)(k, n) (+ beta
 // C, or atomically added), one thread per row m and columns j0 .. j0 +
-// NW - 1, k over the task's K chunk.  TRI = 1 (op(B) lower triangular, zero
-// for k < n) or 2 (upper, zero for k > n): square op(B), one K chunk; in the
-// diagonal block (k in [j0, j0 + NW)) only the triangle is multiplied, the
-// other k run over all NW columns.  An upper op(A) (GEMM_TRI_UPPER_A, with a
+// NW - 1, k over the task's K chunk [kb, ke).  TRI = 1 (op(B) lower
+// triangular, zero for k < n) or 2 (upper, zero for k > n): square op(B);
+// in the diagonal block (k in [j0, j0 + NW)) only the triangle is
+// multiplied, the other k of the chunk run over all NW columns.  An upper op(A) (GEMM_TRI_UPPER_A, with a
 // lower op(B)) starts every warp at its first row.  Lanes past M read row
 // M - 1 and columns past N read column N - 1 (in bounds; never stored).
 // FP64 throughput is the bound: the loads of op(B) are warp-uniform, those
@@ -434,7 +434,7 @@ __device__ __forceinline__ void rows_task(const GemmDesc& d, int m, int warp_m0,
     }
   };
   if (TRI == 1) {
-    const int kstart = (d.tri & GEMM_TRI_UPPER_A) ? max(j0, warp_m0) : j0;
+    const int kstart = max(kb, (d.tri & GEMM_TRI_UPPER_A) ? max(j0, warp_m0) : j0);
 #pragma unroll
     for (int kk = 0; kk < NW; kk++) {
       const int k = j0 + kk;
@@ -445,11 +445,11 @@ __device__ __forceinline__ void rows_task(const GemmDesc& d, int m, int warp_m0,
     }
     full_range(max(j0 + NW, kstart), ke);
   } else if (TRI == 2) {
-    full_range(0, j0);
+    full_range(kb, min(j0, ke));
 #pragma unroll
     for (int kk = 0; kk < NW; kk++) {
       const int k = j0 + kk;
-      if (k >= ke) break;
+      if (k < kb || k >= ke) continue;
       const T a = Ar[(int64_t)k * ak];
 #pragma unroll
       for (int q = kk; q < NW; q++) acc[q] = fma_s(a, bval(k, q), acc[q]);

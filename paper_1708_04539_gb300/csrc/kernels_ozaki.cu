@@ -588,9 +588,9 @@ void launch_wait_selftest(int* err, unsigned long long budget_ns, cudaStream_t s
   wait_selftest_kernel<<<1, 32, 0, st>>>(err, budget_ns);
 }
 
-void launch_zero(const CopySeg* segs, int nseg, cudaStream_t st) {
+void launch_zero(const CopySeg* segs, int nseg, int per_seg, cudaStream_t st) {
   if (nseg <= 0) return;
-  dim3 grid(8, nseg < 65535 ? nseg : 65535);
+  dim3 grid(per_seg > 0 ? per_seg : 8, nseg < 65535 ? nseg : 65535);
   zero_kernel<<<grid, 256, 0, st>>>(segs, nseg);
 }
 
