@@ -193,7 +193,8 @@ enum pselinv_step_kind {
   PSELINV_STEP_GEMM = 0, PSELINV_STEP_TRI_INV = 1, PSELINV_STEP_DIAG_LU = 2,
   PSELINV_STEP_GATHER = 3, PSELINV_STEP_SCATTER_SUB = 4, PSELINV_STEP_COPY = 5,
   PSELINV_STEP_MEMSET = 6, PSELINV_STEP_SCATTER_VALUES = 7, PSELINV_STEP_SLICE = 8,
-  PSELINV_STEP_OZAKI_GEMM = 9, PSELINV_STEP_RECOMBINE = 10
+  PSELINV_STEP_OZAKI_GEMM = 9, PSELINV_STEP_RECOMBINE = 10,
+  PSELINV_STEP_SMALL_LEVEL = 11  /* steps 3-5 of a level of narrow supernodes, one launch */
 };
 
 /* Run the selected-inversion plan (which = 0) or the factorisation plan

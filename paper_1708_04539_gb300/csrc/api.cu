@@ -50,7 +50,8 @@ enum StepKind {
   ST_SLICE,
   ST_OZGEMM,
   ST_ZERO,
-  ST_LU_PANEL
+  ST_LU_PANEL,
+  ST_SMALL_LEVEL
 };
 
 struct Step {
@@ -996,6 +997,56 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
 // largest K split of the normalisation's products
 constexpr int kNormMaxKsplit = 8;
 
+// An FP64 level of narrow supernodes as one fused launch (gather and steps
+// 3-5 in shared memory), each supernode's output columns split into tasks
+// of at most kSmallLevelTaskFma multiply-adds, when every supernode fits
+// and the estimated time (multiply-adds at 2 per cycle and SM) is below
+// that of the gather and two GEMM launches (about 15 us each plus the
+// level's flops at 1 TFLOP/s).  Returns false to leave
+// the level to those launches.
+constexpr double kSmallLevelTaskFma = 65536;
+bool add_small_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, int64_t nb, int lev) {
+  const HostSym& H = h->H;
+  const bool sym = h->opts.symmetric != 0;
+  const double cplx = h->dtype == DT_F64 ? 1.0 : 4.0;
+  std::vector<SnTask> tasks;
+  size_t smem = 0;
+  double fma_max = 0, flops = 0, bytes = 0;
+  for (int64_t K : grp) {
+    const int64_t s = H.sn_width[K], c = cK(H, K);
+    if (c == 0) continue;
+    if (c > kSmallLevelMaxC) return false;
+    // multiply-adds per output column: steps 3 and 5 (c^2 each), step 4 (s c)
+    const double per_col = cplx * ((sym ? 1.0 : 2.0) * c * c + (double)s * c);
+    const int w = (int)std::max<int64_t>(1, std::min<int64_t>(s, (int64_t)(kSmallLevelTaskFma / per_col)));
+    const size_t b = small_level_smem(h->dtype, (int)c, (int)s, w);
+    if (b > kSmallLevelMaxSmem) return false;
+    smem = std::max(smem, b);
+    fma_max = std::max(fma_max, per_col * w);
+    flops += 2.0 * per_col * s * nb;
+    bytes += (double)h->esize * nb * (c * c + 4.0 * c * s + 2.0 * s * s);
+    for (int64_t b2 = 0; b2 < nb; b2++)
+      for (int64_t j0 = 0; j0 < s; j0 += w)
+        tasks.push_back({(int)b2, (int)K, (int)j0, (int)std::min<int64_t>(w, s - j0)});
+  }
+  if (tasks.empty()) return false;
+  // the largest task alone on an SM, or the level's multiply-adds spread
+  // over all 152 SMs, whichever is longer
+  const double t_fused = std::max(fma_max, flops / 2.0 / 152.0) / 2.0 / 2.07e9;
+  const double t_launches = 3 * 15e-6 + flops / 1e12;
+  if (t_fused >= t_launches) return false;
+  Step st;
+  st.kind = ST_SMALL_LEVEL;
+  st.cfg = (int)smem;
+  st.n = (int)tasks.size();
+  st.tasks = P.push(tasks);
+  st.flops = flops;
+  st.bytes = (size_t)bytes;
+  st.level = lev;
+  P.steps.push_back(st);
+  return true;
+}
+
 int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   const HostSym& H = h->H;
   const bool sym = h->opts.symmetric != 0;
@@ -1137,6 +1188,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
         add_ozaki_level(h, P, grp, nb, gbase, (int)lev, max_cursor);
         continue;
       }
+      if (schedule == PSELINV_SCHED_LEVEL && add_small_level(h, P, grp, nb, (int)lev)) continue;
       std::vector<SnTask> gt;
       std::vector<int64_t> gofs;
       std::vector<GemmDesc> main, dg;
@@ -1242,6 +1294,10 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       break;
     case ST_ZERO:
       launch_zero((const CopySeg*)(a + s.tasks), s.n, s.grid, st);
+      break;
+    case ST_SMALL_LEVEL:
+      launch_small_level(h->dtype, h->S, h->ainv, h->nf, (const SnTask*)(a + s.tasks), s.n,
+                         (size_t)s.cfg, h->opts.symmetric != 0, st);
       break;
   }
 }
@@ -1458,6 +1514,7 @@ int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, v
     CK(cudaMalloc(&h->staging, (size_t)nbatch * h->H.nnz * es + 256));
     CK(cudaMalloc(&h->outstage, (size_t)h->H.nnz * es + 256));
     CK(prepare_dense_kernels(dtype, h->max_width));
+    CK(prepare_map_kernels());
     CK(prepare_ozaki_kernels());
     h->slices = h->opts.slices <= 0 ? 6 : std::min(6, std::max(4, (int)h->opts.slices));
     int rc = build_factor_plan(h);
@@ -1622,7 +1679,7 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
                                 PSELINV_STEP_GATHER,  PSELINV_STEP_SCATTER_SUB, PSELINV_STEP_COPY,
                                 PSELINV_STEP_MEMSET,  PSELINV_STEP_SCATTER_VALUES,
                                 PSELINV_STEP_SLICE,   PSELINV_STEP_OZAKI_GEMM, PSELINV_STEP_MEMSET,
-                                PSELINV_STEP_DIAG_LU};
+                                PSELINV_STEP_DIAG_LU, PSELINV_STEP_SMALL_LEVEL};
     out[i].kind = kinds[s.kind];
     out[i].level = s.level;
     out[i].tasks = s.n;

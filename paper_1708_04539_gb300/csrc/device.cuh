@@ -253,6 +253,17 @@ cudaError_t prepare_dense_kernels(int dtype, int max_width);
 // (real data only), the row and column maxima of |G_K| are also accumulated
 // (atomicMax on the bit patterns) into maxbase + mofs[task] (rows, c
 // entries) and maxbase + mofs[task] + c (columns).
+// Algorithm 1 steps 3-5 of a level of narrow supernodes in one launch, a
+// CTA per task {inst, K, j0, w} (c > 0; columns j0 .. j0 + w - 1 of the
+// supernode's outputs) with G, Lhat, Uhat^T and w columns of Ainv(C,K) in
+// `smem` bytes of shared memory (at most kSmallLevelMaxSmem, see
+// small_level_smem); D_K must already be in the diagonal blocks of store
+constexpr size_t kSmallLevelMaxSmem = 160 * 1024;
+constexpr int kSmallLevelMaxC = 128;
+size_t small_level_smem(int dtype, int c, int s, int w);
+cudaError_t prepare_map_kernels();
+void launch_small_level(int dtype, const SymDev& S, void* store, const void* nf, const SnTask* tasks,
+                        int ntasks, size_t smem, int sym, cudaStream_t st);
 void launch_gather(int dtype, const SymDev& S, const void* store, void* out,
                    const int64_t* gofs, const SnTask* tasks, int ntasks, cudaStream_t st,
                    const int64_t* mofs = nullptr, unsigned long long* maxbase = nullptr);

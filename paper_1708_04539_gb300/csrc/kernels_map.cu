@@ -210,6 +210,76 @@ __global__ void __launch_bounds__(kThreads) trace_final_kernel(const T* __restri
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// Algorithm 1 steps 3-5 of an FP64 level of narrow supernodes in one
+// launch.  A task {inst, K, j0, w} owns columns j0 .. j0 + w - 1 of the
+// supernode's outputs: G = Ainv(R_K, R_K) is gathered into shared memory
+// (leading dimension ldg = c | 1, so that the transposed reads of step 5
+// spread over the banks) with Lhat and Uhat^T (c x s); then Ainv(C,K) = -G
+// Lhat and Ainv(K,C)^T = -G^T Uhat^T for those columns into the panels (for
+// a symmetric A the second is a copy of the first) and Ainv_KK(:, j) = D_K(:,
+// j) - Uhat Ainv(C,K)(:, j) onto the diagonal block (D_K written there by
+// the normalisation).  Dot products over c from shared memory; the tasks
+// of a supernode write disjoint columns, so no atomics.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+small_level_kernel(SymDev S, T* store, const T* __restrict__ nf, const SnTask* __restrict__ tasks,
+                   int ntasks, int sym) {
+  extern __shared__ __align__(16) unsigned char small_smem[];
+  T* sm = reinterpret_cast<T*>(small_smem);
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SnTask task = tasks[t];
+    const int K = task.K, j0 = task.a, w = task.b;
+    const int c = S.sn_c[K], s = S.sn_width[K];
+    const int ldg = c | 1;
+    const int64_t rb = S.rows_ptr[K];
+    const int64_t base = (int64_t)task.inst * S.storage;
+    const int64_t so = base + S.sn_off[K], lo = so + (int64_t)s * s, uo = lo + (int64_t)c * s;
+    T* G = sm;
+    T* Lh = G + (int64_t)ldg * c;
+    T* Uh = Lh + (int64_t)c * s;
+    T* X = Uh + (int64_t)c * s;  // c x w: Ainv(C,K)(:, j0 .. j0 + w - 1)
+    const T* src = store + base;
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+      const int p = e % c, q = e / c;
+      T v = sc_zero(T());
+      if (S.check && !map_in_range(S, rb, p, q))
+        set_error(S.err, DEV_CHECK, K);
+      else
+        v = src[map_slot(S, rb, p, q)];
+      G[p + q * ldg] = v;
+    }
+    for (int e = threadIdx.x; e < c * s; e += blockDim.x) {
+      Lh[e] = nf[lo + e];
+      if (!sym) Uh[e] = nf[uo + e];
+    }
+    __syncthreads();
+    // steps 3 and 5
+    for (int e = threadIdx.x; e < c * w; e += blockDim.x) {
+      const int p = e % c, j = j0 + e / c;
+      T a = sc_zero(T()), b = sc_zero(T());
+      for (int q = 0; q < c; q++) {
+        a = fma_s(G[p + q * ldg], Lh[q + j * c], a);
+        if (!sym) b = fma_s(G[q + p * ldg], Uh[q + j * c], b);
+      }
+      a = scale_s(a, -1.0);
+      X[e] = a;
+      store[lo + p + (int64_t)j * c] = a;
+      store[uo + p + (int64_t)j * c] = sym ? a : scale_s(b, -1.0);
+    }
+    __syncthreads();
+    // step 4 (symmetric A: Uhat^T = Lhat)
+    const T* A4 = sym ? Lh : Uh;
+    for (int e = threadIdx.x; e < s * w; e += blockDim.x) {
+      const int i = e % s, jj = e / s;
+      T a = sc_zero(T());
+      for (int q = 0; q < c; q++) a = fma_s(A4[q + i * c], X[q + jj * c], a);
+      T* d = store + so + i + (int64_t)(j0 + jj) * s;
+      *d = sub_s(*d, a);
+    }
+    __syncthreads();
+  }
+}
+
 int grid_for(int64_t n) {
   const int64_t g = (n + kThreads - 1) / kThreads;
   return (int)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
@@ -227,6 +297,31 @@ void launch_scatter_values(int dtype, const SymDev& S, const void* values, void*
   else
     scatter_values_kernel<cdouble><<<grid_for(total), kThreads, 0, st>>>(
         S, (const cdouble*)values, (cdouble*)store, total);
+}
+
+size_t small_level_smem(int dtype, int c, int s, int w) {
+  return (size_t)((int64_t)(c | 1) * c + 2 * (int64_t)c * s + (int64_t)c * w) *
+         (dtype == DT_F64 ? 8 : 16);
+}
+
+cudaError_t prepare_map_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(small_level_kernel<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kSmallLevelMaxSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(small_level_kernel<cdouble>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallLevelMaxSmem);
+}
+
+void launch_small_level(int dtype, const SymDev& S, void* store, const void* nf, const SnTask* tasks,
+                        int ntasks, size_t smem, int sym, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  if (dtype == DT_F64)
+    small_level_kernel<double><<<ntasks, kThreads, smem, st>>>(S, (double*)store, (const double*)nf,
+                                                               tasks, ntasks, sym);
+  else
+    small_level_kernel<cdouble><<<ntasks, kThreads, smem, st>>>(S, (cdouble*)store,
+                                                                (const cdouble*)nf, tasks, ntasks, sym);
 }
 
 void launch_gather(int dtype, const SymDev& S, const void* store, void* out, const int64_t* gofs,
