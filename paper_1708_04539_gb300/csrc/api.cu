@@ -1019,7 +1019,9 @@ bool add_small_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
     // multiply-adds per output column: steps 3 and 5 (c^2 each), step 4 (s c)
     const double per_col = cplx * ((sym ? 1.0 : 2.0) * c * c + (double)s * c);
     const int w = (int)std::max<int64_t>(1, std::min<int64_t>(s, (int64_t)(kSmallLevelTaskFma / per_col)));
-    const size_t b = small_level_smem(h->dtype, (int)c, (int)s, w);
+    const int64_t rb = H.rows_ptr[K], b0 = H.rows_blk[rb], bl = H.rows_blk[rb + c - 1];
+    const int64_t seg = H.blk_rel[bl] + (c - H.blk_pb[bl]) - H.blk_rel[b0];
+    const size_t b = small_level_smem(h->dtype, (int)c, (int)s, w, (int)(bl - b0 + 1), (int)seg);
     if (b > kSmallLevelMaxSmem) return false;
     smem = std::max(smem, b);
     fma_max = std::max(fma_max, per_col * w);

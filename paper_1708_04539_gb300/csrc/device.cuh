@@ -260,7 +260,8 @@ cudaError_t prepare_dense_kernels(int dtype, int max_width);
 // small_level_smem); D_K must already be in the diagonal blocks of store
 constexpr size_t kSmallLevelMaxSmem = 160 * 1024;
 constexpr int kSmallLevelMaxC = 128;
-size_t small_level_smem(int dtype, int c, int s, int w);
+// nblk blocks in R_K, seg relative indices of R_K's blocks
+size_t small_level_smem(int dtype, int c, int s, int w, int nblk, int seg);
 cudaError_t prepare_map_kernels();
 void launch_small_level(int dtype, const SymDev& S, void* store, const void* nf, const SnTask* tasks,
                         int ntasks, size_t smem, int sym, cudaStream_t st);

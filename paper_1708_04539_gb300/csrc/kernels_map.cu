@@ -225,7 +225,6 @@ __global__ void __launch_bounds__(kThreads)
 small_level_kernel(SymDev S, T* store, const T* __restrict__ nf, const SnTask* __restrict__ tasks,
                    int ntasks, int sym) {
   extern __shared__ __align__(16) unsigned char small_smem[];
-  T* sm = reinterpret_cast<T*>(small_smem);
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const SnTask task = tasks[t];
     const int K = task.K, j0 = task.a, w = task.b;
@@ -234,23 +233,62 @@ small_level_kernel(SymDev S, T* store, const T* __restrict__ nf, const SnTask* _
     const int64_t rb = S.rows_ptr[K];
     const int64_t base = (int64_t)task.inst * S.storage;
     const int64_t so = base + S.sn_off[K], lo = so + (int64_t)s * s, uo = lo + (int64_t)c * s;
-    T* G = sm;
+    // index tables of R_K's blocks (consecutive block ids b0 ..): the local
+    // block of every position, the supernode's relative-index segment, and
+    // per block the storage offset, width and |R| of its supernode and the
+    // start of its relative indices within the segment
+    const int b0 = S.rows_blk[rb], nblk = S.rows_blk[rb + c - 1] - b0 + 1;
+    const int64_t rel0 = S.blk_rel[b0];
+    const int seg = (int)(S.blk_rel[b0 + nblk - 1] + (c - S.blk_pb[b0 + nblk - 1]) - rel0);
+    int64_t* m_off = reinterpret_cast<int64_t*>(small_smem);
+    int* m_s = reinterpret_cast<int*>(m_off + nblk);
+    int* m_c = m_s + nblk;
+    int* m_base = m_c + nblk;
+    int* lblk = m_base + nblk;
+    int* rel = lblk + c;
+    const size_t ibytes = ((size_t)nblk * 20 + (size_t)(c + seg) * 4 + 15) & ~size_t(15);
+    T* G = reinterpret_cast<T*>(small_smem + ibytes);
     T* Lh = G + (int64_t)ldg * c;
     T* Uh = Lh + (int64_t)c * s;
     T* X = Uh + (int64_t)c * s;  // c x w: Ainv(C,K)(:, j0 .. j0 + w - 1)
+    for (int l = threadIdx.x; l < nblk; l += blockDim.x) {
+      const int J = S.blk_sn[b0 + l];
+      m_off[l] = S.sn_off[J];
+      m_s[l] = S.sn_width[J];
+      m_c[l] = S.sn_c[J];
+      m_base[l] = (int)(S.blk_rel[b0 + l] - rel0) - S.blk_pb[b0 + l];
+    }
+    for (int p = threadIdx.x; p < c; p += blockDim.x) lblk[p] = S.rows_blk[rb + p] - b0;
+    for (int i = threadIdx.x; i < seg; i += blockDim.x) rel[i] = S.relidx[rel0 + i];
+    for (int e = threadIdx.x; e < c * s; e += blockDim.x) {
+      Lh[e] = nf[lo + e];
+      if (!sym) Uh[e] = nf[uo + e];
+    }
+    __syncthreads();
+    // G = Ainv(R_K, R_K): the slot of (p, q) as in map_slot, from the tables
     const T* src = store + base;
     for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
       const int p = e % c, q = e / c;
       T v = sc_zero(T());
-      if (S.check && !map_in_range(S, rb, p, q))
-        set_error(S.err, DEV_CHECK, K);
-      else
-        v = src[map_slot(S, rb, p, q)];
+      if (S.check) {
+        if (!map_in_range(S, rb, p, q))
+          set_error(S.err, DEV_CHECK, K);
+        else
+          v = src[map_slot(S, rb, p, q)];
+      } else {
+        const int lp = lblk[p], lq = lblk[q], l = lp < lq ? lp : lq;
+        const int rp = rel[m_base[l] + p], rq = rel[m_base[l] + q];
+        const int64_t sJ = m_s[l], cJ = m_c[l];
+        int64_t slot;
+        if (lp == lq)
+          slot = m_off[l] + rp + rq * sJ;
+        else if (lp > lq)
+          slot = m_off[l] + sJ * sJ + rp + rq * cJ;
+        else
+          slot = m_off[l] + sJ * sJ + cJ * sJ + rq + rp * cJ;
+        v = src[slot];
+      }
       G[p + q * ldg] = v;
-    }
-    for (int e = threadIdx.x; e < c * s; e += blockDim.x) {
-      Lh[e] = nf[lo + e];
-      if (!sym) Uh[e] = nf[uo + e];
     }
     __syncthreads();
     // steps 3 and 5
@@ -299,9 +337,10 @@ void launch_scatter_values(int dtype, const SymDev& S, const void* values, void*
         S, (const cdouble*)values, (cdouble*)store, total);
 }
 
-size_t small_level_smem(int dtype, int c, int s, int w) {
-  return (size_t)((int64_t)(c | 1) * c + 2 * (int64_t)c * s + (int64_t)c * w) *
-         (dtype == DT_F64 ? 8 : 16);
+size_t small_level_smem(int dtype, int c, int s, int w, int nblk, int seg) {
+  const size_t ibytes = ((size_t)nblk * 20 + (size_t)(c + seg) * 4 + 15) & ~size_t(15);
+  return ibytes + (size_t)((int64_t)(c | 1) * c + 2 * (int64_t)c * s + (int64_t)c * w) *
+                      (dtype == DT_F64 ? 8 : 16);
 }
 
 cudaError_t prepare_map_kernels() {
