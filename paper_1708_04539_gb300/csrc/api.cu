@@ -75,7 +75,8 @@ struct Step {
 
 // events of a multi-stream plan
 enum PlanEvent {
-  EV_FORK = 0, EV_SIDE_JOIN = 1, EV_THIRD_JOIN = 2, EV_THIRD_DONE = 3, EV_MAIN_JOIN = 4, EV_LEVEL = 5
+  EV_FORK = 0, EV_SIDE_JOIN = 1, EV_THIRD_JOIN = 2, EV_THIRD_DONE = 3, EV_MAIN_JOIN = 4,
+  EV_THIRD_DONE2 = 5, EV_LEVEL = 6
 };
 
 struct Plan {
@@ -467,13 +468,13 @@ struct TriBlock {
   int64_t b, K, w0;
 };
 void add_tri_step(Plan& P, const HostSym& H, const std::vector<TriBlock>& blocks, int level,
-                  int stream) {
+                  int stream, bool allow_small = true) {
   std::vector<SnTask> wide, small;
   std::vector<int64_t> wofs_wide, wofs_small;
   for (const TriBlock& t : blocks) {
     const int64_t s = H.sn_width[t.K];
     for (int which = 0; which < 2; which++) {
-      if (s <= 32) {
+      if (s <= 32 && allow_small) {
         small.push_back({(int)t.b, (int)t.K, which, 0});
         wofs_small.push_back(t.w0 + which * s * s);
         continue;
@@ -996,6 +997,10 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
 
 // largest K split of the normalisation's products
 constexpr int kNormMaxKsplit = 8;
+// triangular-inverse tasks (8 columns each) of the levels whose inverses
+// the side stream computes itself, and of the first third-stream launch
+constexpr int64_t kTriSideTasks = 4 * 152;
+constexpr int64_t kTriThirdTasks = 8 * 152;
 
 // An FP64 level of narrow supernodes as one fused launch (gather and steps
 // 3-5 in shared memory), each supernode's output columns split into tasks
@@ -1072,35 +1077,48 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   // depth level ahead of the sweep so that it overlaps the previous level's
   // products.  Triangular inverses first: the blocks of the levels nearest
   // the roots (needed first, few and wide) in one launch on the side
-  // stream, the rest in one launch on a third stream that runs beside the
-  // first levels; the first normalisation that needs it waits for it.
+  // stream; the next levels' in a launch on a third stream that runs beside
+  // the first levels, and the deep levels' in a second one behind it; the
+  // first normalisation that needs either waits for it.
   const int nlev = (int)H.level_ptr.size() - 1;
-  int lev_a = -1;
+  int lev_a = -1, lev_b = -1;
   {
-    int64_t tasks = 0;
-    for (int l = 0; l < nlev; l++) {
+    auto level_tasks = [&](int l) {
       int64_t t = 0;
       for (int64_t i = H.level_ptr[l]; i < H.level_ptr[l + 1]; i++)
         t += 2 * ((H.sn_width[H.level_sn[i]] + 7) / 8);
-      if (l > 0 && tasks + t * nb > 4 * 152) break;
-      tasks += t * nb;
+      return t * nb;
+    };
+    int64_t tasks = 0;
+    for (int l = 0; l < nlev; l++) {
+      if (l > 0 && tasks + level_tasks(l) > kTriSideTasks) break;
+      tasks += level_tasks(l);
       lev_a = l;
     }
-    std::vector<TriBlock> ta, tb;
+    tasks = 0;
+    lev_b = lev_a;
+    for (int l = lev_a + 1; l < nlev; l++) {
+      if (l > lev_a + 1 && tasks + level_tasks(l) > kTriThirdTasks) break;
+      tasks += level_tasks(l);
+      lev_b = l;
+    }
+    std::vector<TriBlock> ta, tb, tc;
     for (int64_t b = 0; b < nb; b++)
       for (int l = 0; l < nlev; l++)
         for (int64_t i = H.level_ptr[l]; i < H.level_ptr[l + 1]; i++) {
           const int64_t K = H.level_sn[i];
-          (l <= lev_a ? ta : tb).push_back({b, K, wbase[b * H.ns + K]});
+          (l <= lev_a ? ta : l <= lev_b ? tb : tc).push_back({b, K, wbase[b * H.ns + K]});
         }
-    add_tri_step(P, H, ta, -1, 1);
+    add_tri_step(P, H, ta, -1, 1, false);  // one launch: the first normalisation waits for it
     add_tri_step(P, H, tb, -1, 2);
     if (!tb.empty()) P.steps.back().signal = EV_THIRD_DONE;
+    add_tri_step(P, H, tc, -1, 2);
+    if (!tc.empty()) P.steps.back().signal = EV_THIRD_DONE2;
   }
   const size_t norm_base = selinv_main_bytes(H, nb, es);
   const size_t max_base = norm_base + ozaki_norm_bytes(H, nb, 6, es);
   size_t max_cursor = max_base;
-  bool third_waited = false;
+  bool third_waited = false, third_waited2 = false;
   // split = true: Lhat, Uhat^T and D_K as sliced products
   auto add_normalize = [&](int lev, bool split) {
     std::vector<GemmDesc> norm;
@@ -1148,8 +1166,13 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
     if (split) add_ozaki_normalize(h, P, lev, nb, wbase, norm_base);
     for (size_t i = first; i < P.steps.size(); i++) P.steps[i].side = 1;
     if (P.steps.size() > first) {
-      if (lev > lev_a && !third_waited) P.steps[first].wait = EV_THIRD_DONE;
-      third_waited = third_waited || lev > lev_a;
+      if (lev > lev_b && !third_waited2) {
+        P.steps[first].wait = EV_THIRD_DONE2;  // after EV_THIRD_DONE on the same stream
+        third_waited = third_waited2 = true;
+      } else if (lev > lev_a && !third_waited) {
+        P.steps[first].wait = EV_THIRD_DONE;
+        third_waited = true;
+      }
       P.steps.back().signal = EV_LEVEL + lev;
     }
   };
