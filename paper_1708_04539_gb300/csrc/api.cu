@@ -56,7 +56,8 @@ enum StepKind {
 
 struct Step {
   StepKind kind;
-  int cfg = 0;
+  int cfg = 0;    // GEMM: kernel config; TRI_INV: 1 small blocks; SLICE: 1 maxima pass;
+                  // OZGEMM: slices; SMALL_LEVEL: shared-memory bytes of a CTA
   int n = 0;      // tasks / segments
   int grid = 0;
   size_t tasks = 0, descs = 0, offs = 0, offs2 = 0;  // byte offsets into the plan arena

@@ -43,6 +43,22 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def _header_enum(name):
+    txt = open(os.path.join(ROOT, "include", "pselinv.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    body = re.search(r"enum\s+" + name + r"\s*\{(.*?)\}", txt, flags=re.S).group(1)
+    return {k: int(v) for k, v in re.findall(r"(PSELINV_\w+)\s*=\s*(-?\d+)", body)}
+
+
+def test_binding_names_every_step_kind():
+    """The profile records name their launch kind through the binding's
+    table: every kind the header declares has a name there."""
+    kinds = _header_enum("pselinv_step_kind")
+    assert len(kinds) >= 12
+    assert sorted(kinds.values()) == sorted(ps.binding.STEP_KINDS)
+    assert ps.binding.STEP_KINDS[kinds["PSELINV_STEP_SMALL_LEVEL"]] == "small_level"
+
+
 def test_error_strings_and_defaults():
     lib = ps.load_library()
     for code in range(0, -9, -1):
