@@ -394,11 +394,12 @@ tri_inv_small_kernel(SymDev S, const T* store, T* out, const int64_t* __restrict
 // NW - 1, k over the task's K chunk [kb, ke).  TRI = 1 (op(B) lower
 // triangular, zero for k < n) or 2 (upper, zero for k > n): square op(B);
 // in the diagonal block (k in [j0, j0 + NW)) only the triangle is
-// multiplied, the other k of the chunk run over all NW columns.  An upper op(A) (GEMM_TRI_UPPER_A, with a
-// lower op(B)) starts every warp at its first row.  Lanes past M read row
-// M - 1 and columns past N read column N - 1 (in bounds; never stored).
-// FP64 throughput is the bound: the loads of op(B) are warp-uniform, those
-// of A coalesced along m (or, transposed, one row per lane reused from L1).
+// multiplied, the other k of the chunk run over all NW columns.  An upper
+// op(A) (GEMM_TRI_UPPER_A, with a lower op(B)) starts every warp at its
+// first row.  Lanes past M read row M - 1 and columns past N read column
+// N - 1 (in bounds; never stored).  FP64 throughput is the bound: the loads
+// of op(B) are warp-uniform, those of A coalesced along m (or, transposed,
+// one row per lane reused from L1).
 template <typename T, int NW, int TRI>
 __device__ __forceinline__ void rows_task(const GemmDesc& d, int m, int warp_m0, int j0, int kb,
                                           int ke) {
