@@ -179,8 +179,8 @@ typedef struct pselinv_step_stat {
   double flops;   /* useful floating-point operations (real) */
   double bytes;   /* algorithmic bytes moved (operands read + results written) */
   double ms;      /* device time from CUDA events around the launch */
-  int32_t param;  /* GEMM: tile config (0 64x64, 1 32x32, 2 128x64, 3 row panels of a
-                     product with a triangular B); OZAKI_GEMM: K split;
+  int32_t param;  /* GEMM: kernel config (0 64x64, 1 32x32, 2 128x64 tiles, 3 row
+                     panels); OZAKI_GEMM: K split;
                      TRI_INV: 0 wide blocks (a warp per column), 1 blocks <= 32 wide;
                      else -1 */
   int32_t side;   /* stream of the launch in a sweep: 0 main, 1 normalisation side stream,
@@ -243,8 +243,8 @@ typedef struct pselinv_tune_record {
   int32_t precision; /* pselinv_precision of the plan */
   int32_t level;     /* tree level of the launch (-1 = normalisation) */
   int32_t slot;      /* 0 normalisation, 1 steps 3 and 5, 2 step 4 */
-  int32_t kind;      /* PSELINV_STEP_GEMM (param = tile config 0..3: 64x64, 32x32, 128x64,
-                        row panels; 3 only for slot 0)
+  int32_t kind;      /* PSELINV_STEP_GEMM (param = kernel config 0..3: 64x64, 32x32,
+                        128x64 tiles, row panels)
                         or PSELINV_STEP_OZAKI_GEMM (param = K split 1..16) */
   int32_t param;     /* the candidate timed */
   int32_t chosen;    /* 1 for the candidate the tuner kept */
@@ -269,7 +269,8 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
 /* Learned cost model of the launch shapes (not from the paper): an MLP
  *   x (16) -> tanh(W1 x + b1) (H) -> tanh(W2 h1 + b2) (H) -> w3 . h2 + b3
  * predicting log(ms) of a launch.  Input x of a record: feat[0..7] / 32;
- * [8] kind is GEMM; [9] kind is OZAKI_GEMM; [10..12] one-hot GEMM tile config;
+ * [8] kind is GEMM; [9] kind is OZAKI_GEMM; [10..12] one-hot GEMM tile config
+ * 0..2 (all zero for config 3, the row panels);
  * [13] log2(K split) / 4 for OZAKI_GEMM; [14] slot / 2; [15] precision.
  * Parameters (float32, flat): W1 (H x 16, row-major), b1 (H), W2 (H x H),
  * b2 (H), w3 (H), b3 (1).  Weights live on the current device; training and
@@ -303,10 +304,12 @@ int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int
 /* The tuned launch shapes of the plan of `precision`, as (level, slot,
  * value) triples of int32 (not from the paper; a tuning cache, so that a
  * plan tuned once can be replayed in another process).  Slots: 0
- * normalisation GEMM tile config (0..3, 3 the triangular row panels);
- * FP64 plan: 1 steps 3+5, 2 step 4 tile config (0..2); split plan: 1 steps 3+5, 2 step 4 K split (1, 2, 4, 8
- * or 16), 3 level precision (0 split products, 1 FP64), 4 / 5 tile config
- * of the FP64 launches of steps 3+5 / step 4.  Levels are depth levels
+ * normalisation GEMM kernel config (0..3: 64x64, 32x32, 128x64 tiles, row
+ * panels); FP64 plan: 1 steps 3+5, 2 step 4 kernel config (0..3); split
+ * plan: 1 steps 3+5, 2 step 4 K split (1, 2, 4, 8 or 16), 3 level precision
+ * (0 split products, 1 FP64), 4 / 5 kernel config of the FP64 launches of
+ * steps 3+5 / step 4 (an FP64 level of narrow supernodes may run as one
+ * fused launch instead, PSELINV_STEP_SMALL_LEVEL).  Levels are depth levels
  * (0 = roots), up to the structure's level count.
  * get: *count = number of triples; up to cap are written to out[3 * cap].
  * set: replaces all tuned values of `precision` (count = 0 restores the
