@@ -148,6 +148,19 @@ void pselinv_default_opts(pselinv_opts* opts);
 int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
                     const int64_t* perm, const pselinv_opts* opts, pselinv_t* out);
 
+/* Fill-reducing ordering for pselinv_analyze (host only; not from the
+ * paper, which orders with graph partitioners): automatic nested dissection
+ * of the graph of A after George and Liu (1981), separators from the level
+ * structures of pseudo-peripheral vertices, each separator ordered after
+ * the two parts it separates, parts of at most `leaf` vertices (leaf >= 1)
+ * in breadth-first order.  colptr/rowind: the CSC pattern as for
+ * pselinv_analyze (must equal its transpose; the diagonal is ignored).
+ * perm_out[n] (host, caller-owned): new -> old.  Errors: PSELINV_ERR_ARG
+ * (bad pattern, leaf < 1, null pointer), PSELINV_ERR_NOT_STRUCT_SYM,
+ * PSELINV_ERR_OOM. */
+int pselinv_order_nd(int64_t n, const int64_t* colptr, const int64_t* rowind, int64_t leaf,
+                     int64_t* perm_out);
+
 /* Supernodal LU without pivoting of nbatch instances sharing the pattern
  * (Eq. LU, Section 3's prerequisite).  values: nbatch * nnz scalars of dtype,
  * instance b at values + b*nnz, in the CSC order given to pselinv_analyze;

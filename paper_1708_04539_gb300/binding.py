@@ -111,6 +111,8 @@ def load_library():
     I64 = ctypes.c_int64
     lib.pselinv_default_opts.argtypes = [ctypes.POINTER(Opts)]
     lib.pselinv_default_opts.restype = None
+    lib.pselinv_order_nd.argtypes = [I64, P, P, I64, P]
+    lib.pselinv_order_nd.restype = ctypes.c_int
     lib.pselinv_analyze.argtypes = [I64, P, P, P, ctypes.POINTER(Opts), ctypes.POINTER(P)]
     lib.pselinv_analyze.restype = ctypes.c_int
     lib.pselinv_factor.argtypes = [P, ctypes.c_int, I64, P, P]
@@ -562,6 +564,19 @@ class InstanceGroup:
     def split(self, out):
         """Per-instance views of a pattern-of-A result of the group."""
         return [out[self.nz_off[i]:self.nz_off[i + 1]] for i in range(len(self.n))]
+
+
+def order_nd(n, colptr, rowind, leaf=64):
+    """Nested-dissection ordering (new -> old) of a structurally symmetric
+    CSC pattern, computed on the host by ``pselinv_order_nd``."""
+    lib = load_library()
+    cp = np.ascontiguousarray(colptr, dtype=np.int64)
+    ri = np.ascontiguousarray(rowind, dtype=np.int64)
+    perm = np.empty(int(n), dtype=np.int64)
+    rc = lib.pselinv_order_nd(int(n), _ptr(cp), _ptr(ri), int(leaf), _ptr(perm))
+    if rc != 0:
+        raise PselinvError(rc, "pselinv_order_nd")
+    return perm
 
 
 def wait_selftest(budget_us=20000, stream=None):
