@@ -332,6 +332,15 @@ int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int
 int pselinv_plan_get(pselinv_t h, int precision, int32_t* out, int64_t cap, int64_t* count);
 int pselinv_plan_set(pselinv_t h, int precision, const int32_t* in, int64_t count);
 
+/* The same tuned values as a cache file at `path` (host only): save writes
+ * a header naming the precision and the structure (n, supernodes, levels)
+ * and the triples; load reads it back into the handle as pselinv_plan_set
+ * does.  Errors: PSELINV_ERR_ARG for a path that cannot be opened, a file
+ * not in this format, a file saved for another precision or structure, or
+ * a triple out of range (the handle's values are then unchanged). */
+int pselinv_plan_save(pselinv_t h, int precision, const char* path);
+int pselinv_plan_load(pselinv_t h, int precision, const char* path);
+
 /* Pole-expansion consumers of a batch of selected inverses (the use of
  * selected inversion that motivates the method, Section 1: a density matrix
  * or an observable as a weighted sum over shifted matrices).  weights: host

@@ -111,6 +111,10 @@ def load_library():
     I64 = ctypes.c_int64
     lib.pselinv_default_opts.argtypes = [ctypes.POINTER(Opts)]
     lib.pselinv_default_opts.restype = None
+    lib.pselinv_plan_save.argtypes = [P, ctypes.c_int, ctypes.c_char_p]
+    lib.pselinv_plan_save.restype = ctypes.c_int
+    lib.pselinv_plan_load.argtypes = [P, ctypes.c_int, ctypes.c_char_p]
+    lib.pselinv_plan_load.restype = ctypes.c_int
     lib.pselinv_order_nd.argtypes = [I64, P, P, I64, P]
     lib.pselinv_order_nd.restype = ctypes.c_int
     lib.pselinv_analyze.argtypes = [I64, P, P, P, ctypes.POINTER(Opts), ctypes.POINTER(P)]
@@ -336,6 +340,16 @@ class SelInv:
         buf = (ctypes.c_int32 * max(3, len(flat)))(*flat)
         self._check(self._lib.pselinv_plan_set(self._h, int(precision), buf, len(flat) // 3),
                     "pselinv_plan_set")
+
+    def plan_save(self, path, precision=PREC_FP64):
+        """Write the tuned values of `precision` to a cache file."""
+        self._check(self._lib.pselinv_plan_save(self._h, int(precision), os.fsencode(path)),
+                    "pselinv_plan_save")
+
+    def plan_load(self, path, precision=PREC_FP64):
+        """Load tuned values saved for this structure and precision."""
+        self._check(self._lib.pselinv_plan_load(self._h, int(precision), os.fsencode(path)),
+                    "pselinv_plan_load")
 
     def _weights(self, weights):
         cplx = self.dtype == C128

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <map>
 #include <tuple>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -2075,6 +2076,53 @@ int pselinv_plan_set(pselinv_t h, int precision, const int32_t* in, int64_t coun
   for (const auto& e : entries) h->tuned[e.first] = e.second;
   for (auto& p : h->selinv_plan[precision]) p.release();
   return PSELINV_OK;
+}
+
+// Tuning cache file: a header line naming the format, the precision and
+// the structure it was tuned on, then one "level slot value" line per
+// tuned value (the triples of pselinv_plan_get).
+int pselinv_plan_save(pselinv_t h, int precision, const char* path) {
+  if (!h || !path) return PSELINV_ERR_ARG;
+  int64_t count = 0;
+  int rc = pselinv_plan_get(h, precision, nullptr, 0, &count);
+  if (rc != PSELINV_OK) return rc;
+  std::vector<int32_t> t((size_t)(3 * count));
+  rc = pselinv_plan_get(h, precision, t.data(), count, &count);
+  if (rc != PSELINV_OK) return rc;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return PSELINV_ERR_ARG;
+  const int64_t nlev = h->H.level_ptr.empty() ? 0 : (int64_t)h->H.level_ptr.size() - 1;
+  bool ok = std::fprintf(f, "pselinv-plan 1 %d %lld %lld %lld %lld\n", precision, (long long)h->H.n,
+                         (long long)h->H.ns, (long long)nlev, (long long)count) > 0;
+  for (int64_t i = 0; i < count && ok; i++)
+    ok = std::fprintf(f, "%d %d %d\n", t[3 * i], t[3 * i + 1], t[3 * i + 2]) > 0;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? PSELINV_OK : PSELINV_ERR_ARG;
+}
+
+int pselinv_plan_load(pselinv_t h, int precision, const char* path) {
+  if (!h || !path || (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16))
+    return PSELINV_ERR_ARG;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return PSELINV_ERR_ARG;
+  int version = 0, prec = -1;
+  long long n = -1, ns = -1, nlev = -1, count = -1;
+  const int64_t my_nlev = h->H.level_ptr.empty() ? 0 : (int64_t)h->H.level_ptr.size() - 1;
+  bool ok = std::fscanf(f, "pselinv-plan %d %d %lld %lld %lld %lld", &version, &prec, &n, &ns,
+                        &nlev, &count) == 6 &&
+            version == 1 && prec == precision && n == h->H.n && ns == h->H.ns && nlev == my_nlev &&
+            count >= 0 && count <= 64 * (my_nlev + 1);
+  std::vector<int32_t> t;
+  for (long long i = 0; ok && i < count; i++) {
+    int a = 0, b = 0, c = 0;
+    ok = std::fscanf(f, "%d %d %d", &a, &b, &c) == 3;
+    t.push_back(a);
+    t.push_back(b);
+    t.push_back(c);
+  }
+  std::fclose(f);
+  if (!ok) return PSELINV_ERR_ARG;
+  return pselinv_plan_set(h, precision, t.data(), count);  // validates every triple
 }
 
 int pselinv_tune_records(pselinv_t h, pselinv_tune_record* out, int64_t cap, int64_t* count) {

@@ -43,6 +43,41 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_plan_cache_file_round_trip_host_only(tmp_path):
+    """Tuned values saved to a cache file come back into another handle of
+    the same structure; a file for another structure or precision, a
+    malformed file and a missing file are refused without changing the
+    handle's values."""
+    p = gen.conv_diff_2d(24, seed=3)
+    h = ps.SelInv.from_problem(p, host_only=True)
+    nlev = h.structure()["nlevels"]
+    triples = [(0, 0, 3), (0, 3, 1), (1, 1, 4), (nlev - 1, 4, 2), (nlev - 1, 5, 3)]
+    h.plan_set(triples, ps.PREC_OZAKI_FP16)
+    path = tmp_path / "plan.txt"
+    h.plan_save(path, ps.PREC_OZAKI_FP16)
+    h2 = ps.SelInv.from_problem(p, host_only=True)
+    h2.plan_load(path, ps.PREC_OZAKI_FP16)
+    assert h2.plan_get(ps.PREC_OZAKI_FP16) == sorted(triples)
+    keep = [(0, 0, 1)]
+    other = ps.SelInv.from_problem(gen.conv_diff_2d(20, seed=3), host_only=True)
+    other.plan_set(keep, ps.PREC_OZAKI_FP16)
+    bad = tmp_path / "bad.txt"
+    bad.write_text("not a plan\n")
+    for h3, path3, prec in [(other, path, ps.PREC_OZAKI_FP16), (h2, path, ps.PREC_FP64),
+                            (other, bad, ps.PREC_OZAKI_FP16),
+                            (other, tmp_path / "missing.txt", ps.PREC_OZAKI_FP16)]:
+        with pytest.raises(ps.PselinvError):
+            h3.plan_load(path3, prec)
+    assert other.plan_get(ps.PREC_OZAKI_FP16) == keep
+    # a saved value out of range is refused too
+    txt = path.read_text().splitlines()
+    txt[1] = "0 0 9"
+    bad.write_text("\n".join(txt) + "\n")
+    with pytest.raises(ps.PselinvError):
+        h2.plan_load(bad, ps.PREC_OZAKI_FP16)
+    assert h2.plan_get(ps.PREC_OZAKI_FP16) == sorted(triples)
+
+
 def _header_enum(name):
     txt = open(os.path.join(ROOT, "include", "pselinv.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
