@@ -93,7 +93,10 @@ typedef struct pselinv_opts {
                             of U, step 5's product (a copy) and the column slicing of G
                             (the symmetric variant of Algorithm 1).  Not checked: values
                             that are not symmetric give a wrong result.  Default 0. */
-  int32_t reserved[6];
+  int32_t nd_leaf;       /* perm == NULL in pselinv_analyze: 0 (default) the natural order;
+                            > 0 the nested-dissection ordering of pselinv_order_nd with
+                            leaves of at most nd_leaf vertices (see the structure's perm) */
+  int32_t reserved[5];
 } pselinv_opts;
 
 typedef struct pselinv_ctx* pselinv_t;
@@ -143,7 +146,8 @@ void pselinv_default_opts(pselinv_opts* opts);
  * row structures, the supernodal tree and its levels, the block index maps
  * used by the device gathers/scatters, and uploads them.
  * n >= 0; colptr[n+1], rowind[nnz] host arrays, rows strictly increasing per
- * column; perm[n] host (NULL = identity); opts NULL = defaults.
+ * column; perm[n] host (NULL = identity, or with opts->nd_leaf > 0 the
+ * nested-dissection ordering); opts NULL = defaults.
  * Needs a current CUDA device.  On success *out is a new handle. */
 int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
                     const int64_t* perm, const pselinv_opts* opts, pselinv_t* out);

@@ -63,7 +63,8 @@ class Opts(ctypes.Structure):
                 ("schedule", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("check_level", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("split_normalise", ctypes.c_int32),
-                ("symmetric", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("symmetric", ctypes.c_int32), ("nd_leaf", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _P64 = ctypes.POINTER(ctypes.c_int64)
@@ -224,7 +225,7 @@ class SelInv:
 
     def __init__(self, n, colptr, rowind, perm=None, max_supernode=256, relax_pct=20,
                  schedule=SCHED_LEVEL, use_graph=True, check_level=0, precision=PREC_FP64,
-                 slices=0, host_only=False, split_normalise=False, symmetric=False):
+                 slices=0, host_only=False, split_normalise=False, symmetric=False, nd_leaf=0):
         lib = load_library()
         self._lib = lib
         opts = Opts()
@@ -239,6 +240,7 @@ class SelInv:
         opts.host_only = 1 if host_only else 0
         opts.split_normalise = 1 if split_normalise else 0
         opts.symmetric = 1 if symmetric else 0
+        opts.nd_leaf = int(nd_leaf)  # perm None: 0 natural order, > 0 nested dissection
         self._colptr = np.ascontiguousarray(colptr, dtype=np.int64)
         self._rowind = np.ascontiguousarray(rowind, dtype=np.int64)
         p = None if perm is None else np.ascontiguousarray(perm, dtype=np.int64)

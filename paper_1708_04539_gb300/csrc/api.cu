@@ -1491,9 +1491,24 @@ int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind, con
   pselinv_ctx* h = new (std::nothrow) pselinv_ctx();
   if (!h) return PSELINV_ERR_OOM;
   if (opts) h->opts = *opts; else pselinv_default_opts(&h->opts);
-  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 256) {
+  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 256 || h->opts.nd_leaf < 0) {
     delete h;
     return PSELINV_ERR_ARG;
+  }
+  std::vector<int64_t> nd;  // the nested-dissection ordering asked for by opts.nd_leaf
+  if (!perm && h->opts.nd_leaf > 0 && n > 0) {
+    try {
+      nd.resize((size_t)n);
+    } catch (const std::bad_alloc&) {
+      delete h;
+      return PSELINV_ERR_OOM;
+    }
+    const int orc = pselinv_order_nd(n, colptr, rowind, h->opts.nd_leaf, nd.data());
+    if (orc != PSELINV_OK) {
+      delete h;
+      return orc;
+    }
+    perm = nd.data();
   }
   int rc = analyze_host(n, colptr, rowind, perm, h->opts.max_supernode, h->opts.relax_pct, h->H);
   if (rc != PSELINV_OK) {

@@ -121,3 +121,16 @@ def test_host_pipeline_consumes_the_ordering(name, make):
     x = oracle.extract(oracle.selected_inverse(q), q.colptr, q.rowind)
     y = oracle.extract(oracle.selected_inverse(p), p.colptr, p.rowind)
     assert np.abs(x - y).max() <= 1e-12 * np.abs(y).max()
+
+
+def test_analyze_orders_by_nested_dissection_on_request():
+    """perm None with nd_leaf > 0: the analysis uses pselinv_order_nd's
+    ordering (the structure reports it); nd_leaf 0 keeps the natural order;
+    a negative nd_leaf is refused."""
+    p = gen.upwind_3d(8, 4)
+    h = ps.SelInv(p.n, p.colptr, p.rowind, None, nd_leaf=16, host_only=True)
+    assert np.array_equal(h.structure()["perm"], ps.order_nd(p.n, p.colptr, p.rowind, leaf=16))
+    h0 = ps.SelInv(p.n, p.colptr, p.rowind, None, host_only=True)
+    assert np.array_equal(h0.structure()["perm"], np.arange(p.n))
+    with pytest.raises(ps.PselinvError):
+        ps.SelInv(p.n, p.colptr, p.rowind, None, nd_leaf=-1, host_only=True)
