@@ -14,13 +14,15 @@
 //   * pseudo-peripheral vertex: from a vertex of least degree, repeatedly
 //     re-root the level structure at a least-degree vertex of its last
 //     level while that makes the structure deeper;
-//   * separator: the level where the count of vertices up to it reaches half
-//     of the part (kept strictly inside the structure), restricted to the
-//     vertices that have a neighbour in the next level; the rest of that
-//     level stays with the lower side;
+//   * separator: a level strictly inside the structure, restricted to the
+//     vertices that have a neighbour in the next level (the rest of that
+//     level stays with the lower side): the smallest such separator among
+//     the levels that leave at least a fifth of the part on each side,
+//     else the level where the count of vertices up to it reaches half;
 //   * a part at most `leaf` large, or too shallow to split (fewer than three
 //     levels), is ordered by its breadth-first order.
 #include <algorithm>
+#include <cstdlib>
 #include <new>
 #include <utility>
 #include <vector>
@@ -188,11 +190,34 @@ extern "C" int pselinv_order_nd(int64_t n, const int64_t* colptr, const int64_t*
         for (int64_t i = 0; i < m; i++) perm_out[P.lo + i] = order[i];
         continue;
       }
-      // separator level: cumulative count reaches half the part, 1 <= j <= depth - 2
-      std::vector<int64_t> cnt(depth, 0);
-      for (int64_t v : order) cnt[lev[v]]++;
+      // separator level j in [1, depth - 2]: the smallest separator (below)
+      // among the levels that leave at least a fifth of the part on each
+      // side, else the level where the count reaches half the part
+      std::vector<int64_t> cnt(depth, 0), scnt(depth, 0);
+      for (int64_t v : order) {
+        cnt[lev[v]]++;
+        for (int64_t p = g.ptr[v]; p < g.ptr[v + 1]; p++) {
+          const int64_t u = g.adj[p];
+          if (part[u] == tag && lev[u] == lev[v] + 1) {
+            scnt[lev[v]]++;
+            break;
+          }
+        }
+      }
       int64_t j = 1, acc = cnt[0];
       while (j < depth - 2 && acc + cnt[j] < (m + 1) / 2) acc += cnt[j++];
+      {
+        int64_t below = cnt[0], best = -1;
+        for (int64_t l = 1; l <= depth - 2; l++) {
+          const int64_t lower = below + cnt[l] - scnt[l], upper = m - lower - scnt[l];
+          below += cnt[l];
+          if (5 * std::min(lower, upper) < m) continue;
+          if (best < 0 || scnt[l] < scnt[best] ||
+              (scnt[l] == scnt[best] && std::llabs(l - j) < std::llabs(best - j)))
+            best = l;
+        }
+        if (best >= 0) j = best;
+      }
       // separator: the vertices of level j with a neighbour in level j + 1
       std::vector<int64_t> sep, rest;
       for (int64_t v : order) {
