@@ -239,16 +239,20 @@ int pselinv_plan_stats(pselinv_t h, int64_t* launches_selinv, int64_t* launches_
  *   leading dimension ld_in) holds L unit lower below the diagonal and U on
  *   and above it -- the layout of a diagonal block of
  *   PSELINV_LAYOUT_FACTORS.  inv_out: s x s, leading dimension ld_out.
- * Both pointers are device memory owned by the caller; dtype is PSELINV_F64
- * or PSELINV_C128; 1 <= s <= PSELINV_NOALLOC_MAX_S (larger s returns
+ * Both pointers are device memory of the CURRENT device, owned by the
+ * caller, and `stream` belongs to that device; a pointer that is host
+ * memory or lives on another device returns PSELINV_ERR_ARG before any
+ * launch (checked with cudaPointerGetAttributes).  dtype is PSELINV_F64 or
+ * PSELINV_C128; 1 <= s <= PSELINV_NOALLOC_MAX_S (larger s returns
  * PSELINV_ERR_ARG).  The call allocates nothing: the two triangular inverses
  * are kept in a 2 MiB array compiled into the library, which every GPU that
  * loads the library holds until the process exits.  The first call on a
- * device looks up that array's address (with the device current), so make
- * it before any stream capture.  All calls share the array: calls that
- * overlap on the GPU race and must be serialised by the caller.  Work is
- * queued on `stream`; a zero pivot in U gives non-finite output and is not
- * reported. */
+ * device looks up that array's address (with the device current) and keeps
+ * it, so make that call before any stream capture, and do not use the entry
+ * point on a device after cudaDeviceReset of that device.  All calls share
+ * the array: calls that overlap on the GPU race and must be serialised by
+ * the caller.  Work is queued on `stream`; a zero pivot in U gives
+ * non-finite output and is not reported. */
 #define PSELINV_NOALLOC_MAX_S 256
 int pselinv_block_inverse_noalloc(int dtype, int64_t s, const void* lu_block, int64_t ld_in,
                                   void* inv_out, int64_t ld_out, void* stream);

@@ -528,14 +528,60 @@ def make_record(**kw):
 NOALLOC_MAX_S = 256
 
 
+def _noalloc_args(lu_block, out, s):
+    """Check the operands of block_inverse_noalloc before any pointer reaches
+    the GPU; returns (s, dtype code).  Both must be contiguous CUDA tensors
+    of one device and one dtype (float64 or complex128) holding at least
+    s * s scalars each (column-major storage, leading dimension s)."""
+    for name, t in (("lu_block", lu_block), ("out", out)):
+        if not (hasattr(t, "is_cuda") and hasattr(t, "data_ptr")):
+            raise TypeError(f"{name} must be a CUDA torch tensor, not {type(t).__name__}")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be on a CUDA device (got {t.device})")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    import torch
+    if lu_block.dtype not in (torch.float64, torch.complex128):
+        raise ValueError(f"lu_block must be float64 or complex128, not {lu_block.dtype}")
+    if out.dtype != lu_block.dtype:
+        raise ValueError(f"out has dtype {out.dtype}, lu_block {lu_block.dtype}")
+    if out.device != lu_block.device:
+        raise ValueError(f"out is on {out.device}, lu_block on {lu_block.device}")
+    if s is None:
+        if lu_block.dim() == 2 and lu_block.shape[0] == lu_block.shape[1]:
+            s = int(lu_block.shape[0])
+        elif lu_block.dim() == 1:
+            r = int(np.sqrt(lu_block.numel()) + 0.5)
+            if r * r != lu_block.numel():
+                raise ValueError(f"a flat lu_block of {lu_block.numel()} scalars is not square; "
+                                 "pass s")
+            s = r
+        else:
+            raise ValueError(f"cannot infer s from shape {tuple(lu_block.shape)}; pass s")
+    s = int(s)
+    if not 1 <= s <= NOALLOC_MAX_S:
+        raise ValueError(f"s = {s} outside 1..{NOALLOC_MAX_S}")
+    for name, t in (("lu_block", lu_block), ("out", out)):
+        if t.numel() < s * s:
+            raise ValueError(f"{name} holds {t.numel()} scalars, fewer than s * s = {s * s}")
+    return s, (C128 if lu_block.dtype == torch.complex128 else F64)
+
+
 def block_inverse_noalloc(lu_block, out, s=None, stream=None):
     """(L U)^{-1} of an LU-factored s x s block (column-major device arrays)
-    through the allocation-free entry point; see pselinv_block_inverse_noalloc."""
+    through the allocation-free entry point; see pselinv_block_inverse_noalloc.
+
+    ``lu_block`` and ``out`` are contiguous CUDA tensors of the same device
+    and dtype (float64 or complex128) with at least s * s scalars; ``s``
+    defaults to the side of a square 2-D tensor or of a flat buffer whose
+    length is a perfect square.  The call runs with the tensors' device
+    current (the library requires that of its pointers)."""
+    s, dt = _noalloc_args(lu_block, out, s)
     lib = load_library()
-    s = int(lu_block.shape[0]) if s is None else int(s)
-    dt = C128 if _is_complex(lu_block) else F64
-    rc = lib.pselinv_block_inverse_noalloc(dt, s, _ptr(lu_block), s, _ptr(out), s,
-                                           _stream(stream))
+    import torch
+    with torch.cuda.device(lu_block.device):
+        rc = lib.pselinv_block_inverse_noalloc(dt, s, _ptr(lu_block), s, _ptr(out), s,
+                                               _stream(stream))
     if rc != 0:
         raise PselinvError(rc, "pselinv_block_inverse_noalloc")
     return out

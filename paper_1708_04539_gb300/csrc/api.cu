@@ -2094,8 +2094,31 @@ int pselinv_plan_set(pselinv_t h, int precision, const int32_t* in, int64_t coun
 }
 
 // Tuning cache file: a header line naming the format, the precision and
-// the structure it was tuned on, then one "level slot value" line per
-// tuned value (the triples of pselinv_plan_get).
+// the structure it was tuned on (counts and a 64-bit FNV-1a hash of the
+// supernode widths, row-structure sizes and depth levels, so that a plan
+// tuned for another matrix with the same counts is refused), then one
+// "level slot value" line per tuned value (the triples of pselinv_plan_get).
+static unsigned long long structure_hash(const HostSym& H) {
+  unsigned long long x = 1469598103934665603ull;
+  auto mix = [&](int64_t v) {
+    for (int b = 0; b < 8; b++) {
+      x ^= (unsigned long long)((uint64_t)v >> (8 * b)) & 0xFFull;
+      x *= 1099511628211ull;
+    }
+  };
+  auto mixv = [&](const std::vector<int64_t>& v) {
+    mix((int64_t)v.size());
+    for (int64_t e : v) mix(e);
+  };
+  mix(H.n);
+  mix(H.ns);
+  mixv(H.sn_width);
+  mixv(H.rows_ptr);
+  mixv(H.level_ptr);
+  mixv(H.level_sn);
+  return x;
+}
+
 int pselinv_plan_save(pselinv_t h, int precision, const char* path) {
   if (!h || !path) return PSELINV_ERR_ARG;
   int64_t count = 0;
@@ -2107,8 +2130,9 @@ int pselinv_plan_save(pselinv_t h, int precision, const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return PSELINV_ERR_ARG;
   const int64_t nlev = h->H.level_ptr.empty() ? 0 : (int64_t)h->H.level_ptr.size() - 1;
-  bool ok = std::fprintf(f, "pselinv-plan 1 %d %lld %lld %lld %lld\n", precision, (long long)h->H.n,
-                         (long long)h->H.ns, (long long)nlev, (long long)count) > 0;
+  bool ok = std::fprintf(f, "pselinv-plan 2 %d %lld %lld %lld %016llx %lld\n", precision,
+                         (long long)h->H.n, (long long)h->H.ns, (long long)nlev,
+                         structure_hash(h->H), (long long)count) > 0;
   for (int64_t i = 0; i < count && ok; i++)
     ok = std::fprintf(f, "%d %d %d\n", t[3 * i], t[3 * i + 1], t[3 * i + 2]) > 0;
   ok = (std::fclose(f) == 0) && ok;
@@ -2122,11 +2146,12 @@ int pselinv_plan_load(pselinv_t h, int precision, const char* path) {
   if (!f) return PSELINV_ERR_ARG;
   int version = 0, prec = -1;
   long long n = -1, ns = -1, nlev = -1, count = -1;
+  unsigned long long hash = 0;
   const int64_t my_nlev = h->H.level_ptr.empty() ? 0 : (int64_t)h->H.level_ptr.size() - 1;
-  bool ok = std::fscanf(f, "pselinv-plan %d %d %lld %lld %lld %lld", &version, &prec, &n, &ns,
-                        &nlev, &count) == 6 &&
-            version == 1 && prec == precision && n == h->H.n && ns == h->H.ns && nlev == my_nlev &&
-            count >= 0 && count <= 64 * (my_nlev + 1);
+  bool ok = std::fscanf(f, "pselinv-plan %d %d %lld %lld %lld %llx %lld", &version, &prec, &n,
+                        &ns, &nlev, &hash, &count) == 7 &&
+            version == 2 && prec == precision && n == h->H.n && ns == h->H.ns && nlev == my_nlev &&
+            hash == structure_hash(h->H) && count >= 0 && count <= 64 * (my_nlev + 1);
   std::vector<int32_t> t;
   for (long long i = 0; ok && i < count; i++) {
     int a = 0, b = 0, c = 0;

@@ -13,10 +13,14 @@
 // library holds it (2 MiB) until the process exits.  Its host-side name is
 // only a stand-in, so the per-device address is looked up once with
 // cudaGetSymbolAddress, on the first call made on that device, with the
-// device current.  All calls share the array and it keeps the last call's
-// contents; calls that overlap on the GPU (different streams, or the same
-// device from several threads) race on it and must be serialised by the
-// caller.
+// device current, and kept for the life of the process (so the entry point
+// must not be used on a device after cudaDeviceReset of that device: the
+// module, and with it the array, may then live at another address).  All
+// calls share the array and it keeps the last call's contents; calls that
+// overlap on the GPU (different streams, or the same device from several
+// threads) race on it and must be serialised by the caller.  Both pointers
+// must be device memory of the current device (checked with
+// cudaPointerGetAttributes; anything else is refused before any launch).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -153,6 +157,22 @@ cudaError_t run(const void* lu, int ld_in, int s, void* inv, int ld_out, cudaStr
   return cudaGetLastError();
 }
 
+// Whether p is device (or managed) memory of the current device: a host
+// pointer, or one of another device, would make the kernels fault.
+bool on_current_device(const void* p) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 }  // namespace
 }  // namespace pselinv
 
@@ -163,6 +183,7 @@ extern "C" int pselinv_block_inverse_noalloc(int dtype, int64_t s, const void* l
   if (dtype != PSELINV_F64 && dtype != PSELINV_C128) return PSELINV_ERR_ARG;
   if (s < 1 || s > PSELINV_NOALLOC_MAX_S || ld_in < s || ld_out < s || !lu_block || !inv_out)
     return PSELINV_ERR_ARG;
+  if (!on_current_device(lu_block) || !on_current_device(inv_out)) return PSELINV_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const cudaError_t e =
       dtype == PSELINV_F64

@@ -78,6 +78,43 @@ def test_plan_cache_file_round_trip_host_only(tmp_path):
     assert h2.plan_get(ps.PREC_OZAKI_FP16) == sorted(triples)
 
 
+def _blocks_problem(sizes):
+    """Block-diagonal pattern of dense diagonal blocks of the given sizes."""
+    n = sum(sizes)
+    rows, cols, o = [], [], 0
+    for b in sizes:
+        ii, jj = np.meshgrid(np.arange(o, o + b), np.arange(o, o + b), indexing="ij")
+        rows.append(ii.ravel())
+        cols.append(jj.ravel())
+        o += b
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    order = np.lexsort((r, c))
+    r, c = r[order], c[order]
+    colptr = np.concatenate([[0], np.cumsum(np.bincount(c, minlength=n))]).astype(np.int64)
+    return n, colptr, r.astype(np.int64)
+
+
+def test_plan_cache_refuses_structure_with_same_counts(tmp_path):
+    """Two structures with the same n, supernode count and level count but
+    different supernodes: a plan saved for one is refused by the other."""
+    na, cpa, ria = _blocks_problem([2, 2])
+    nb, cpb, rib = _blocks_problem([3, 1])
+    ha = ps.SelInv(na, cpa, ria, max_supernode=3, relax_pct=0, host_only=True)
+    hb = ps.SelInv(nb, cpb, rib, max_supernode=3, relax_pct=0, host_only=True)
+    sa, sb = ha.structure(), hb.structure()
+    assert (sa["n"], sa["nsuper"], sa["nlevels"]) == (sb["n"], sb["nsuper"], sb["nlevels"])
+    assert list(sa["sn_width"]) != list(sb["sn_width"])
+    ha.plan_set([(0, 0, 3)], ps.PREC_FP64)
+    path = tmp_path / "plan_a.txt"
+    ha.plan_save(path, ps.PREC_FP64)
+    ha2 = ps.SelInv(na, cpa, ria, max_supernode=3, relax_pct=0, host_only=True)
+    ha2.plan_load(path, ps.PREC_FP64)
+    assert ha2.plan_get(ps.PREC_FP64) == [(0, 0, 3)]
+    with pytest.raises(ps.PselinvError):
+        hb.plan_load(path, ps.PREC_FP64)
+    assert hb.plan_get(ps.PREC_FP64) == []
+
+
 def _header_enum(name):
     txt = open(os.path.join(ROOT, "include", "pselinv.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)

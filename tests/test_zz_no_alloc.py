@@ -73,11 +73,29 @@ def test_noalloc_matches_handle_path_twice(torch):
 
 
 def test_noalloc_rejects_oversized_block(torch):
+    import ctypes
     import paper_1708_04539_gb300 as ps
     from paper_1708_04539_gb300.binding import NOALLOC_MAX_S, block_inverse_noalloc
     s = NOALLOC_MAX_S + 1
     blk = torch.zeros((s, s), dtype=torch.float64, device="cuda")
     out = torch.zeros_like(blk)
-    with pytest.raises(ps.PselinvError) as e:
+    with pytest.raises(ValueError):
         block_inverse_noalloc(blk, out, s=s)
-    assert e.value.code == -1
+    # the library itself refuses it too (no launch is made)
+    lib = ps.load_library()
+    rc = lib.pselinv_block_inverse_noalloc(ps.F64, s, ctypes.c_void_p(blk.data_ptr()), s,
+                                           ctypes.c_void_p(out.data_ptr()), s, None)
+    assert rc == -1
+
+
+def test_noalloc_library_rejects_host_pointers(torch):
+    """A host buffer never reaches a kernel: the library checks where its
+    pointers live before launching."""
+    import ctypes
+    import paper_1708_04539_gb300 as ps
+    lib = ps.load_library()
+    host = np.eye(8)
+    dev = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    hp, dp = ctypes.c_void_p(host.ctypes.data), ctypes.c_void_p(dev.data_ptr())
+    assert lib.pselinv_block_inverse_noalloc(ps.F64, 8, hp, 8, dp, 8, None) == -1
+    assert lib.pselinv_block_inverse_noalloc(ps.F64, 8, dp, 8, hp, 8, None) == -1
