@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the selected-inversion hot path on one GB300 (or N replicas).
 
-Workload: 3D 7-point upwind convection-diffusion on a 40^3 grid
-(n = 64,000, FP64), nested-dissection ordering, supernodes of at most 256
-columns.  One step = pselinv_selinv (normalisation + the whole root-to-leaf
-sweep) + extraction of the selected entries on the pattern of A, with the
-LU factors resident in HBM.  The factorisation is timed separately.
+Default workload: the block-sparse DG operator of 16^3 elements x 64 unknowns
+(n = 262,144, FP64), nested dissection on the element grid, supernodes of
+at most 256 columns: the largest single-GPU workload of the benchmark set.
+One step = pselinv_selinv (normalisation + the whole root-to-leaf sweep) +
+extraction of the selected entries on the pattern of A, with the LU factors
+resident in HBM.  The factorisation is timed separately (and inside the
+end-to-end figure).  ``--config 2`` runs the 40^3 upwind convection-diffusion
+matrix instead (``--config 3`` / ``4``: the complex and pole-batch workloads).
 
 Metric: FP64-equivalent GFLOP/s of selected inversion, counting
 sum_K 4 c^2 s + 4 c s^2 + 4/3 s^3 over the strict (unrelaxed) supernodes.
@@ -32,22 +35,27 @@ if ROOT not in sys.path:
 
 METRIC = "selinv_fp64_equiv_gflops"
 UNIT = "GFLOP/s"
-WORKLOAD = ("3D 7-point upwind convection-diffusion 40^3 (n=64000), FP64, nested dissection, "
-            "max supernode 256, relaxed supernodes (<=20% explicit zeros)")
-OTHER_WORKLOADS = {
+HEADLINE_CONFIG = 5
+WORKLOADS = {
+    2: "3D 7-point upwind convection-diffusion {m}^3 (n={n}), FP64, nested dissection, "
+       "max supernode 256, relaxed supernodes (<=20% explicit zeros)",
     3: "3D 27-point complex operator A = H - zS + 0.2N on a {m}^3 grid (n={n}), complex128, "
        "nested dissection, max supernode 256",
     4: "pole-expansion batch: 40 complex shifts of a 3D 7-point {m}^3 operator (n={n}), "
        "complex128, one sweep for all shifts, max supernode 256",
     5: "block-sparse DG operator: {m}^3 elements x 64 unknowns (n={n}), dense element and "
-       "upwind face blocks, FP64, nested dissection on the element grid, max supernode 256",
+       "upwind face blocks, FP64, nested dissection on the element grid, max supernode 256, "
+       "relaxed supernodes (<=20% explicit zeros)",
 }
-# FP64 DFMA pipe of GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz max SM clock
-FP64_ALU_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-SAMPLE_TARGET_N = 4000  # unknowns of the leading nested-dissection subdomain timed on the CPU
+DEFAULT_SIZE = {2: 40, 3: 60, 4: 32, 5: 16}
+# unknowns of the leading nested-dissection subdomain the CPU oracle is timed on
+SAMPLE_TARGET_N = {2: 4000, 3: 2000, 4: 4000, 5: 2048}
+# smaller matrices of the same family whose tuner records train the cost model
+TRAIN_SIZES = {2: (20, 24, 28), 5: (8, 10, 12)}
+SLICES = 6
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -58,8 +66,12 @@ def parse():
                     help="ozaki: FP16-sliced tensor-core products (default); fp64: every product in FP64")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP64 level-batched / per-supernode comparison and error report")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned cost model against the exhaustive tuner and the heuristic")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="end-to-end steps (default 5; 1 for the DG operator, whose "
+                         "factorisation dominates)")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true",
                     help="skip the launch-by-launch replay (roofline fields become null)")
@@ -75,29 +87,52 @@ def parse():
     ap.add_argument("--split-normalise", action="store_true",
                     help="also slice the normalisation and D_K (by default they stay FP64)")
     ap.add_argument("--size", type=int, default=None,
-                    help="grid side (default: the configuration's own; 40 for the benchmark "
-                         "workload; smaller for profiling captures)")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
-                    help="2: 40^3 upwind (the benchmark workload); 3: 60^3 complex 27-point; "
-                         "4: 40 complex shifts of a 32^3 operator; 5: 16^3 x 64 DG operator")
-    return ap.parse_args()
+                    help="grid side (elements per side for the DG operator; default: the "
+                         "configuration's own; smaller for profiling captures)")
+    ap.add_argument("--config", type=int, default=HEADLINE_CONFIG, choices=[2, 3, 4, 5],
+                    help="5: 16^3 x 64 DG operator (default); 2: 40^3 upwind; 3: 60^3 complex "
+                         "27-point; 4: 40 complex shifts of a 32^3 operator")
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def leading_subdomain(p, target):
     """The leading nested-dissection subdomain of ``p`` with at most ``target``
-    unknowns, as a Problem in the permuted ordering (identity perm)."""
+    unknowns, as a Problem in the permuted ordering (identity perm).
+
+    The factor of a leading principal submatrix of the permuted matrix is the
+    leading block of the whole factor, so the elimination tree of the first
+    M = 4 target columns, analysed alone, gives the subtree sizes there."""
     import scipy.sparse as sp
 
     import gen
     import oracle
 
-    s = oracle.analyze(p, relax_pct=0)
     n = p.n
-    size = np.ones(n, dtype=np.int64)
-    for j in range(n):
+    M = min(n, 4 * target)
+    cols = np.repeat(np.arange(n), np.diff(p.colptr))
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[p.perm] = np.arange(n)
+    r, c = iperm[p.rowind], iperm[cols]
+    keep = (r < M) & (c < M)
+    vals = p.values if p.values.ndim == 1 else p.values[0]
+    a = sp.csc_matrix((vals[keep], (r[keep], c[keep])), shape=(M, M))
+    a.sort_indices()
+    lead = gen.Problem(f"{p.name}_prefix{M}", M, a.indptr.astype(np.int64),
+                       a.indices.astype(np.int64), a.data.copy(), np.arange(M, dtype=np.int64),
+                       p.max_supernode)
+    s = oracle.analyze(lead, relax_pct=0)
+    size = np.ones(M, dtype=np.int64)
+    for j in range(M):
         if s.parent[j] >= 0:
             size[s.parent[j]] += size[j]
     # walk up from column 0: the largest complete subtree that is exactly the
@@ -107,13 +142,10 @@ def leading_subdomain(p, target):
         if size[j] == j + 1:
             m = j + 1
         j = int(s.parent[j])
-    iperm = np.empty(n, dtype=np.int64)
-    iperm[p.perm] = np.arange(n)
-    cols = np.repeat(np.arange(n), np.diff(p.colptr))
-    a = sp.csc_matrix((p.values, (iperm[p.rowind], iperm[cols])), shape=(n, n))[:m, :m].tocsc()
-    a.sort_indices()
-    return gen.Problem(f"{p.name}_lead{m}", m, a.indptr.astype(np.int64),
-                       a.indices.astype(np.int64), a.data.copy(), np.arange(m, dtype=np.int64),
+    b = a[:m, :m].tocsc()
+    b.sort_indices()
+    return gen.Problem(f"{p.name}_lead{m}", m, b.indptr.astype(np.int64),
+                       b.indices.astype(np.int64), b.data.copy(), np.arange(m, dtype=np.int64),
                        p.max_supernode)
 
 
@@ -124,31 +156,40 @@ def exact_flops(sym):
 
 
 class OracleSample:
-    def __init__(self, p):
+    def __init__(self, p, target):
         import oracle
-        self.q = leading_subdomain(p, SAMPLE_TARGET_N)
+        self.q = leading_subdomain(p, target)
         self.sym = oracle.analyze(self.q, relax_pct=0)
         self.fac = oracle.lu(self.sym, self.q.colptr, self.q.rowind, self.q.values)
-        self.flops = exact_flops(self.sym)
-        self.desc = (f"selected inversion (Theorem 1 oracle, single thread) of the leading "
-                     f"nested-dissection subdomain of the same matrix: n={self.q.n}, "
-                     f"{self.flops:.3e} flop; LU untimed")
+        self.flops = exact_flops(self.sym) * (4.0 if np.iscomplexobj(self.q.values) else 1.0)
+        self.desc = (f"selected inversion (Theorem 1 oracle) of the leading nested-dissection "
+                     f"subdomain of the same matrix: n={self.q.n}, {self.flops:.3e} flop; "
+                     f"LU untimed")
 
-    def step(self):
+    def step(self, threads=1):
         import oracle
         t0 = time.perf_counter()
-        oracle.selinv(self.fac)
+        if threads == 1:
+            oracle.selinv(self.fac)
+        else:
+            oracle.selinv_parallel(self.fac, threads)
         return time.perf_counter() - t0
 
 
-def cpu_baseline(p, min_seconds=10.0, max_reps=5):
-    smp = OracleSample(p)
+def cpu_baseline(p, target, min_seconds=6.0, max_reps=5):
+    """The oracle on every host core (independent columns of one depth, or one
+    column's dot products, in parallel), with its single-thread time beside it."""
+    smp = OracleSample(p, target)
+    cores = host_cores()
+    single = smp.step(1)
     times = []
     while len(times) < max_reps and (sum(times) < min_seconds or len(times) < 1):
-        times.append(smp.step())
+        times.append(smp.step(cores))
     t = statistics.median(times)
-    return {"value": smp.flops / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": smp.desc, "seconds_per_sample": t, "reps": len(times)}
+    return {"value": smp.flops / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": smp.desc, "seconds_per_sample": t, "reps": len(times),
+            "single_thread": {"value": smp.flops / single / 1e9, "cores": 1,
+                              "seconds_per_sample": single}}
 
 
 # ---------------------------------------------------------------------------
@@ -216,7 +257,7 @@ def measured_peaks():
 GEMM_TEMPLATES = {0: "64,64,16", 1: "32,32,16", 2: "128,64,8"}  # tile config -> BM,BN,BK (3: row panels)
 
 
-def roofline_from_profile(prof, slices):
+def roofline_from_profile(prof, slices, fp64_peak):
     """Roofline record of the kernel kind with the largest share of the step."""
     kinds = {}
     for r in prof:
@@ -247,8 +288,9 @@ def roofline_from_profile(prof, slices):
             tile = GEMM_TEMPLATES.get(main_param, "?")
             name, tkey = f"gemm_kernel<double,{tile}> (FP64 DFMA)", "gemm_kernel_f64"
         rec = {"bound": "alu", "kernel": name,
-               "achieved": achieved, "peak": FP64_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+               "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+               "peak_source": "measured in this run: pselinv_measure_fp64_peak (FP64 FMA loop "
+                              "on every SM; mma.sync f64 measured slower on GB300)",
                "traffic": traffic_from_profiles(tkey)}
     elif top == "ozaki_gemm":
         pairs = slices * (slices + 1) // 2
@@ -273,24 +315,110 @@ def roofline_from_profile(prof, slices):
                  for n, v in kinds.items()}
 
 
-def selected_error(x, r, rows, cols, n):
-    """max |x - r| / max(row max, column max of |r|) over the entries given."""
-    a = np.abs(r)
-    rowmax = np.zeros(n)
-    colmax = np.zeros(n)
-    np.maximum.at(rowmax, rows, a)
-    np.maximum.at(colmax, cols, a)
-    rho = np.maximum(rowmax[rows], colmax[cols])
-    rho[rho == 0] = 1.0
-    return float(np.max(np.abs(x - r) / rho))
+def path_roofline(st, cplx, nbatch, ms_step, fp64_peak, split):
+    """Path-level roofline of one sweep from its level structure.
+
+    Per supernode (width s, c = |R_K|, relaxed structure): products of steps
+    3-5 P = 4 c^2 s + 2 c s^2, FP64 normalisation and diagonal block
+    F = 2 c s^2 + 4/3 s^3, algorithmic bytes (c^2 + 2 (2 c s + s^2)) w (G read
+    once, panels read and written).  FP64 roofline of level l:
+    min(P_fp64, AI_l x HBM) over all its flops; split roofline: the sliced
+    products at the tensor peak (21 slice products each) or HBM, whichever
+    is slower, plus F at the FP64 peak.  frac = roofline time / measured."""
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6778.7)) * 1e9
+    tensor = float(peaks.get("bf16_tflops", 1925.5)) * 1e12
+    p64 = fp64_peak * 1e12
+    mult = (4.0 if cplx else 1.0) * nbatch
+    w = (16.0 if cplx else 8.0)
+    width = np.asarray(st["sn_width"], dtype=float)
+    c = np.diff(np.asarray(st["rows_ptr"])).astype(float)
+    depth = np.asarray(st["sn_depth"])
+    prod = (4 * c * c * width + 2 * c * width * width) * mult
+    norm = (2 * c * width * width + 4.0 / 3.0 * width ** 3) * mult
+    byts = (c * c + 2 * (2 * c * width + width * width)) * w * nbatch
+    t64 = tsplit = 0.0
+    pairs = SLICES * (SLICES + 1) // 2
+    for lev in range(int(st["nlevels"])):
+        m = depth == lev
+        f, b = float((prod[m] + norm[m]).sum()), float(byts[m].sum())
+        if f <= 0:
+            continue
+        t64 += f / min(p64, f / b * hbm)
+        tsplit += max(float(prod[m].sum()) * pairs / tensor, b / hbm) + float(norm[m].sum()) / p64
+    sec = ms_step * 1e-3
+    out = {"fp64_roofline_ms": t64 * 1e3, "frac_vs_fp64_roofline": t64 / sec,
+           "definition": "sum over depth levels of flops_l / min(P_fp64, AI_l x HBM), over the "
+                         "measured step (the split path may exceed 1)"}
+    if split:
+        out.update({"split_roofline_ms": tsplit * 1e3, "frac_vs_split_roofline": tsplit / sec,
+                    "split_definition": "per level max(21 x products / tensor peak, bytes / HBM) "
+                                        "+ FP64 normalisation / P_fp64, over the measured step"})
+    return out
 
 
-def time_steps(h, prec, stream, steps, out_dev):
+def _supernode_blocks(st, K):
+    """(offset, s, first column, R_K) of supernode K of the storage."""
+    s = int(st["sn_width"][K])
+    f = int(st["sn_first"][K])
+    R = st["rows"][st["rows_ptr"][K]:st["rows_ptr"][K + 1]]
+    return int(st["sn_offset"][K]), s, f, R
+
+
+def selected_error_supernodal(st, x, r):
+    """Error of the supernodal storage x against r (device tensors of one
+    instance): max over every stored entry (i, j) of |x_ij - r_ij| /
+    max(max_k |r_ik|, max_k |r_kj|), the maxima over the stored entries of
+    row i and column j; and the normwise error max |x - r| / max |r|.
+    Computed supernode by supernode on the device."""
+    import torch
+    n = int(st["n"])
+    dev = r.device
+    ra = r.abs() if not r.is_complex() else r.abs()
+    rowmax = torch.zeros(n, dtype=torch.float64, device=dev)
+    colmax = torch.zeros(n, dtype=torch.float64, device=dev)
+    views = []
+    for K in range(int(st["nsuper"])):
+        o, s, f, R = _supernode_blocks(st, K)
+        c = R.size
+        Rd = torch.from_numpy(np.ascontiguousarray(R)).to(dev)
+        d = ra[o:o + s * s].view(s, s)                    # [col][row]: (f+i, f+j) at i + j s
+        rowmax[f:f + s] = torch.maximum(rowmax[f:f + s], d.amax(dim=0))
+        colmax[f:f + s] = torch.maximum(colmax[f:f + s], d.amax(dim=1))
+        if c:
+            lp = ra[o + s * s:o + s * s + c * s].view(s, c)   # [t][p] = (R[p], f+t)
+            up = ra[o + s * s + c * s:o + s * s + 2 * c * s].view(s, c)  # [t][p] = (f+t, R[p])
+            rowmax[Rd] = torch.maximum(rowmax[Rd], lp.amax(dim=0))
+            colmax[f:f + s] = torch.maximum(colmax[f:f + s], lp.amax(dim=1))
+            rowmax[f:f + s] = torch.maximum(rowmax[f:f + s], up.amax(dim=1))
+            colmax[Rd] = torch.maximum(colmax[Rd], up.amax(dim=0))
+        views.append((o, s, f, c, Rd))
+    worst = torch.zeros((), dtype=torch.float64, device=dev)
+    for o, s, f, c, Rd in views:
+        rm, cm = rowmax[f:f + s], colmax[f:f + s]
+        e = (x[o:o + s * s] - r[o:o + s * s]).abs().view(s, s)
+        rho = torch.maximum(rm[None, :], cm[:, None])
+        worst = torch.maximum(worst, (e / torch.where(rho > 0, rho, 1.0)).max())
+        if c:
+            a, b = o + s * s, o + s * s + c * s
+            e = (x[a:b] - r[a:b]).abs().view(s, c)
+            rho = torch.maximum(rowmax[Rd][None, :], cm[:, None])
+            worst = torch.maximum(worst, (e / torch.where(rho > 0, rho, 1.0)).max())
+            e = (x[b:b + c * s] - r[b:b + c * s]).abs().view(s, c)
+            rho = torch.maximum(rm[:, None], colmax[Rd][None, :])
+            worst = torch.maximum(worst, (e / torch.where(rho > 0, rho, 1.0)).max())
+    normwise = float((x - r).abs().max() / ra.max())
+    return float(worst), normwise
+
+
+def time_steps(h, prec, stream, steps, out_dev, warm=True):
+    """Mean ms of `steps` sweeps + extractions (CUDA events on `stream`)."""
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
-        h.selinv(precision=prec, stream=stream)
-        h.get_selected(out_dev, stream=stream)
+        if warm:
+            h.selinv(precision=prec, stream=stream)
+            h.get_selected(out_dev, stream=stream)
         e0.record(stream)
         for _ in range(steps):
             h.selinv(precision=prec, stream=stream)
@@ -300,45 +428,103 @@ def time_steps(h, prec, stream, steps, out_dev):
     return e0.elapsed_time(e1) / steps
 
 
-def comparison(p, h, stream, out_dev, flops):
+def comparison(p, h, stream, out_dev, flops, big):
     """FP64 level-batched and FP64 per-supernode sweeps of the same matrix,
-    and the error of the split-precision result against the FP64 one."""
+    and the error of the split-precision result against the FP64 one.
+
+    big: the FP64 arms take about a minute each, so they run the built-in
+    heuristic plan once (no tuning, no repeat; the plan is built before the
+    timed call)."""
     import torch
     import paper_1708_04539_gb300 as ps
-    from paper_1708_04539_gb300.binding import supernodal_coordinates
     st = h.structure()
-    rows, cols = supernodal_coordinates(st)
-    h.selinv(precision=ps.PREC_OZAKI_FP16, stream=stream)
-    split = h.get_selected(layout=ps.LAYOUT_SUPERNODAL, stream=stream)
-    h.tune(precision=ps.PREC_FP64, mode=ps.TUNE_EXHAUSTIVE, stream=stream)
-    fp64_level_ms = time_steps(h, ps.PREC_FP64, stream, 3, out_dev)
-    ref = h.get_selected(layout=ps.LAYOUT_SUPERNODAL, stream=stream)
-    err = selected_error(split, ref, rows, cols, p.n)
-    normwise = float(np.max(np.abs(split - ref)) / np.max(np.abs(ref)))
-    g = ps.SelInv.from_problem(p, relax_pct=20, schedule=ps.SCHED_PER_SUPERNODE)
+    cplx = np.iscomplexobj(p.values)
+    odt = torch.complex128 if cplx else torch.float64
+    total = int(st["storage_size"])
+    split = torch.empty(total, dtype=odt, device="cuda")
+    ref = torch.empty(total, dtype=odt, device="cuda")
     with torch.cuda.stream(stream):
-        g.factor(torch.from_numpy(p.values).cuda(), stream=stream)
-    per_sn_ms = time_steps(g, ps.PREC_FP64, stream, 2, out_dev)
-    g.close()
-    # option: normalisation and D_K as sliced products too
-    q = ps.SelInv.from_problem(p, relax_pct=20, split_normalise=True)
+        h.selinv(precision=ps.PREC_OZAKI_FP16, stream=stream)
+        h.get_selected(split, layout=ps.LAYOUT_SUPERNODAL, stream=stream)
+    torch.cuda.synchronize()
+    h.tune(precision=ps.PREC_FP64, mode=ps.TUNE_RESET if big else ps.TUNE_EXHAUSTIVE,
+           stream=stream)
+    fp64_level_ms = time_steps(h, ps.PREC_FP64, stream, 1 if big else 3, out_dev, warm=not big)
     with torch.cuda.stream(stream):
-        q.factor(torch.from_numpy(p.values).cuda(), stream=stream)
-        q.tune(precision=ps.PREC_OZAKI_FP16, mode=ps.TUNE_EXHAUSTIVE, stream=stream)
-    sn_ms = time_steps(q, ps.PREC_OZAKI_FP16, stream, 5, out_dev)
-    sn_err = selected_error(q.get_selected(layout=ps.LAYOUT_SUPERNODAL, stream=stream), ref,
-                            rows, cols, p.n)
-    q.close()
-    return {"fp64_level_batched_ms": fp64_level_ms,
-            "fp64_level_batched_gflops": flops / (fp64_level_ms * 1e-3) / 1e9,
-            "fp64_per_supernode_ms": per_sn_ms,
-            "fp64_per_supernode_gflops": flops / (per_sn_ms * 1e-3) / 1e9,
-            "split_vs_fp64_selected_error": err, "split_vs_fp64_normwise_error": normwise,
-            "split_normalise_option_ms": sn_ms,
-            "split_normalise_option_gflops": flops / (sn_ms * 1e-3) / 1e9,
-            "split_normalise_option_error": sn_err,
-            "error_metric": "max |x - r| / max(max_k |r_ik|, max_k |r_kj|) over every entry "
-                            "of the pattern of L+U; r = FP64 GPU result"}
+        h.get_selected(ref, layout=ps.LAYOUT_SUPERNODAL, stream=stream)
+    torch.cuda.synchronize()
+    err, normwise = selected_error_supernodal(st, split, ref)
+    del split
+    h.set_schedule(ps.SCHED_PER_SUPERNODE)
+    h.tune(precision=ps.PREC_FP64, mode=ps.TUNE_RESET, stream=stream)  # builds its plan
+    per_sn_ms = time_steps(h, ps.PREC_FP64, stream, 1 if big else 2, out_dev, warm=not big)
+    h.set_schedule(ps.SCHED_LEVEL)
+    out = {"fp64_level_batched_ms": fp64_level_ms,
+           "fp64_level_batched_gflops": flops / (fp64_level_ms * 1e-3) / 1e9,
+           "fp64_level_plan": "heuristic" if big else "exhaustive",
+           "fp64_per_supernode_ms": per_sn_ms,
+           "fp64_per_supernode_gflops": flops / (per_sn_ms * 1e-3) / 1e9,
+           "split_vs_fp64_selected_error": err, "split_vs_fp64_normwise_error": normwise,
+           "error_metric": "max |x - r| / max(max_k |r_ik|, max_k |r_kj|) over every entry "
+                           "of the pattern of L+U; r = FP64 GPU result"}
+    if not big:
+        # option: normalisation and D_K as sliced products too
+        q = ps.SelInv.from_problem(p, relax_pct=20, split_normalise=True)
+        with torch.cuda.stream(stream):
+            q.factor(torch.from_numpy(p.values).cuda(), stream=stream)
+            q.tune(precision=ps.PREC_OZAKI_FP16, mode=ps.TUNE_EXHAUSTIVE, stream=stream)
+        sn_ms = time_steps(q, ps.PREC_OZAKI_FP16, stream, 5, out_dev)
+        qx = torch.empty(total, dtype=odt, device="cuda")
+        with torch.cuda.stream(stream):
+            q.get_selected(qx, layout=ps.LAYOUT_SUPERNODAL, stream=stream)
+        torch.cuda.synchronize()
+        sn_err, _ = selected_error_supernodal(st, qx, ref)
+        q.close()
+        out.update({"split_normalise_option_ms": sn_ms,
+                    "split_normalise_option_gflops": flops / (sn_ms * 1e-3) / 1e9,
+                    "split_normalise_option_error": sn_err})
+    del ref
+    return out
+
+
+def train_cost_model(config, prec, stream):
+    """A cost model trained on the exhaustive tuner's records of smaller
+    matrices of the same family (never on the benchmark matrix itself)."""
+    import torch
+
+    import gen
+    import paper_1708_04539_gb300 as ps
+    recs, names = [], []
+    for size in TRAIN_SIZES[config]:
+        if config == 5:
+            q = gen.dg_blocks(size, 64, 1708045390 + 50 + size, max_sn=256)
+        else:
+            q = gen.upwind_3d(size, 1708045390 + 80 + size, max_sn=256)
+        g = ps.SelInv.from_problem(q, relax_pct=20)
+        with torch.cuda.stream(stream):
+            g.factor(torch.from_numpy(q.values).cuda(), stream=stream)
+            g.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE, stream=stream)
+        recs += g.tune_records()
+        names.append(f"n={q.n}")
+        g.close()
+    m = ps.CostModel(hidden=32, seed=5)
+    loss = m.train(recs, epochs=4000, lr=3e-3, stream=stream)
+    return m, {"records": len(recs), "matrices": names, "final_loss": loss,
+               "network": "16 -> 32 -> 32 -> 1 tanh MLP, full-batch Adam, 4000 epochs"}
+
+
+def learned_vs_exhaustive(h, prec, stream, out_dev, model, info, exhaustive_ms, triples):
+    """Sweep time of the heuristic plan, the model-tuned plan and the
+    exhaustive plan (already timed); the exhaustive plan is restored after."""
+    import paper_1708_04539_gb300 as ps
+    h.tune(precision=prec, mode=ps.TUNE_RESET, stream=stream)
+    heur = time_steps(h, prec, stream, 3, out_dev)
+    h.tune(precision=prec, mode=ps.TUNE_MODEL, model=model, stream=stream)
+    mod = time_steps(h, prec, stream, 3, out_dev)
+    h.plan_set(triples, prec)
+    return dict(info, heuristic_ms=heur, model_ms=mod, exhaustive_ms=exhaustive_ms,
+                regret_vs_exhaustive=(mod - exhaustive_ms) / exhaustive_ms,
+                gain_over_heuristic=heur / mod)
 
 
 def max_over_ranks(value, dist, device):
@@ -377,26 +563,36 @@ def traffic_from_profiles(kernel):
     return ent["bytes_per_launch"] if sha == ent.get("source_sha") else None
 
 
+def workload_name(config, size, n):
+    return WORKLOADS[config].format(m=size, n=n)
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import gen
-    p = gen.make_config(2)
-    smp = OracleSample(p)
+    config = args.config
+    size = args.size or DEFAULT_SIZE[config]
+    p = gen.make_config(config, size=args.size)
+    if config == 4:
+        p = p[0]
+    smp = OracleSample(p, SAMPLE_TARGET_N[config])
+    cores = host_cores()
     for _ in range(args.warmup):
-        smp.step()
-    times = [smp.step() for _ in range(args.steps)]
+        smp.step(cores)
+    times = [smp.step(cores) for _ in range(args.steps)]
     t = sum(times) / len(times)
     value = smp.flops / t / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": smp.desc},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "vs_baseline": None, "dtype": "c128" if np.iscomplexobj(p.values) else "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(config, size, p.n), "sample": smp.desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": smp.desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -409,6 +605,7 @@ def run_ours(args):
 
     import gen
     import paper_1708_04539_gb300 as ps
+    from paper_1708_04539_gb300.binding import measure_fp64_peak
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -429,18 +626,17 @@ def run_ours(args):
         dist.barrier()
     ps.load_library()
 
-    p = gen.make_config(args.config, size=args.size)
-    if args.config == 4:
+    config = args.config
+    p = gen.make_config(config, size=args.size)
+    if config == 4:
         p = p[0]  # the shift family (the uneven grids are a parity case)
-    size = args.size or {2: 40, 3: 60, 4: 32, 5: 16}[args.config]
-    if args.config == 2:
-        workload = WORKLOAD if size == 40 else WORKLOAD.replace(
-            "40^3 (n=64000)", f"{size}^3 (n={size ** 3})")
-    else:
-        workload = OTHER_WORKLOADS[args.config].format(m=size, n=p.n)
+    size = args.size or DEFAULT_SIZE[config]
+    workload = workload_name(config, size, p.n)
+    big = config == 5 and size >= 14
+    headline = config in (2, 5)
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else (1 if big else 5)
     cplx = np.iscomplexobj(p.values)
     nbatch = p.nbatch
-    headline = args.config == 2
     sched = ps.SCHED_PER_SUPERNODE if args.schedule == "per_supernode" else ps.SCHED_LEVEL
     h = ps.SelInv.from_problem(p, relax_pct=20, schedule=sched, use_graph=not args.no_graph,
                                split_normalise=args.split_normalise)
@@ -452,17 +648,28 @@ def run_ours(args):
     odt = torch.complex128 if cplx else torch.float64
     out_dev = torch.zeros((nbatch, p.nnz), dtype=odt, device="cuda")
 
-    # factorisation (timed separately)
+    # factorisation: the first call builds its plan (untimed); it is timed
+    # inside the end-to-end step below (and here when there is none)
     with torch.cuda.stream(stream):
         h.factor(vals_dev, stream=stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h.factor(vals_dev, stream=stream)
-        e1.record(stream)
     torch.cuda.synchronize()
-    factor_ms = e0.elapsed_time(e1)
+    factor_ms = None
+    if e2e_steps <= 0:
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.factor(vals_dev, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        factor_ms = e0.elapsed_time(e1)
+    fp64_peak, _ = measure_fp64_peak(stream)
 
     prec = ps.PREC_OZAKI_FP16 if args.precision == "ozaki" else ps.PREC_FP64
+    learned = (not args.no_learned and rank == 0 and world == 1 and headline and
+               args.tune == "exhaustive" and not args.plan_in and config in TRAIN_SIZES)
+    model = model_info = None
+    if learned:
+        model, model_info = train_cost_model(config, prec, stream)
     tune_s = 0.0
     tuning = args.tune
     if args.plan_in:
@@ -475,10 +682,11 @@ def run_ours(args):
             h.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE, stream=stream)
         torch.cuda.synchronize()
         tune_s = time.perf_counter() - t0
+    triples = h.plan_get(prec)
     if args.plan_out:
         with open(args.plan_out, "w") as f:
-            json.dump({"precision": args.precision, "config": args.config, "size": size,
-                       "triples": h.plan_get(prec)}, f)
+            json.dump({"precision": args.precision, "config": config, "size": size,
+                       "triples": triples}, f)
 
     def step():
         h.selinv(precision=prec, stream=stream)
@@ -510,45 +718,63 @@ def run_ours(args):
 
     # launch-by-launch replay with CUDA events on the same stream
     prof = [] if args.no_profile else h.profile(0, stream=stream)
-    roofline, kinds = roofline_from_profile(prof, slices=6)
+    roofline, kinds = roofline_from_profile(prof, SLICES, fp64_peak)
+    if roofline is not None:
+        roofline["path"] = path_roofline(st, cplx, nbatch, ms_per_step / 1.0, fp64_peak,
+                                         prec == ps.PREC_OZAKI_FP16)
     if args.dump_profile and rank == 0:
         with torch.cuda.stream(stream):
-            fprof = h.profile(1, stream=stream)
+            fprof = [] if big else h.profile(1, stream=stream)
             h.profile(2, stream=stream)  # warm the multi-stream timeline once
             timeline = h.profile(2, stream=stream)
         with open(args.dump_profile, "w") as f:
-            json.dump({"precision": args.precision, "config": args.config, "size": size, "steps": prof,
+            json.dump({"precision": args.precision, "config": config, "size": size, "steps": prof,
                        "factor_steps": fprof, "timeline": timeline}, f)
+
+    # the learned cost model against the exhaustive tuner and the heuristic
+    learned_rec = None
+    if learned:
+        learned_rec = learned_vs_exhaustive(h, prec, stream, out_dev[0], model, model_info,
+                                            ms_per_step, triples)
+        model.close()
 
     # end to end through the C ABI with host buffers: H2D values, factor,
     # selected inversion, D2H of the selected entries
     e2e = None
-    if args.e2e_steps > 0:
+    if e2e_steps > 0:
         vals_host = torch.from_numpy(p.values.copy()).pin_memory()
         out_host = torch.zeros((nbatch, p.nnz), dtype=odt).pin_memory()
+        fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-        def e2e_step():
+        def e2e_step(time_factor):
+            if time_factor:
+                fe0.record(stream)
             h.factor(vals_host, stream=stream)
+            if time_factor:
+                fe1.record(stream)
             h.selinv(precision=prec, stream=stream)
             for b in range(nbatch):
                 h.get_selected(out_host[b], batch=b, stream=stream)
 
-        with torch.cuda.stream(stream):
-            e2e_step()
-        torch.cuda.synchronize()
+        if not big:
+            with torch.cuda.stream(stream):
+                e2e_step(False)
+            torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for _ in range(args.e2e_steps):
-                e2e_step()
+            for i in range(e2e_steps):
+                e2e_step(i == 0)
         torch.cuda.synchronize()
-        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, "cuda")
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
+        factor_ms = fe0.elapsed_time(fe1)
         io_bytes = int(p.nnz * nbatch * (16 if cplx else 8))
         e2e = {"value": world * flops / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
-               "ms_per_step": e2e_s * 1e3,
+               "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
                "includes": "H2D values, factor, selinv, extract, D2H"}
+        del vals_host, out_host
 
     stats = h.plan_stats()
     nl = stats["launches_selinv"]
@@ -568,23 +794,27 @@ def run_ours(args):
                    "tuning": tuning, "tuning_seconds": tune_s,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.0f MB of factors read per step)"
-                         % (st["storage_size"] * 8 / 1e6)},
+                         % (st["storage_size"] * (16 if cplx else 8) * nbatch / 1e6)},
         "time_per_matrix_ms": ms_per_step / nbatch,
         "factor_ms": factor_ms,
         "e2e": e2e,
-        "gpu_launches": int((nl + 1) * args.steps),
+        "gpu_launches": int((nl + nbatch) * args.steps),
+        "launches_per_sweep": int(nl),
         "launches_factor": int(stats["launches_factor"]),
+        "fp64_peak_tflops": fp64_peak,
         "roofline": roofline,
         "kernel_shares": kinds,
         "clocks": clk.summary(),
     }
     if not prof:
         line["roofline"] = None
+    if learned_rec is not None:
+        line["learned"] = learned_rec
     if not args.no_compare and args.precision == "ozaki" and rank == 0 and headline:
-        line["comparison"] = comparison(p, h, stream, out_dev[0], flops)
+        line["comparison"] = comparison(p, h, stream, out_dev[0], flops, big)
     h.close()
-    if rank == 0 and world == 1 and not args.skip_cpu_baseline and headline and size == 40:
-        line["cpu_baseline"] = cpu_baseline(p)
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline and headline:
+        line["cpu_baseline"] = cpu_baseline(p, SAMPLE_TARGET_N[config])
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

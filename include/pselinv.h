@@ -177,6 +177,14 @@ int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, v
  * on `stream`. */
 int pselinv_selinv(pselinv_t h, int precision, void* stream);
 
+/* Schedule of later pselinv_selinv / pselinv_tune calls (the handle's
+ * opts.schedule): PSELINV_SCHED_LEVEL (one batched launch per kind and
+ * depth level, the priority list of Section 3.3 as levels) or
+ * PSELINV_SCHED_PER_SUPERNODE (the same products launched supernode by
+ * supernode, for comparison).  The plan of each schedule is built on its
+ * first use and kept.  Host only. */
+int pselinv_set_schedule(pselinv_t h, int schedule);
+
 /* Copy results of instance `batch` (Algorithm 1 step 6 and Theorem 2 for
  * PSELINV_LAYOUT_PATTERN_A: out[p] = (A^{-1})_{rowind[p], j} for entry p of
  * column j of the input; PSELINV_LAYOUT_SUPERNODAL: storage_size scalars of
@@ -373,6 +381,16 @@ int pselinv_trace(pselinv_t h, const void* weights, const void* B, void* out, vo
  * when the timeout was detected and reported to the host (the expected
  * result), PSELINV_OK if it was not. */
 int pselinv_wait_selftest(void* stream, int64_t budget_us);
+
+/* FP64 peak of the current device, measured (not from the paper; the
+ * denominator of the FP64 roofline that the products, normalisation and
+ * factorisation kernels are reported against): one launch of a loop of
+ * fused multiply-adds, eight independent chains per thread and eight CTAs
+ * of 256 threads per SM, timed with CUDA events on `stream` after a shorter
+ * warm-up launch.  *tflops = FP64 TFLOP/s (2 flops per FMA); *ms (nullable)
+ * = the timed launch's duration.  Allocates and frees a small device
+ * buffer; synchronises `stream`. */
+int pselinv_measure_fp64_peak(void* stream, double* tflops, double* ms);
 
 /* Wait for `stream` and report a device-side error recorded by earlier calls. */
 int pselinv_sync(pselinv_t h, void* stream);

@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(d) <= t for d in deps):
             return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
            "-o", tmp] + src + ["-lm"]
     subprocess.run(cmd, check=True, cwd=_HERE)
     os.replace(tmp, _LIB_PATH)
@@ -75,6 +75,9 @@ def _load():
             f.argtypes = [P, P, P, P, P, P, P, ctypes.POINTER(I)]
             f.restype = ctypes.c_int
             f = getattr(lib, f"oracle_selinv_{t}")
+            f.argtypes = [P, P, P, P, P, P, P, ctypes.c_int]
+            f.restype = ctypes.c_int
+            f = getattr(lib, f"oracle_selinv_par_{t}")
             f.argtypes = [P, P, P, P, P, P, P, ctypes.c_int]
             f.restype = ctypes.c_int
             f = getattr(lib, f"oracle_extract_{t}")
@@ -202,6 +205,23 @@ def selinv(fac: Factors, mutation: int = 0) -> Selected:
            int(mutation))
     if rc != 0:
         raise OracleError(rc, "selinv")
+    return Selected(sym, bl, bu, bd)
+
+
+def selinv_parallel(fac: Factors, nthreads: int) -> Selected:
+    """selinv with the independent columns of each depth of the structures'
+    tree run by ``nthreads`` OpenMP threads (bit for bit selinv's result)."""
+    lib = _load()
+    sym = fac.sym
+    dt = fac.low.dtype
+    bl = np.zeros(sym.nnzl, dtype=dt)
+    bu = np.zeros(sym.nnzl, dtype=dt)
+    bd = np.zeros(sym.n, dtype=dt)
+    f = lib.oracle_selinv_par_z if np.iscomplexobj(fac.low) else lib.oracle_selinv_par_d
+    rc = f(sym._h, _ptr(fac.low), _ptr(fac.up), _ptr(fac.diag), _ptr(bl), _ptr(bu), _ptr(bd),
+           int(nthreads))
+    if rc != 0:
+        raise OracleError(rc, "selinv_parallel")
     return Selected(sym, bl, bu, bd)
 
 

@@ -385,6 +385,12 @@ int oracle_selinv_z(const oracle_sym* s, const void* Llow, const void* Uup, cons
                               (const double _Complex*)Udiag, (double _Complex*)Blow,
                               (double _Complex*)Bup, (double _Complex*)Bdiag, mutation);
 }
+int oracle_selinv_par_z(const oracle_sym* s, const void* Llow, const void* Uup, const void* Udiag,
+                        void* Blow, void* Bup, void* Bdiag, int nthreads) {
+  return oracle_selinv_par_z_impl(s, (const double _Complex*)Llow, (const double _Complex*)Uup,
+                                  (const double _Complex*)Udiag, (double _Complex*)Blow,
+                                  (double _Complex*)Bup, (double _Complex*)Bdiag, nthreads);
+}
 int oracle_extract_z(const oracle_sym* s, const int64_t* colptr, const int64_t* rowind,
                      const void* Blow, const void* Bup, const void* Bdiag, void* out) {
   return oracle_extract_z_impl(s, colptr, rowind, (const double _Complex*)Blow,

@@ -94,6 +94,14 @@ int oracle_selinv_d(const oracle_sym* s, const double* Llow, const double* Uup,
                     int mutation);
 int oracle_selinv_z(const oracle_sym* s, const void* Llow, const void* Uup,
                     const void* Udiag, void* Blow, void* Bup, void* Bdiag, int mutation);
+/* The same, with the columns of one depth of the structures' tree (roots
+ * first; they never read each other's entries) run by nthreads OpenMP
+ * threads; bit for bit the result of oracle_selinv_* (no mutations). */
+int oracle_selinv_par_d(const oracle_sym* s, const double* Llow, const double* Uup,
+                        const double* Udiag, double* Blow, double* Bup, double* Bdiag,
+                        int nthreads);
+int oracle_selinv_par_z(const oracle_sym* s, const void* Llow, const void* Uup,
+                        const void* Udiag, void* Blow, void* Bup, void* Bdiag, int nthreads);
 
 /* Selected entries in the ORIGINAL ordering on the pattern of A (Theorem 2):
  * out[p] = (A^{-1})_{rowind[p], j} for p in column j. */

@@ -29,7 +29,8 @@ _EXPORTS = [
     "pselinv_get_selected", "pselinv_get_structure", "pselinv_profile", "pselinv_plan_stats",
     "pselinv_sync", "pselinv_last_info", "pselinv_error_string", "pselinv_free",
     "pselinv_block_inverse_noalloc", "pselinv_tune", "pselinv_tune_records",
-    "pselinv_plan_get", "pselinv_plan_set", "pselinv_wait_selftest",
+    "pselinv_plan_get", "pselinv_plan_set", "pselinv_wait_selftest", "pselinv_measure_fp64_peak",
+    "pselinv_set_schedule",
     "pselinv_weighted_sum", "pselinv_trace",
     "pselinv_model_create", "pselinv_model_train", "pselinv_model_gradients",
     "pselinv_model_predict", "pselinv_model_get_params", "pselinv_model_set_params",
@@ -145,6 +146,11 @@ def load_library():
     lib.pselinv_block_inverse_noalloc.restype = ctypes.c_int
     lib.pselinv_wait_selftest.argtypes = [P, I64]
     lib.pselinv_wait_selftest.restype = ctypes.c_int
+    lib.pselinv_measure_fp64_peak.argtypes = [P, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]
+    lib.pselinv_measure_fp64_peak.restype = ctypes.c_int
+    lib.pselinv_set_schedule.argtypes = [P, ctypes.c_int]
+    lib.pselinv_set_schedule.restype = ctypes.c_int
     RP = ctypes.POINTER(TuneRecord)
     lib.pselinv_tune.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     lib.pselinv_tune.restype = ctypes.c_int
@@ -310,6 +316,10 @@ class SelInv:
         self._check(self._lib.pselinv_plan_stats(self._h, ctypes.byref(a), ctypes.byref(b)),
                     "pselinv_plan_stats")
         return {"launches_selinv": a.value, "launches_factor": b.value}
+
+    def set_schedule(self, schedule):
+        """Schedule of later selinv/tune calls (SCHED_LEVEL or SCHED_PER_SUPERNODE)."""
+        self._check(self._lib.pselinv_set_schedule(self._h, int(schedule)), "pselinv_set_schedule")
 
     def tune(self, precision=PREC_FP64, mode=TUNE_EXHAUSTIVE, model=None, stream=None):
         """Autotune the launch shapes of the selected-inversion plan."""
@@ -641,6 +651,17 @@ def order_nd(n, colptr, rowind, leaf=4):
     if rc != 0:
         raise PselinvError(rc, "pselinv_order_nd")
     return perm
+
+
+def measure_fp64_peak(stream=None):
+    """(TFLOP/s, ms) of the library's FP64 fused multiply-add loop on every SM
+    of the current device (the FP64 roofline's denominator)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = load_library().pselinv_measure_fp64_peak(_stream(stream), ctypes.byref(tf),
+                                                  ctypes.byref(ms))
+    if rc != 0:
+        raise PselinvError(rc, "pselinv_measure_fp64_peak")
+    return tf.value, ms.value
 
 
 def wait_selftest(budget_us=20000, stream=None):

@@ -1056,6 +1056,18 @@ bool add_small_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   return true;
 }
 
+// FP64-equivalent flops of the products of steps 3-5 of depth level `lev`
+// over every instance (sum 4 c^2 s; x4 for complex)
+double level_product_flops(const pselinv_ctx* h, int lev) {
+  const HostSym& H = h->H;
+  double lf = 0;
+  for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
+    const double c = (double)cK(H, H.level_sn[i]), w = (double)H.sn_width[H.level_sn[i]];
+    lf += 4.0 * c * c * w;
+  }
+  return lf * (double)h->nbatch * (h->dtype == DT_F64 ? 1.0 : 4.0);
+}
+
 int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   const HostSym& H = h->H;
   const bool sym = h->opts.symmetric != 0;
@@ -1187,15 +1199,8 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
     // to pay for the slicing, the FP64 ones; the default is a flop
     // threshold, the tuner times both
     int mode = 0;
-    if (precision == PSELINV_PREC_OZAKI_FP16) {
-      double lf = 0;
-      for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
-        const double c = (double)cK(H, H.level_sn[i]), w = (double)H.sn_width[H.level_sn[i]];
-        lf += 4.0 * c * c * w;
-      }
-      lf *= (double)nb * (dt == DT_F64 ? 1.0 : 4.0);
-      mode = tuned_value(h, precision, (int)lev, 3, lf < 2e8 ? 1 : 0);
-    }
+    if (precision == PSELINV_PREC_OZAKI_FP16)
+      mode = tuned_value(h, precision, (int)lev, 3, level_product_flops(h, (int)lev) < 2e8 ? 1 : 0);
     const bool split_level = precision == PSELINV_PREC_OZAKI_FP16 && mode == 0;
     add_normalize((int)lev, split_level && h->opts.split_normalise != 0);
     const size_t first_main = P.steps.size();
@@ -1593,6 +1598,13 @@ int pselinv_selinv(pselinv_t h, int precision, void* stream) {
   return PSELINV_OK;
 }
 
+int pselinv_set_schedule(pselinv_t h, int schedule) {
+  if (!h || (schedule != PSELINV_SCHED_LEVEL && schedule != PSELINV_SCHED_PER_SUPERNODE))
+    return PSELINV_ERR_ARG;
+  h->opts.schedule = schedule;
+  return PSELINV_OK;
+}
+
 int pselinv_get_selected(pselinv_t h, int layout, int64_t batch, void* out, void* stream) {
   if (!h || !out || batch < 0 || batch >= h->nbatch) return PSELINV_ERR_ARG;
   if (layout == PSELINV_LAYOUT_FACTORS ? !h->factored : !h->inverted) return PSELINV_ERR_ARG;
@@ -1761,6 +1773,7 @@ template <class RB>
 static int model_tune(pselinv_ctx* h, Plan& P0, int precision, pselinv_model_t model, RB rebuild) {
   if (!model) return PSELINV_ERR_ARG;
   static const int gemm_cands[4] = {GEMM_64x64, GEMM_32x32, GEMM_128x64, GEMM_ROWS};
+  constexpr double kTuneFp64MaxFlops = 2e10;
   static const int ks_cands[5] = {1, 2, 4, 8, 16};
   std::vector<std::tuple<int, int, int>> keys;
   std::vector<pselinv_tune_record> q;
@@ -1822,6 +1835,7 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
   if (mode != PSELINV_TUNE_EXHAUSTIVE) return PSELINV_ERR_ARG;
 
   static const int gemm_cands[4] = {GEMM_64x64, GEMM_32x32, GEMM_128x64, GEMM_ROWS};
+  constexpr double kTuneFp64MaxFlops = 2e10;
   static const int ks_cands[5] = {1, 2, 4, 8, 16};
   struct Key {
     int level, slot, kind;
@@ -1897,9 +1911,18 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
       rc = measure(0);
       if (rc != PSELINV_OK) return rc;
     }
-    // phase B: every level FP64, tile shapes and row panels
+    // phase B: FP64 levels, tile shapes and row panels.  Only levels whose
+    // products are small enough that FP64 could win are run in FP64 (a level
+    // of kTuneFp64MaxFlops takes about 20 ms in FP64 and 1 ms split); the
+    // others stay split at the default K split and keep that mode.
     for (int v = 0; v < 4; v++) {
       for (int l = 0; l < nlev; l++) {
+        if (level_product_flops(h, l) > kTuneFp64MaxFlops) {
+          h->tuned.erase(std::make_tuple(precision, l, 1));
+          h->tuned.erase(std::make_tuple(precision, l, 2));
+          h->tuned[std::make_tuple(precision, l, 3)] = 0;
+          continue;
+        }
         h->tuned[std::make_tuple(precision, l, 3)] = 1;
         h->tuned[std::make_tuple(precision, l, 4)] = gemm_cands[v];
         h->tuned[std::make_tuple(precision, l, 5)] = gemm_cands[v];
@@ -1945,7 +1968,7 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
   if (precision == PSELINV_PREC_OZAKI_FP16)
     for (int l = 0; l < nlev; l++) {
       auto a = level_ms.find(std::make_pair(l, 0)), b = level_ms.find(std::make_pair(l, 1));
-      if (a != level_ms.end() && b != level_ms.end())
+      if (a != level_ms.end() && b != level_ms.end() && level_product_flops(h, l) <= kTuneFp64MaxFlops)
         h->tuned[std::make_tuple(precision, l, 3)] = b->second < a->second ? 1 : 0;
     }
   rc = rebuild();
@@ -1955,6 +1978,41 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
   if (rc != PSELINV_OK) return rc;
   CK(cudaStreamSynchronize(st));
   h->inverted = true;
+  return PSELINV_OK;
+}
+
+int pselinv_measure_fp64_peak(void* stream, double* tflops, double* ms) {
+  if (!tflops) return PSELINV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = fp64_peak_grid(sms);
+  double* out = nullptr;
+  CK(cudaMalloc(&out, (size_t)grid * 256 * sizeof(double)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int iters = 20000;  // about 80 ms at 1.26 TFLOP/s
+  double flops = 0;
+  float t = 0;
+  if (e == cudaSuccess) {
+    launch_fp64_peak(out, grid, iters / 10, st);  // warm-up
+    e = cudaEventRecord(e0, st);
+  }
+  if (e == cudaSuccess) {
+    flops = launch_fp64_peak(out, grid, iters, st);
+    e = cudaEventRecord(e1, st);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  CK(e);
+  if (t <= 0.0f) return PSELINV_ERR_CUDA;
+  *tflops = flops / ((double)t * 1e-3) / 1e12;
+  if (ms) *ms = t;
   return PSELINV_OK;
 }
 

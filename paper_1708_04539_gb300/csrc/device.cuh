@@ -246,6 +246,10 @@ void launch_lu_panel(int dtype, const SymDev& S, void* store, const SnTask* task
 void launch_tri_inv(int dtype, const SymDev& S, const void* store, void* out,
                     const int64_t* wofs, const SnTask* tasks, int ntasks, int max_width,
                     int small, cudaStream_t st);
+// FP64 peak loop (the FP64 roofline's denominator): grid for `sms` SMs;
+// the launch returns its flops (out: grid * 256 doubles of device scratch)
+int fp64_peak_grid(int sms);
+double launch_fp64_peak(double* out, int grid, int iters, cudaStream_t st);
 // one-time kernel attributes (dynamic shared memory of tri_inv for max_width)
 cudaError_t prepare_dense_kernels(int dtype, int max_width);
 // G_K = Ainv(R_K, R_K) gathered from `store` into out + gofs[task]

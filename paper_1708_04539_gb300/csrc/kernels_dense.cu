@@ -561,6 +561,35 @@ void launch_lu_panel(int dtype, const SymDev& S, void* store, const SnTask* task
 
 cudaError_t prepare_dense_kernels(int, int) { return cudaSuccess; }
 
+namespace {
+// FP64 pipe throughput: kPeakChains independent fused multiply-add chains
+// per thread (enough to hide the pipe's latency), `iters` rounds; the sum is
+// stored so that nothing is optimised away.
+constexpr int kPeakChains = 8;
+__global__ void __launch_bounds__(kThreads)
+fp64_peak_kernel(double* out, int iters, double a, double b) {
+  double x[kPeakChains];
+#pragma unroll
+  for (int j = 0; j < kPeakChains; j++) x[j] = threadIdx.x * 1e-3 + j;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int j = 0; j < kPeakChains; j++) x[j] = fma(x[j], a, b);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int j = 0; j < kPeakChains; j++) sum += x[j];
+  out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = sum;
+}
+}  // namespace
+
+int fp64_peak_grid(int sms) { return sms * 8; }
+
+// flops of one launch of the FP64 peak loop over `grid` CTAs
+double launch_fp64_peak(double* out, int grid, int iters, cudaStream_t st) {
+  fp64_peak_kernel<<<grid, kThreads, 0, st>>>(out, iters, 0.999999, 1e-7);
+  return 2.0 * kPeakChains * (double)iters * (double)grid * kThreads;
+}
+
 void launch_tri_inv(int dtype, const SymDev& S, const void* store, void* out,
                     const int64_t* wofs, const SnTask* tasks, int ntasks, int, int small,
                     cudaStream_t st) {

@@ -181,3 +181,23 @@ def test_library_encoding_literal_vectors():
                         feat=r.feat) for r, _ in ENCODE_CASES]
     want = np.array([c[1] for c in ENCODE_CASES], dtype=np.float32)
     assert np.array_equal(encode_records(recs), want)
+
+
+# ---------------------------------------------------------------------------
+# the oracle's level-parallel driver (CPU baseline timing) = its serial sweep
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("make", [
+    lambda: gen.conv_diff_2d(20, 311, sigma=0.1, max_sn=16),
+    lambda: gen.random_struct_sym(150, 0.03, 312, complex_values=True, permute=True),
+    lambda: gen.upwind_3d(9, 313, max_sn=32),
+])
+def test_parallel_oracle_is_bitwise_serial(make, oracle_lib):
+    p = make()
+    for relax in (0, 20):
+        sym = oracle.analyze(p, relax_pct=relax)
+        fac = oracle.lu(sym, p.colptr, p.rowind, p.values)
+        a = oracle.selinv(fac)
+        for nt in (1, 3, 8):
+            b = oracle.selinv_parallel(fac, nt)
+            assert np.array_equal(a.low, b.low) and np.array_equal(a.up, b.up)
+            assert np.array_equal(a.diag, b.diag)
