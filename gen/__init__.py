@@ -27,6 +27,8 @@ from .problems import (  # noqa: F401
     tridiagonal,
     arrow,
     dense,
+    general_random,
+    upwind_oneway_2d,
     make_config,
     CONFIG_NAMES,
 )

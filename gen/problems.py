@@ -456,6 +456,93 @@ def dense(n: int, seed: int, complex_values: bool = False, max_sn: int = 16) -> 
 
 
 # ---------------------------------------------------------------------------
+# general (not structurally symmetric) patterns with static pivoting
+# ---------------------------------------------------------------------------
+def _scramble(n, rows, cols, vals, seed, name, max_sn, dims, cperm, row_scramble):
+    """A = P^T Atilde Q^T from a pivoted matrix Atilde given in COO (new
+    indices): rperm / cperm (new -> old, in meta) recover Atilde = P A Q.
+    The rows of A are a random permutation of Atilde's when row_scramble
+    (the row permutation a static pivoting would have to find), else they
+    follow the columns (P = Q^T)."""
+    rng = _rng(seed, 11)
+    cperm = np.asarray(cperm, dtype=np.int64)
+    rperm = rng.permutation(n).astype(np.int64) if row_scramble else cperm.copy()
+    colptr, rowind, v = _to_csc(n, rperm[rows], cperm[cols], vals)
+    return Problem(name, n, colptr, rowind, v, cperm, max_sn, dims,
+                   meta={"rperm": rperm, "cperm": cperm, "general": True})
+
+
+def general_random(n: int, density: float, seed: int, complex_values: bool = False,
+                   max_sn: int = 16, triangle: str = "", row_scramble: bool = True) -> Problem:
+    """Random pattern that is NOT structurally symmetric: each off-diagonal
+    (i, j) of the pivoted matrix Atilde is present with probability
+    `density`, independently of (j, i) (triangle "upper" / "lower": only
+    that triangle).  Atilde is strictly diagonally dominant by rows and
+    columns (no-pivot LU is safe); A is Atilde with scrambled rows and
+    columns (see _scramble)."""
+    rng = _rng(seed, 12)
+    m = int(round(density * n * (n - 1)))
+    i = rng.integers(0, n, size=2 * m + 8)
+    j = rng.integers(0, n, size=2 * m + 8)
+    keep = i != j
+    if triangle == "upper":
+        keep &= i < j
+    elif triangle == "lower":
+        keep &= i > j
+    key = np.unique(i[keep] * n + j[keep])
+    key = rng.permutation(key)[:m]
+    r, c = key // n, key % n
+    vals = rng.uniform(-1.0, 1.0, size=r.size)
+    if complex_values:
+        vals = vals + 1j * rng.uniform(-1.0, 1.0, size=r.size)
+    a = np.abs(vals)
+    diag = (np.bincount(r, weights=a, minlength=n) + np.bincount(c, weights=a, minlength=n)
+            + 1.0 + rng.uniform(0.0, 1.0, size=n))
+    if complex_values:
+        diag = diag + 1j * rng.uniform(-0.5, 0.5, size=n)
+    idx = np.arange(n, dtype=np.int64)
+    return _scramble(n, np.concatenate([idx, r]), np.concatenate([idx, c]),
+                     np.concatenate([diag, vals]), seed, f"general_{n}_{density}{triangle}",
+                     max_sn, (n,), rng.permutation(n), row_scramble)
+
+
+def upwind_oneway_2d(m: int, seed: int, max_sn: int = 64, complex_values: bool = False,
+                     row_scramble: bool = True) -> Problem:
+    """2D convection on an m x m grid with one-sided (upwind) couplings:
+    node i couples to its -x and -y neighbours always and to its +x / +y
+    neighbour with probability 1/2 each, so the pattern is not structurally
+    symmetric.  Values U(-1, 0) off the diagonal, a_ii = 1 + sum of the
+    absolute values of row i and column i.  Columns in the grid's nested
+    dissection order; rows scrambled (static pivoting restores them)."""
+    dims = (m, m)
+    idx, coords = _coords(dims)
+    n = idx.size
+    rng = _rng(seed, 13)
+    rows, cols = [], []
+    for d in range(2):
+        for sgn, prob in ((-1, 1.0), (+1, 0.5)):
+            off = [0, 0]
+            off[d] = sgn
+            mask, j = _neighbour(dims, coords, off)
+            mask &= rng.uniform(0.0, 1.0, size=n) < prob
+            rows.append(idx[mask])
+            cols.append(j[mask])
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    vals = -rng.uniform(0.0, 1.0, size=r.size)
+    if complex_values:
+        vals = vals + 1j * rng.uniform(-0.5, 0.5, size=r.size)
+    a = np.abs(vals)
+    diag = 1.0 + np.bincount(r, weights=a, minlength=n) + np.bincount(c, weights=a, minlength=n)
+    perm = nd_perm(dims, max_sn)
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[perm] = np.arange(n)
+    # Atilde in the nested-dissection order: new index iperm[old]
+    return _scramble(n, iperm[np.concatenate([idx, r])], iperm[np.concatenate([idx, c])],
+                     np.concatenate([diag.astype(vals.dtype), vals]), seed,
+                     f"upwind_oneway_2d_{m}", max_sn, dims, perm, row_scramble)
+
+
+# ---------------------------------------------------------------------------
 # the five workloads
 # ---------------------------------------------------------------------------
 def make_config(k: int, size: int | None = None, instances: int | None = None):

@@ -36,8 +36,9 @@ class OracleError(RuntimeError):
 
 def build(force: bool = False) -> str:
     """Compile liboracle.so (plain C11, no FMA contraction)."""
-    src = [os.path.join(_HERE, "oracle.c")]
-    deps = src + [os.path.join(_HERE, "oracle.h"), os.path.join(_HERE, "oracle_num.inc")]
+    src = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "oracle_general.c")]
+    deps = src + [os.path.join(_HERE, "oracle.h"), os.path.join(_HERE, "oracle_num.inc"),
+                  os.path.join(_HERE, "oracle_gnum.inc")]
     if not force and os.path.exists(_LIB_PATH):
         t = os.path.getmtime(_LIB_PATH)
         if all(os.path.getmtime(d) <= t for d in deps):
@@ -268,3 +269,163 @@ def selected_inverse(problem, b: int = 0, mutation: int = 0, relax_pct: int | No
     vals = problem.values if problem.values.ndim == 1 else problem.values[b]
     fac = lu(sym, problem.colptr, problem.rowind, vals)
     return selinv(fac, mutation=mutation)
+
+
+# ---------------------------------------------------------------------------
+# general patterns and static pivoting (oracle_general.c)
+# ---------------------------------------------------------------------------
+def _gload():
+    lib = _load()
+    if getattr(lib, "_general_bound", False):
+        return lib
+    P = ctypes.c_void_p
+    I = ctypes.c_int64
+    lib.oracle_ganalyze.argtypes = [I, P, P, P, P, ctypes.POINTER(P)]
+    lib.oracle_ganalyze.restype = ctypes.c_int
+    lib.oracle_gsym_free.argtypes = [P]
+    lib.oracle_gsym_free.restype = None
+    for name in ("oracle_gsym_n", "oracle_gsym_nnzl", "oracle_gsym_nnzu"):
+        getattr(lib, name).argtypes = [P]
+        getattr(lib, name).restype = I
+    for name in ("oracle_gsym_lptr", "oracle_gsym_lidx", "oracle_gsym_uptr", "oracle_gsym_uidx"):
+        getattr(lib, name).argtypes = [P]
+        getattr(lib, name).restype = ctypes.POINTER(I)
+    for t in ("d", "z"):
+        f = getattr(lib, f"oracle_glu_{t}")
+        f.argtypes = [P, P, P, P, P, P, P, ctypes.POINTER(I)]
+        f.restype = ctypes.c_int
+        f = getattr(lib, f"oracle_gselinv_{t}")
+        f.argtypes = [P, P, P, P, P, P, P, ctypes.c_int]
+        f.restype = ctypes.c_int
+        f = getattr(lib, f"oracle_gextract_{t}")
+        f.argtypes = [P, P, P, P, P, P, P]
+        f.restype = ctypes.c_int
+    lib._general_bound = True
+    return lib
+
+
+class GSymbolic:
+    """Structures C_L(k) (columns of L) and C_U(k) (rows of U) of
+    Atilde = P A Q, permuted indices (oracle_ganalyze)."""
+
+    def __init__(self, n, colptr, rowind, rperm=None, cperm=None):
+        lib = _gload()
+        self._colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+        self._rowind = np.ascontiguousarray(rowind, dtype=np.int64)
+        rp = None if rperm is None else np.ascontiguousarray(rperm, dtype=np.int64)
+        cp = None if cperm is None else np.ascontiguousarray(cperm, dtype=np.int64)
+        h = ctypes.c_void_p()
+        rc = lib.oracle_ganalyze(int(n), _ptr(self._colptr), _ptr(self._rowind),
+                                 None if rp is None else _ptr(rp),
+                                 None if cp is None else _ptr(cp), ctypes.byref(h))
+        if rc != 0:
+            raise OracleError(rc, "ganalyze")
+        self._h = h
+        self.n = int(lib.oracle_gsym_n(h))
+        self.nnzl = int(lib.oracle_gsym_nnzl(h))
+        self.nnzu = int(lib.oracle_gsym_nnzu(h))
+        self.lptr = _arr(lib.oracle_gsym_lptr(h), self.n + 1)
+        self.lidx = _arr(lib.oracle_gsym_lidx(h), self.nnzl)
+        self.uptr = _arr(lib.oracle_gsym_uptr(h), self.n + 1)
+        self.uidx = _arr(lib.oracle_gsym_uidx(h), self.nnzu)
+        self.rperm = np.arange(self.n) if rp is None else rp.copy()
+        self.cperm = np.arange(self.n) if cp is None else cp.copy()
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.oracle_gsym_free(h)
+            self._h = None
+
+    def col_l(self, k):
+        return self.lidx[self.lptr[k]:self.lptr[k + 1]]
+
+    def row_u(self, k):
+        return self.uidx[self.uptr[k]:self.uptr[k + 1]]
+
+    def inverse_pattern(self):
+        """(rows, cols) of the computed entries B_{i,j} of Atilde^{-1} (the
+        pattern of (L+U)^T) in the order diag, BL, BU."""
+        kl = np.repeat(np.arange(self.n), np.diff(self.lptr))
+        ku = np.repeat(np.arange(self.n), np.diff(self.uptr))
+        rows = np.concatenate([np.arange(self.n), kl, self.uidx])
+        cols = np.concatenate([np.arange(self.n), self.lidx, ku])
+        return rows, cols
+
+
+def ganalyze(problem) -> GSymbolic:
+    """General analysis of a Problem with optional ``rperm``/``cperm`` in its
+    meta (default: its symmetric ``perm`` for both)."""
+    rp = problem.meta.get("rperm", problem.perm)
+    cp = problem.meta.get("cperm", problem.perm)
+    return GSymbolic(problem.n, problem.colptr, problem.rowind, rp, cp)
+
+
+class GFactors:
+    def __init__(self, sym, low, up, diag):
+        self.sym, self.low, self.up, self.diag = sym, low, up, diag
+
+
+class GSelected:
+    def __init__(self, sym, bl, bu, bd):
+        self.sym, self.bl, self.bu, self.bd = sym, bl, bu, bd
+
+    def values(self):
+        """Values in the order of GSymbolic.inverse_pattern()."""
+        return np.concatenate([self.bd, self.bl, self.bu])
+
+
+def glu(sym: GSymbolic, colptr, rowind, values) -> GFactors:
+    lib = _gload()
+    values = np.ascontiguousarray(values)
+    cplx = np.iscomplexobj(values)
+    dt = np.complex128 if cplx else np.float64
+    values = values.astype(dt, copy=False)
+    low = np.zeros(sym.nnzl, dtype=dt)
+    up = np.zeros(sym.nnzu, dtype=dt)
+    diag = np.zeros(sym.n, dtype=dt)
+    bad = ctypes.c_int64(-1)
+    colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+    rowind = np.ascontiguousarray(rowind, dtype=np.int64)
+    f = lib.oracle_glu_z if cplx else lib.oracle_glu_d
+    rc = f(sym._h, _ptr(colptr), _ptr(rowind), _ptr(values), _ptr(low), _ptr(up), _ptr(diag),
+           ctypes.byref(bad))
+    if rc != 0:
+        raise OracleError(rc, f"glu (column {bad.value})")
+    return GFactors(sym, low, up, diag)
+
+
+def gselinv(fac: GFactors, mutation: int = 0) -> GSelected:
+    lib = _gload()
+    sym = fac.sym
+    dt = fac.diag.dtype
+    bl = np.zeros(sym.nnzl, dtype=dt)
+    bu = np.zeros(sym.nnzu, dtype=dt)
+    bd = np.zeros(sym.n, dtype=dt)
+    f = lib.oracle_gselinv_z if np.iscomplexobj(fac.diag) else lib.oracle_gselinv_d
+    rc = f(sym._h, _ptr(fac.low), _ptr(fac.up), _ptr(fac.diag), _ptr(bl), _ptr(bu), _ptr(bd),
+           int(mutation))
+    if rc != 0:
+        raise OracleError(rc, "gselinv")
+    return GSelected(sym, bl, bu, bd)
+
+
+def gextract(sel: GSelected, colptr, rowind) -> np.ndarray:
+    """out[p] = (A^{-1})_{x,y} for entry p of A at row y = rowind[p], column x."""
+    lib = _gload()
+    colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+    rowind = np.ascontiguousarray(rowind, dtype=np.int64)
+    out = np.zeros(rowind.size, dtype=sel.bd.dtype)
+    f = lib.oracle_gextract_z if np.iscomplexobj(sel.bd) else lib.oracle_gextract_d
+    rc = f(sel.sym._h, _ptr(colptr), _ptr(rowind), _ptr(sel.bl), _ptr(sel.bu), _ptr(sel.bd),
+           _ptr(out))
+    if rc != 0:
+        raise OracleError(rc, "gextract")
+    return out
+
+
+def general_selected_inverse(problem, b: int = 0, mutation: int = 0) -> GSelected:
+    """ganalyze + glu + gselinv for instance b of a Problem."""
+    sym = ganalyze(problem)
+    vals = problem.values if problem.values.ndim == 1 else problem.values[b]
+    return gselinv(glu(sym, problem.colptr, problem.rowind, vals), mutation=mutation)

@@ -103,6 +103,43 @@ int oracle_selinv_par_d(const oracle_sym* s, const double* Llow, const double* U
 int oracle_selinv_par_z(const oracle_sym* s, const void* Llow, const void* Uup,
                         const void* Udiag, void* Blow, void* Bup, void* Bdiag, int nthreads);
 
+/* ---------------------------------------------------------------------
+ * General patterns and static pivoting (oracle_general.c): Atilde = P A Q
+ * with rperm (new -> old rows) and cperm (new -> old columns), NULL =
+ * identity; C_L(k) and C_U(k) need not agree.  Factors and inverse are
+ * stored column k of L (rows lidx[lptr[k]..lptr[k+1]) = C_L(k)) and row k
+ * of U (columns uidx[uptr[k]..uptr[k+1]) = C_U(k)):
+ *   L[p] = L_{lidx[p],k}, U[p] = U_{k,uidx[p]}, D[k] = U_{k,k};
+ *   BL[p] = (Atilde^{-1})_{k,lidx[p]}, BU[p] = (Atilde^{-1})_{uidx[p],k},
+ *   BD[k] = (Atilde^{-1})_{k,k}   (the pattern of (L+U)^T).
+ * gextract: out[p] = (A^{-1})_{x,y} for entry p of A at row y, column x
+ * (Eq. sel_entries, Theorem 2).  gselinv mutations 1-4 plant mistakes
+ * (see oracle_gnum.inc).
+ * --------------------------------------------------------------------- */
+typedef struct oracle_gsym oracle_gsym;
+int oracle_ganalyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
+                    const int64_t* rperm, const int64_t* cperm, oracle_gsym** out);
+void oracle_gsym_free(oracle_gsym* s);
+int64_t oracle_gsym_n(const oracle_gsym* s);
+int64_t oracle_gsym_nnzl(const oracle_gsym* s);
+int64_t oracle_gsym_nnzu(const oracle_gsym* s);
+const int64_t* oracle_gsym_lptr(const oracle_gsym* s);
+const int64_t* oracle_gsym_lidx(const oracle_gsym* s);
+const int64_t* oracle_gsym_uptr(const oracle_gsym* s);
+const int64_t* oracle_gsym_uidx(const oracle_gsym* s);
+int oracle_glu_d(const oracle_gsym* s, const int64_t* colptr, const int64_t* rowind,
+                 const double* values, double* L, double* U, double* D, int64_t* bad_col);
+int oracle_glu_z(const oracle_gsym* s, const int64_t* colptr, const int64_t* rowind,
+                 const void* values, void* L, void* U, void* D, int64_t* bad_col);
+int oracle_gselinv_d(const oracle_gsym* s, const double* L, const double* U, const double* D,
+                     double* BL, double* BU, double* BD, int mutation);
+int oracle_gselinv_z(const oracle_gsym* s, const void* L, const void* U, const void* D,
+                     void* BL, void* BU, void* BD, int mutation);
+int oracle_gextract_d(const oracle_gsym* s, const int64_t* colptr, const int64_t* rowind,
+                      const double* BL, const double* BU, const double* BD, double* out);
+int oracle_gextract_z(const oracle_gsym* s, const int64_t* colptr, const int64_t* rowind,
+                      const void* BL, const void* BU, const void* BD, void* out);
+
 /* Selected entries in the ORIGINAL ordering on the pattern of A (Theorem 2):
  * out[p] = (A^{-1})_{rowind[p], j} for p in column j. */
 int oracle_extract_d(const oracle_sym* s, const int64_t* colptr, const int64_t* rowind,
