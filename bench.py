@@ -563,6 +563,36 @@ def traffic_from_profiles(kernel):
     return ent["bytes_per_launch"] if sha == ent.get("source_sha") else None
 
 
+def group_problem(fam, grids):
+    """The pole-expansion batch as one direct sum: each shift of `fam` and
+    each grid a member, in member order (the pattern the library's
+    pselinv_group forms; the values concatenated the same way)."""
+    import gen
+    patterns = [fam] + list(grids)
+    member_of = [0] * fam.nbatch + list(range(1, len(grids) + 1))
+    cps, ris, vals = [np.zeros(1, dtype=np.int64)], [], []
+    n = nnz = 0
+    for k, i in enumerate(member_of):
+        q = patterns[i]
+        cps.append(q.colptr[1:] + nnz)
+        ris.append(q.rowind + n)
+        vals.append(fam.values[k] if i == 0 else q.values)
+        n += q.n
+        nnz += q.nnz
+    return gen.Problem("pole_batch", n, np.concatenate(cps), np.concatenate(ris),
+                       np.concatenate([np.asarray(v, dtype=np.complex128) for v in vals]),
+                       np.arange(n, dtype=np.int64), fam.max_supernode,
+                       meta={"members": patterns, "member_of": member_of, "family_n": fam.n})
+
+
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress of the run on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def workload_name(config, size, n):
     return WORKLOADS[config].format(m=size, n=n)
 
@@ -628,19 +658,35 @@ def run_ours(args):
 
     config = args.config
     p = gen.make_config(config, size=args.size)
+    nmat = 1
     if config == 4:
-        p = p[0]  # the shift family (the uneven grids are a parity case)
+        # the pole-expansion batch: every shift of the 3D operator and every
+        # uneven 2D grid is a member of one group (pselinv_group), so one
+        # sweep with one launch per kernel kind and level covers all of them
+        fam, grids = p[0], p[1:]
+        p = group_problem(fam, grids)
+        nmat = fam.nbatch + len(grids)
     size = args.size or DEFAULT_SIZE[config]
-    workload = workload_name(config, size, p.n)
+    workload = workload_name(config, size, p.n if config != 4 else p.meta["family_n"])
     big = config == 5 and size >= 14
     headline = config in (2, 5)
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else (1 if big else 5)
     cplx = np.iscomplexobj(p.values)
     nbatch = p.nbatch
     sched = ps.SCHED_PER_SUPERNODE if args.schedule == "per_supernode" else ps.SCHED_LEVEL
-    h = ps.SelInv.from_problem(p, relax_pct=20, schedule=sched, use_graph=not args.no_graph,
-                               split_normalise=args.split_normalise)
+    log(f"workload generated: n={p.n} nnz={p.nnz}")
+    hkw = dict(relax_pct=20, schedule=sched, use_graph=not args.no_graph,
+               split_normalise=args.split_normalise)
+    if config == 4:
+        members = [ps.SelInv.from_problem(q, host_only=True, relax_pct=20)
+                   for q in p.meta["members"]]
+        h = ps.SelInv.group([members[i] for i in p.meta["member_of"]], max_supernode=256, **hkw)
+        for m in members:
+            m.close()
+    else:
+        h = ps.SelInv.from_problem(p, **hkw)
     st = h.structure()
+    log(f"analysed: {int(st['nsuper'])} supernodes, {int(st['nlevels'])} levels")
     # FP64-equivalent flops of one sweep over every instance (x4 for complex)
     flops = float(st["flops_selinv_exact"]) * (4.0 if cplx else 1.0) * nbatch
     stream = torch.cuda.Stream()
@@ -663,6 +709,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         factor_ms = e0.elapsed_time(e1)
     fp64_peak, _ = measure_fp64_peak(stream)
+    log(f"factorised; FP64 peak {fp64_peak:.3f} TFLOP/s")
 
     prec = ps.PREC_OZAKI_FP16 if args.precision == "ozaki" else ps.PREC_FP64
     learned = (not args.no_learned and rank == 0 and world == 1 and headline and
@@ -670,6 +717,7 @@ def run_ours(args):
     model = model_info = None
     if learned:
         model, model_info = train_cost_model(config, prec, stream)
+        log(f"cost model trained on {model_info['records']} records")
     tune_s = 0.0
     tuning = args.tune
     if args.plan_in:
@@ -683,6 +731,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         tune_s = time.perf_counter() - t0
     triples = h.plan_get(prec)
+    log(f"tuned in {tune_s:.1f} s")
     if args.plan_out:
         with open(args.plan_out, "w") as f:
             json.dump({"precision": args.precision, "config": config, "size": size,
@@ -715,6 +764,7 @@ def run_ours(args):
     h.sync(stream=stream)
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     value, ms_per_step = aggregate_throughput(flops, elapsed_ms, args.steps, world)
+    log(f"timed: {ms_per_step:.3f} ms per step, {value:.1f} GFLOP/s")
 
     # launch-by-launch replay with CUDA events on the same stream
     prof = [] if args.no_profile else h.profile(0, stream=stream)
@@ -737,6 +787,7 @@ def run_ours(args):
         learned_rec = learned_vs_exhaustive(h, prec, stream, out_dev[0], model, model_info,
                                             ms_per_step, triples)
         model.close()
+        log("learned vs exhaustive done")
 
     # end to end through the C ABI with host buffers: H2D values, factor,
     # selected inversion, D2H of the selected entries
@@ -775,6 +826,7 @@ def run_ours(args):
                "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
                "includes": "H2D values, factor, selinv, extract, D2H"}
         del vals_host, out_host
+        log(f"end to end {e2e_s * 1e3:.1f} ms")
 
     stats = h.plan_stats()
     nl = stats["launches_selinv"]
@@ -785,7 +837,7 @@ def run_ours(args):
         "dtype": ("c128" if cplx else "f64") + ("" if args.precision == "fp64" else "+f16-slices"),
         "data": "synthetic (seeded generator, nested dissection)",
         "precision": args.precision,
-        "config": {"workload": workload, "n": p.n, "nnz": p.nnz, "instances": nbatch,
+        "config": {"workload": workload, "n": p.n, "nnz": p.nnz, "instances": nbatch * nmat,
                    "supernodes": int(st["nsuper"]), "levels": int(st["nlevels"]),
                    "flops_per_matrix": flops / nbatch,
                    "flops_relaxed_structure": st["flops_selinv"] * (4.0 if cplx else 1.0),
@@ -795,7 +847,8 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.0f MB of factors read per step)"
                          % (st["storage_size"] * (16 if cplx else 8) * nbatch / 1e6)},
-        "time_per_matrix_ms": ms_per_step / nbatch,
+        "time_per_matrix_ms": ms_per_step / (nbatch * nmat),
+        "matrices_per_step": nbatch * nmat,
         "factor_ms": factor_ms,
         "e2e": e2e,
         "gpu_launches": int((nl + nbatch) * args.steps),
@@ -812,6 +865,7 @@ def run_ours(args):
         line["learned"] = learned_rec
     if not args.no_compare and args.precision == "ozaki" and rank == 0 and headline:
         line["comparison"] = comparison(p, h, stream, out_dev[0], flops, big)
+        log("comparison done")
     h.close()
     if rank == 0 and world == 1 and not args.skip_cpu_baseline and headline:
         line["cpu_baseline"] = cpu_baseline(p, SAMPLE_TARGET_N[config])

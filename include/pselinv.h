@@ -135,6 +135,23 @@ typedef struct pselinv_structure {
   double flops_selinv;         /* sum_K 4 c^2 s + 4 c s^2 + 4/3 s^3 on this structure (real) */
   double flops_selinv_exact;   /* the same sum on the strict (relax 0) supernodes */
   double flops_factor;         /* sum_K 2 c^2 s + 2 c s^2 + 2/3 s^3 (real) */
+  /* General patterns (handles of pselinv_analyze_general; for the others
+   * general = 0, rperm = perm, urows = rows and out_map = value_map):
+   * rows_ptr / rows hold R_L(K) (= C_L, the L panel's c_L rows) and
+   * urows_ptr / urows R_U(K) (= C_U, the columns of U right of K, the c_U
+   * rows of the U^T panel, which follows the L panel: at sn_offset[K] +
+   * s*s + c_L*s).  After pselinv_selinv the diagonal block holds Ainv_KK,
+   * the L panel (Ainv_{K,R_L})^T and the U^T panel Ainv_{R_U,K} (the
+   * pattern of (L+U)^T, the paper's A^{-T} in place).  The c of the flop
+   * counts is then sum_K 4 c_L c_U s + 2 (c_L + c_U) s^2 + 4/3 s^3; the
+   * exact count is taken over the scalar structures.  etree[j] = first row
+   * of C_L(j) (the tree of the L structures). */
+  int64_t general;
+  const int64_t* rperm;        /* [n] row ordering new -> old (general) */
+  const int64_t* urows_ptr;    /* [nsuper + 1] */
+  const int64_t* urows;        /* [urows_ptr[nsuper]] */
+  const int64_t* out_map;      /* [nnz_a] storage slot of the selected entry returned for each
+                                  input entry by PSELINV_LAYOUT_PATTERN_A */
 } pselinv_structure;
 
 /* Fill *opts with the defaults. */
@@ -152,6 +169,31 @@ void pselinv_default_opts(pselinv_opts* opts);
 int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
                     const int64_t* perm, const pselinv_opts* opts, pselinv_t* out);
 
+/* Symbolic analysis of a GENERAL pattern with static pivoting (Section 1:
+ * non-symmetric matrices, Eq. sel_entries; Section 2: C_L != C_U in
+ * Theorem 1 and Algorithm 1; Theorem 2 with P != Q^T).  Atilde = P A Q with
+ * Atilde(i, k) = A(rperm[i], cperm[k]); rperm, cperm: host int64 new -> old
+ * (NULL = identity), typically a fill-reducing column ordering and a row
+ * permutation that puts large entries on the diagonal (static pivoting; the
+ * library computes neither).  The pattern need not be structurally
+ * symmetric; the diagonal of Atilde counts as present.  The LU factors of
+ * Atilde are formed without pivoting on the structures C_L(k), C_U(k) of
+ * the fill rule (eliminating k fills C_L(k) x C_U(k)), supernodes join
+ * columns whose diagonal block is connected (relax_pct as for
+ * pselinv_analyze), and the two supernodal row structures R_L(K), R_U(K)
+ * are closed under the supernodal updates.  The depth levels of the sweep
+ * follow the dependencies of Theorem 1 (K after every supernode of R_L(K)
+ * and R_U(K)).  Results: pselinv_get_selected(PATTERN_A) returns, for
+ * entry p of A at row y = rowind[p] of column x, the selected entry
+ * (A^{-1})_{x,y} (Eq. sel_entries: the transposed position), and
+ * pselinv_trace / pselinv_weighted_sum use the same entries.  Only
+ * PSELINV_PREC_FP64 is available for these handles (PSELINV_ERR_UNSUPPORTED
+ * otherwise); opts->symmetric must be 0.  Other errors as pselinv_analyze
+ * (PSELINV_ERR_ARG for an invalid ordering or pattern). */
+int pselinv_analyze_general(int64_t n, const int64_t* colptr, const int64_t* rowind,
+                            const int64_t* rperm, const int64_t* cperm, const pselinv_opts* opts,
+                            pselinv_t* out);
+
 /* Fill-reducing ordering for pselinv_analyze (host only; not from the
  * paper, which orders with graph partitioners): automatic nested dissection
  * of the graph of A after George and Liu (1981), separators from the level
@@ -165,6 +207,27 @@ int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
 int pselinv_order_nd(int64_t n, const int64_t* colptr, const int64_t* rowind, int64_t leaf,
                      int64_t* perm_out);
 
+/* One handle for several independent matrices of DIFFERENT patterns
+ * (instances of uneven size; not from the paper, whose method takes one
+ * matrix: the batching of Algorithm 1 over many matrices).  The group's
+ * matrix is the direct sum A_1 (+) A_2 (+) ... (+) A_count of the members'
+ * patterns in member order: member m's rows and columns are shifted by the
+ * sizes of the members before it, and so is its ordering (the structure's
+ * perm), so the group's elimination forest is the union of the members'
+ * trees and every depth level of the sweep holds the supernodes of every
+ * member (one launch per kernel kind and level for all of them).  The
+ * selected inverse of a block-diagonal matrix is block diagonal, so each
+ * member's result is its slice of the group's.
+ *   members[count]: analysed handles (host_only ones too); they are only
+ *     read, stay valid and are freed by the caller as usual.
+ *   opts: NULL = the first member's options (with host_only off).
+ * pselinv_factor of the group takes the members' CSC values concatenated in
+ * member order (member m's entries at the sum of the earlier members' nnz);
+ * pselinv_get_selected(PATTERN_A) returns the same concatenation, whose
+ * slice m is (A_m^{-1}) on member m's pattern.  Errors as pselinv_analyze. */
+int pselinv_group(const pselinv_t* members, int64_t count, const pselinv_opts* opts,
+                  pselinv_t* out);
+
 /* Supernodal LU without pivoting of nbatch instances sharing the pattern
  * (Eq. LU, Section 3's prerequisite).  values: nbatch * nnz scalars of dtype,
  * instance b at values + b*nnz, in the CSC order given to pselinv_analyze;
@@ -176,6 +239,36 @@ int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, v
  * precision = pselinv_precision or -1 for the handle's option.  Asynchronous
  * on `stream`. */
 int pselinv_selinv(pselinv_t h, int precision, void* stream);
+
+/* Partitioned sweep over several GPUs (not from the paper, whose parallel
+ * design distributes every supernode's blocks over a process grid; here
+ * whole subtrees go to a rank).  The subtrees below the top of the
+ * supernodal tree are independent once the selected inverse of the top is
+ * known: a supernode K below a subtree root r reads Ainv only inside the
+ * subtree and at R_r x R_r (R_K minus the subtree lies in R_r), so the top
+ * is computed once and each subtree root's G_r = Ainv(R_r, R_r) is sent to
+ * the rank that owns it, in one exchange step.
+ *   partition: owner[nsuper] (host, caller-owned) = the rank of every
+ *     supernode, -1 for the top.  The heaviest subtree (by the flops of its
+ *     supernodes) is split into its children until there are about eight
+ *     subtrees per rank, then subtrees go to ranks heaviest first, each to
+ *     the least loaded rank.  nranks = 1: no top.
+ *   set_subset: later pselinv_selinv / pselinv_tune calls cover only the
+ *     supernodes with owner[K] == rank (owner NULL: all again); plans are
+ *     rebuilt.  Host only.
+ *   export_block: buf (device, c_K x c_K column-major, caller-owned) =
+ *     G_K = Ainv(R_K, R_K) of instance `batch`, gathered from the handle's
+ *     selected inverse; import_block writes such a block into the handle's
+ *     storage (the blocks of R_K's supernodes), as a rank does with the
+ *     G_r it receives before sweeping its subtrees.  Both synchronise
+ *     `stream`.
+ * Structurally symmetric handles only (PSELINV_ERR_UNSUPPORTED for general
+ * patterns, whose dependencies are not a tree); PSELINV_ERR_ARG for bad
+ * arguments or a host `buf`. */
+int pselinv_partition(pselinv_t h, int32_t nranks, int32_t* owner);
+int pselinv_set_subset(pselinv_t h, const int32_t* owner, int32_t rank);
+int pselinv_export_block(pselinv_t h, int64_t K, int64_t batch, void* buf, void* stream);
+int pselinv_import_block(pselinv_t h, int64_t K, int64_t batch, const void* buf, void* stream);
 
 /* Schedule of later pselinv_selinv / pselinv_tune calls (the handle's
  * opts.schedule): PSELINV_SCHED_LEVEL (one batched launch per kind and
@@ -219,7 +312,10 @@ enum pselinv_step_kind {
   PSELINV_STEP_GATHER = 3, PSELINV_STEP_SCATTER_SUB = 4, PSELINV_STEP_COPY = 5,
   PSELINV_STEP_MEMSET = 6, PSELINV_STEP_SCATTER_VALUES = 7, PSELINV_STEP_SLICE = 8,
   PSELINV_STEP_OZAKI_GEMM = 9, PSELINV_STEP_RECOMBINE = 10,
-  PSELINV_STEP_SMALL_LEVEL = 11  /* steps 3-5 of a level of narrow supernodes, one launch */
+  PSELINV_STEP_SMALL_LEVEL = 11, /* steps 3-5 of a level of narrow supernodes, one launch */
+  PSELINV_STEP_GATHER_SLICE = 12 /* split levels: Ainv_CC gathered and sliced in one pass
+                                    (maxima, or slices in both layouts), with the panels'
+                                    slicing; Ainv_CC is never stored in FP64 */
 };
 
 /* Run the selected-inversion plan (which = 0) or the factorisation plan

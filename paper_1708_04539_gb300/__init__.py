@@ -7,6 +7,7 @@ every entry point raises ``LibraryMissing``.
 """
 from .binding import (  # noqa: F401
     supernodal_coordinates,
+    inverse_coordinates,
     order_nd,
     LibraryMissing,
     PselinvError,

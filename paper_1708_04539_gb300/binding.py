@@ -30,7 +30,8 @@ _EXPORTS = [
     "pselinv_sync", "pselinv_last_info", "pselinv_error_string", "pselinv_free",
     "pselinv_block_inverse_noalloc", "pselinv_tune", "pselinv_tune_records",
     "pselinv_plan_get", "pselinv_plan_set", "pselinv_wait_selftest", "pselinv_measure_fp64_peak",
-    "pselinv_set_schedule",
+    "pselinv_set_schedule", "pselinv_group", "pselinv_analyze_general",
+    "pselinv_partition", "pselinv_set_subset", "pselinv_export_block", "pselinv_import_block",
     "pselinv_weighted_sum", "pselinv_trace",
     "pselinv_model_create", "pselinv_model_train", "pselinv_model_gradients",
     "pselinv_model_predict", "pselinv_model_get_params", "pselinv_model_set_params",
@@ -41,7 +42,7 @@ TUNE_RESET, TUNE_EXHAUSTIVE, TUNE_MODEL = 0, 1, 2
 
 STEP_KINDS = {0: "gemm", 1: "tri_inv", 2: "diag_lu", 3: "gather", 4: "scatter_sub", 5: "copy",
               6: "memset", 7: "scatter_values", 8: "slice", 9: "ozaki_gemm", 10: "recombine",
-              11: "small_level"}
+              11: "small_level", 12: "gather_slice"}
 
 
 class LibraryMissing(RuntimeError):
@@ -90,7 +91,9 @@ class Structure(ctypes.Structure):
                 ("sn_parent", _P64), ("sn_depth", _P64), ("sn_offset", _P64),
                 ("rows_ptr", _P64), ("rows", _P64), ("level_ptr", _P64), ("level_sn", _P64),
                 ("value_map", _P64), ("flops_selinv", ctypes.c_double),
-                ("flops_selinv_exact", ctypes.c_double), ("flops_factor", ctypes.c_double)]
+                ("flops_selinv_exact", ctypes.c_double), ("flops_factor", ctypes.c_double),
+                ("general", ctypes.c_int64), ("rperm", _P64), ("urows_ptr", _P64),
+                ("urows", _P64), ("out_map", _P64)]
 
 
 _lib = None
@@ -149,6 +152,19 @@ def load_library():
     lib.pselinv_measure_fp64_peak.argtypes = [P, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double)]
     lib.pselinv_measure_fp64_peak.restype = ctypes.c_int
+    lib.pselinv_analyze_general.argtypes = [I64, P, P, P, P, ctypes.POINTER(Opts),
+                                            ctypes.POINTER(P)]
+    lib.pselinv_analyze_general.restype = ctypes.c_int
+    lib.pselinv_group.argtypes = [P, I64, ctypes.POINTER(Opts), ctypes.POINTER(P)]
+    lib.pselinv_group.restype = ctypes.c_int
+    lib.pselinv_partition.argtypes = [P, ctypes.c_int32, P]
+    lib.pselinv_partition.restype = ctypes.c_int
+    lib.pselinv_set_subset.argtypes = [P, P, ctypes.c_int32]
+    lib.pselinv_set_subset.restype = ctypes.c_int
+    lib.pselinv_export_block.argtypes = [P, I64, I64, P, P]
+    lib.pselinv_export_block.restype = ctypes.c_int
+    lib.pselinv_import_block.argtypes = [P, I64, I64, P, P]
+    lib.pselinv_import_block.restype = ctypes.c_int
     lib.pselinv_set_schedule.argtypes = [P, ctypes.c_int]
     lib.pselinv_set_schedule.restype = ctypes.c_int
     RP = ctypes.POINTER(TuneRecord)
@@ -229,11 +245,10 @@ def _is_complex(x) -> bool:
 class SelInv:
     """One analysed pattern (a handle of the C library)."""
 
-    def __init__(self, n, colptr, rowind, perm=None, max_supernode=256, relax_pct=20,
-                 schedule=SCHED_LEVEL, use_graph=True, check_level=0, precision=PREC_FP64,
-                 slices=0, host_only=False, split_normalise=False, symmetric=False, nd_leaf=0):
-        lib = load_library()
-        self._lib = lib
+    @staticmethod
+    def _opts(lib, max_supernode=256, relax_pct=20, schedule=SCHED_LEVEL, use_graph=True,
+              check_level=0, precision=PREC_FP64, slices=0, host_only=False,
+              split_normalise=False, symmetric=False, nd_leaf=0):
         opts = Opts()
         lib.pselinv_default_opts(ctypes.byref(opts))
         opts.max_supernode = int(max_supernode)
@@ -247,6 +262,12 @@ class SelInv:
         opts.split_normalise = 1 if split_normalise else 0
         opts.symmetric = 1 if symmetric else 0
         opts.nd_leaf = int(nd_leaf)  # perm None: 0 natural order, > 0 nested dissection
+        return opts
+
+    def __init__(self, n, colptr, rowind, perm=None, **kw):
+        lib = load_library()
+        self._lib = lib
+        opts = self._opts(lib, **kw)
         self._colptr = np.ascontiguousarray(colptr, dtype=np.int64)
         self._rowind = np.ascontiguousarray(rowind, dtype=np.int64)
         p = None if perm is None else np.ascontiguousarray(perm, dtype=np.int64)
@@ -260,6 +281,64 @@ class SelInv:
         self.nnz = int(self._colptr[-1])
         self.dtype = None
         self.nbatch = 0
+
+    @classmethod
+    def general(cls, n, colptr, rowind, rperm=None, cperm=None, **kw):
+        """Handle of a general pattern with static pivoting, Atilde = P A Q
+        (pselinv_analyze_general; rperm / cperm new -> old)."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        self._lib = lib
+        opts = cls._opts(lib, **kw)
+        self._colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+        self._rowind = np.ascontiguousarray(rowind, dtype=np.int64)
+        rp = None if rperm is None else np.ascontiguousarray(rperm, dtype=np.int64)
+        cp = None if cperm is None else np.ascontiguousarray(cperm, dtype=np.int64)
+        h = ctypes.c_void_p()
+        rc = lib.pselinv_analyze_general(int(n), _ptr(self._colptr), _ptr(self._rowind), _ptr(rp),
+                                         _ptr(cp), ctypes.byref(opts), ctypes.byref(h))
+        if rc != 0:
+            raise PselinvError(rc, "pselinv_analyze_general")
+        self._h = h
+        self.n = int(n)
+        self.nnz = int(self._colptr[-1])
+        self.dtype = None
+        self.nbatch = 0
+        return self
+
+    @classmethod
+    def from_general_problem(cls, problem, **kw):
+        """General handle of a Problem whose meta carries rperm / cperm."""
+        kw.setdefault("max_supernode", problem.max_supernode)
+        return cls.general(problem.n, problem.colptr, problem.rowind,
+                           problem.meta.get("rperm", problem.perm),
+                           problem.meta.get("cperm", problem.perm), **kw)
+
+    @classmethod
+    def group(cls, members, **kw):
+        """One handle for the direct sum of the members' patterns, in member
+        order (pselinv_group); keyword options as for the constructor (none:
+        the first member's options)."""
+        lib = load_library()
+        arr = (ctypes.c_void_p * len(members))(*[m._h.value for m in members])
+        opts = cls._opts(lib, **kw) if kw else None
+        h = ctypes.c_void_p()
+        rc = lib.pselinv_group(arr, len(members), ctypes.byref(opts) if opts is not None else None,
+                               ctypes.byref(h))
+        if rc != 0:
+            raise PselinvError(rc, "pselinv_group")
+        self = cls.__new__(cls)
+        self._lib = lib
+        self._h = h
+        self._colptr = np.concatenate([[0]] + [m._colptr[1:] + off for m, off in zip(
+            members, np.cumsum([0] + [m.nnz for m in members[:-1]]))]).astype(np.int64)
+        self._rowind = np.concatenate([m._rowind + off for m, off in zip(
+            members, np.cumsum([0] + [m.n for m in members[:-1]]))]).astype(np.int64)
+        self.n = int(sum(m.n for m in members))
+        self.nnz = int(sum(m.nnz for m in members))
+        self.dtype = None
+        self.nbatch = 0
+        return self
 
     @classmethod
     def from_problem(cls, problem, **kw):
@@ -316,6 +395,30 @@ class SelInv:
         self._check(self._lib.pselinv_plan_stats(self._h, ctypes.byref(a), ctypes.byref(b)),
                     "pselinv_plan_stats")
         return {"launches_selinv": a.value, "launches_factor": b.value}
+
+    def partition(self, nranks):
+        """Rank of every supernode of a partitioned sweep (-1: the top)."""
+        ns = int(self.structure()["nsuper"])
+        owner = np.empty(max(ns, 1), dtype=np.int32)
+        self._check(self._lib.pselinv_partition(self._h, int(nranks), _ptr(owner)),
+                    "pselinv_partition")
+        return owner[:ns]
+
+    def set_subset(self, owner=None, rank=0):
+        """Later sweeps cover the supernodes with owner == rank (None: all)."""
+        o = None if owner is None else np.ascontiguousarray(owner, dtype=np.int32)
+        self._check(self._lib.pselinv_set_subset(self._h, _ptr(o), int(rank)), "pselinv_set_subset")
+
+    def export_block(self, K, buf, batch=0, stream=None):
+        """buf (CUDA tensor, c_K^2 scalars) = Ainv(R_K, R_K)."""
+        self._check(self._lib.pselinv_export_block(self._h, int(K), int(batch), _ptr(buf),
+                                                   _stream(stream)), "pselinv_export_block")
+        return buf
+
+    def import_block(self, K, buf, batch=0, stream=None):
+        """Write Ainv(R_K, R_K) from buf (CUDA tensor) into the storage."""
+        self._check(self._lib.pselinv_import_block(self._h, int(K), int(batch), _ptr(buf),
+                                                   _stream(stream)), "pselinv_import_block")
 
     def set_schedule(self, schedule):
         """Schedule of later selinv/tune calls (SCHED_LEVEL or SCHED_PER_SUPERNODE)."""
@@ -416,6 +519,11 @@ class SelInv:
             "flops_factor": s.flops_factor,
         }
         out["rows"] = arr(s.rows, int(out["rows_ptr"][-1]) if ns else 0)
+        out["general"] = bool(s.general)
+        out["rperm"] = arr(s.rperm, s.n)
+        out["urows_ptr"] = arr(s.urows_ptr, ns + 1)
+        out["urows"] = arr(s.urows, int(out["urows_ptr"][-1]) if ns else 0)
+        out["out_map"] = arr(s.out_map, s.nnz_a)
         return out
 
     def close(self):
@@ -610,24 +718,19 @@ class InstanceGroup:
     """
 
     def __init__(self, patterns, **kw):
-        """patterns: list of (n, colptr, rowind, perm or None)."""
+        """patterns: list of (n, colptr, rowind, perm or None); the grouped
+        handle is built by pselinv_group from host-only member analyses."""
         self.n = [int(p[0]) for p in patterns]
         self.nnz = [int(np.asarray(p[1])[-1]) for p in patterns]
         self.row_off = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
         self.nz_off = np.concatenate([[0], np.cumsum(self.nnz)]).astype(np.int64)
-        N = int(self.row_off[-1])
-        colptr = [np.zeros(1, dtype=np.int64)]
-        rowind, perm = [], []
-        for i, (n, cp, ri, pm) in enumerate(patterns):
-            cp = np.asarray(cp, dtype=np.int64)
-            colptr.append(cp[1:] + self.nz_off[i])
-            rowind.append(np.asarray(ri, dtype=np.int64) + self.row_off[i])
-            pm = np.arange(n, dtype=np.int64) if pm is None else np.asarray(pm, dtype=np.int64)
-            perm.append(pm + self.row_off[i])
-        self.colptr = np.concatenate(colptr)
-        self.rowind = np.concatenate(rowind)
-        self.perm = np.concatenate(perm)
-        self.handle = SelInv(N, self.colptr, self.rowind, self.perm, **kw)
+        mkw = {k: v for k, v in kw.items() if k in ("max_supernode", "relax_pct")}
+        members = [SelInv(n, cp, ri, pm, host_only=True, **mkw) for (n, cp, ri, pm) in patterns]
+        self.handle = SelInv.group(members, **kw)
+        for m in members:
+            m.close()
+        self.colptr = self.handle._colptr
+        self.rowind = self.handle._rowind
 
     def values(self, per_instance):
         """Concatenate the instances' CSC values (host arrays)."""
@@ -667,6 +770,34 @@ def measure_fp64_peak(stream=None):
 def wait_selftest(budget_us=20000, stream=None):
     """Status of the bounded-wait check (PSELINV_ERR_TIMEOUT = -6 expected)."""
     return int(load_library().pselinv_wait_selftest(_stream(stream), int(budget_us)))
+
+
+def inverse_coordinates(st: dict):
+    """(rows, cols) in permuted indices of the entry of Atilde^{-1} that every
+    slot of the supernodal storage holds after pselinv_selinv.  Structurally
+    symmetric handles: as supernodal_coordinates.  General handles (the
+    pattern of (L+U)^T): diagonal block Ainv_KK, L panel (Ainv_{K,R_L})^T,
+    U^T panel Ainv_{R_U,K}."""
+    if not st.get("general", False):
+        return supernodal_coordinates(st)
+    total = int(st["storage_size"])
+    rows = np.empty(total, dtype=np.int64)
+    cols = np.empty(total, dtype=np.int64)
+    for K in range(int(st["nsuper"])):
+        f, s = int(st["sn_first"][K]), int(st["sn_width"][K])
+        RL = st["rows"][st["rows_ptr"][K]:st["rows_ptr"][K + 1]]
+        RU = st["urows"][st["urows_ptr"][K]:st["urows_ptr"][K + 1]]
+        o = int(st["sn_offset"][K])
+        loc = np.arange(f, f + s)
+        rows[o:o + s * s] = np.tile(loc, s)
+        cols[o:o + s * s] = np.repeat(loc, s)
+        o += s * s
+        rows[o:o + RL.size * s] = np.repeat(loc, RL.size)
+        cols[o:o + RL.size * s] = np.tile(RL, s)
+        o += RL.size * s
+        rows[o:o + RU.size * s] = np.tile(RU, s)
+        cols[o:o + RU.size * s] = np.repeat(loc, RU.size)
+    return rows, cols
 
 
 def supernodal_coordinates(st: dict):

@@ -52,7 +52,8 @@ enum StepKind {
   ST_OZGEMM,
   ST_ZERO,
   ST_LU_PANEL,
-  ST_SMALL_LEVEL
+  ST_SMALL_LEVEL,
+  ST_GSLICE
 };
 
 struct Step {
@@ -60,6 +61,7 @@ struct Step {
   int cfg = 0;    // GEMM: kernel config; TRI_INV: 1 small blocks; SLICE: 1 maxima pass;
                   // OZGEMM: slices; SMALL_LEVEL: shared-memory bytes of a CTA
   int n = 0;      // tasks / segments
+  int n2 = 0;     // GSLICE: ordinary slice tasks after the n G tiles
   int grid = 0;
   size_t tasks = 0, descs = 0, offs = 0, offs2 = 0;  // byte offsets into the plan arena
   void* ptr = nullptr;                    // memset target / store
@@ -157,6 +159,13 @@ struct pselinv_ctx {
   cudaStream_t third_stream = nullptr;  // triangular inverses of the deeper levels (lowest)
   int64_t last_info = -1;
   int last_status = 0;
+  // supernodes the selected-inversion plan covers (empty = all): one
+  // rank's share of a partitioned sweep (pselinv_set_subset)
+  std::vector<char> subset;
+  // staging of pselinv_export_block / pselinv_import_block: tile tasks and
+  // their (zero) offsets
+  void* blk_buf = nullptr;
+  size_t blk_buf_bytes = 0;
 };
 
 namespace {
@@ -193,6 +202,23 @@ int upload_structure(pselinv_ctx* h) {
   upload(host, o_brel, H.blk_rel);
   upload(host, o_rel, H.relidx);
   upload(host, o_vmap, H.value_map);
+  // general patterns: the second row structure and its maps
+  size_t o_cu = 0, o_urptr = 0, o_lrows = 0, o_urows = 0, o_urblk = 0, o_q0 = 0, o_ubsn = 0,
+         o_ubrel = 0, o_ubq0 = 0, o_inv = 0;
+  if (H.general) {
+    std::vector<int64_t> sn_cu(H.ns);
+    for (int64_t k = 0; k < H.ns; k++) sn_cu[k] = H.urows_ptr[k + 1] - H.urows_ptr[k];
+    upload(host, o_cu, narrow<int32_t>(sn_cu));
+    upload(host, o_urptr, H.urows_ptr);
+    upload(host, o_lrows, narrow<int32_t>(H.rows));
+    upload(host, o_urows, narrow<int32_t>(H.urows));
+    upload(host, o_urblk, H.urows_blk);
+    upload(host, o_q0, H.blk_q0);
+    upload(host, o_ubsn, H.ublk_sn);
+    upload(host, o_ubrel, H.ublk_rel);
+    upload(host, o_ubq0, H.ublk_q0);
+    upload(host, o_inv, H.inv_map);
+  }
   CK(cudaMalloc(&h->dsym, host.size() + 256));
   CK(cudaMemcpy(h->dsym, host.data(), host.size(), cudaMemcpyHostToDevice));
   CK(cudaMalloc(&h->derr, 4 * sizeof(int)));
@@ -216,10 +242,28 @@ int upload_structure(pselinv_ctx* h) {
   S.check = h->opts.check_level > 0 ? 1 : 0;
   S.relidx_size = (int64_t)H.relidx.size();
   S.err = h->derr;
+  S.out_map = S.value_map;
+  S.general = H.general ? 1 : 0;
+  if (H.general) {
+    S.sn_cu = (const int32_t*)(b + o_cu);
+    S.urows_ptr = (const int64_t*)(b + o_urptr);
+    S.lrows = (const int32_t*)(b + o_lrows);
+    S.urows = (const int32_t*)(b + o_urows);
+    S.urows_blk = (const int32_t*)(b + o_urblk);
+    S.blk_q0 = (const int32_t*)(b + o_q0);
+    S.ublk_sn = (const int32_t*)(b + o_ubsn);
+    S.ublk_rel = (const int64_t*)(b + o_ubrel);
+    S.ublk_q0 = (const int32_t*)(b + o_ubq0);
+    S.out_map = (const int64_t*)(b + o_inv);
+  }
   return PSELINV_OK;
 }
 
 inline int64_t cK(const HostSym& H, int64_t K) { return H.rows_ptr[K + 1] - H.rows_ptr[K]; }
+// rows of K's U^T panel: |R_U(K)| for a general pattern, else c_K
+inline int64_t cU(const HostSym& H, int64_t K) {
+  return H.general ? H.urows_ptr[K + 1] - H.urows_ptr[K] : cK(H, K);
+}
 
 int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -330,12 +374,13 @@ inline size_t slice_bytes(int64_t R, int64_t Kd, int S) {
 }
 inline size_t exps_bytes(int64_t R) { return align256((size_t)R * 4); }
 
-// bytes one supernode needs during a split-precision level: G, five slice
-// sets (G by rows, G by columns, Lhat, Uhat^T, Ainv(C,K)) and their exponents
+// bytes one supernode needs during a split-precision level: five slice sets
+// (G by rows, G by columns, Lhat, Uhat^T, Ainv(C,K)) and their exponents (G
+// itself is sliced straight from the ancestors' blocks, never stored)
 size_t ozaki_sn_bytes(int64_t s, int64_t c, int S, size_t es) {
   if (c == 0) return 0;
   const size_t parts = es / 8;  // complex: real and imaginary slice halves
-  return align256((size_t)c * c * es) + 2 * (parts * slice_bytes(c, c, S) + exps_bytes(c)) +
+  return 2 * (parts * slice_bytes(c, c, S) + exps_bytes(c)) +
          3 * (parts * slice_bytes(s, c, S) + exps_bytes(s)) + (size_t)(2 * c + 3 * s) * 8 + 2048;
 }
 size_t ozaki_level_bytes(const HostSym& H, int64_t nb, int S, size_t es) {
@@ -376,8 +421,7 @@ size_t selinv_main_bytes(const HostSym& H, int64_t nb, size_t es) {
   for (size_t d = 0; d + 1 < H.level_ptr.size(); d++) {
     int64_t g = 0;
     for (int64_t i = H.level_ptr[d]; i < H.level_ptr[d + 1]; i++) {
-      const int64_t c = cK(H, H.level_sn[i]);
-      g += c * c;
+      g += cK(H, H.level_sn[i]) * cU(H, H.level_sn[i]);
     }
     gmax = std::max(gmax, g);
   }
@@ -403,8 +447,8 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
   for (size_t d = 0; d + 1 < H.hlevel_ptr.size(); d++) {
     int64_t f = 0;
     for (int64_t i = H.hlevel_ptr[d]; i < H.hlevel_ptr[d + 1]; i++) {
-      const int64_t K = H.hlevel_sn[i], s = H.sn_width[K], c = cK(H, K);
-      f += 2 * s * s + 2 * c * s + c * c;
+      const int64_t K = H.hlevel_sn[i], s = H.sn_width[K], c = cK(H, K), cu = cU(H, K);
+      f += 2 * s * s + (c + cu) * s + c * cu;
     }
     fmax = std::max(fmax, f);
   }
@@ -539,11 +583,13 @@ int build_factor_plan(pselinv_ctx* h) {
     int64_t off = 0;  // scalars into scratch
     for (int64_t b = 0; b < nb; b++)
       for (int64_t i = H.hlevel_ptr[lev]; i < H.hlevel_ptr[lev + 1]; i++) {
-        const int64_t K = H.hlevel_sn[i], s = H.sn_width[K], c = cK(H, K);
-        const int64_t w0 = off, t0 = w0 + 2 * s * s, s0 = t0 + 2 * c * s;
-        off = s0 + c * c;
+        // c: rows of the L panel (R_K, or R_L(K) for a general pattern),
+        // cu: rows of the U^T panel (c, or R_U(K))
+        const int64_t K = H.hlevel_sn[i], s = H.sn_width[K], c = cK(H, K), cu = cU(H, K);
+        const int64_t w0 = off, t0 = w0 + 2 * s * s, s0 = t0 + (c + cu) * s;
+        off = s0 + c * cu;
         diag.push_back({(int)b, (int)K, 0, 0});
-        if (c == 0) continue;
+        if (c == 0 && cu == 0) continue;
         tri.push_back({b, K, w0});
         char* base = h->lu + ((size_t)b * H.storage + H.sn_offset[K]) * es;
         char* Lp = base + (size_t)s * s * es;
@@ -554,17 +600,21 @@ int build_factor_plan(pselinv_ctx* h) {
         char* TU = TL + (size_t)c * s * es;
         char* Sc = h->scratch + (size_t)s0 * es;
         // L = A U^-1, U^T = A^T L^-T: both B operands upper triangular
-        trsm.push_back(make_desc(Lp, Uinv, TL, c, s, s, c, s, c, 0, 0, 1.0, 0.0, 0, 1,
-                                 GEMM_TRI_UPPER_B));
-        trsm.push_back(make_desc(Up, Linv, TU, c, s, s, c, s, c, 0, 1, 1.0, 0.0, 0, 1,
-                                 GEMM_TRI_UPPER_B));
-        schur.push_back(make_desc(TL, TU, Sc, c, c, s, c, c, c, 0, 1, 1.0, 0.0));
-        for (int tq = 0; tq < ceil_div(c, 32); tq++)
-          for (int tp = 0; tp < ceil_div(c, 32); tp++) {
-            gt.push_back({(int)b, (int)K, tp, tq});
-            gofs.push_back(s0);
-          }
-        segs.push_back({TL, Lp, 2 * c * s});
+        if (c > 0)
+          trsm.push_back(make_desc(Lp, Uinv, TL, c, s, s, c, s, c, 0, 0, 1.0, 0.0, 0, 1,
+                                   GEMM_TRI_UPPER_B));
+        if (cu > 0)
+          trsm.push_back(make_desc(Up, Linv, TU, cu, s, s, cu, s, cu, 0, 1, 1.0, 0.0, 0, 1,
+                                   GEMM_TRI_UPPER_B));
+        if (c > 0 && cu > 0) {
+          schur.push_back(make_desc(TL, TU, Sc, c, cu, s, c, cu, c, 0, 1, 1.0, 0.0));
+          for (int tq = 0; tq < ceil_div(cu, 32); tq++)
+            for (int tp = 0; tp < ceil_div(c, 32); tp++) {
+              gt.push_back({(int)b, (int)K, tp, tq});
+              gofs.push_back(s0);
+            }
+        }
+        segs.push_back({TL, Lp, (c + cu) * s});
       }
     // blocked LU of the diagonal blocks: panels of 32 columns, each a panel
     // launch (pivot block, L21 rows, U12 columns) and a trailing-update GEMM,
@@ -680,6 +730,41 @@ void add_slice_step(Plan& P, const std::vector<SliceDesc>& descs, int level, boo
   st.bytes = (size_t)bytes;
   st.level = level;
   P.steps.push_back(st);
+}
+
+// Maxima (maxima = true) or slicing pass over the G tiles of a level and
+// the ordinary slice sets descs[dense[i]] of its panels, in one launch.
+void add_gslice_step(Plan& P, const std::vector<SliceDesc>& descs,
+                     const std::vector<GTileTask>& gtasks, const std::vector<int>& dense,
+                     int level, bool maxima, size_t es) {
+  if (gtasks.empty() && dense.empty()) return;
+  std::vector<SliceTask> st;
+  double bytes = 0;
+  for (int d : dense) {
+    const SliceDesc& g = descs[d];
+    for (int kc = 0; kc < ceil_div(g.K32, 2); kc++)
+      for (int rb = 0; rb < g.R64; rb++) st.push_back({d, rb, kc});
+    bytes += 8.0 * g.R * g.Kd * (g.cplx ? 2 : 1);
+    if (!maxima) bytes += 2.0 * g.S * g.R64 * 64.0 * g.K32 * 32;
+  }
+  for (const GTileTask& t : gtasks) {
+    const SliceDesc& g = descs[t.dr];
+    const double rows = std::min(64, g.R - 64 * t.tp), cols = std::min(64, g.R - 64 * t.tq);
+    bytes += rows * cols * (double)es;  // the tile's entries, read once
+    if (!maxima)  // its slices in one or two layouts
+      bytes += (t.dc >= 0 ? 2.0 : 1.0) * 2.0 * g.S * 64.0 * 64.0 * (g.cplx ? 2 : 1);
+  }
+  Step s;
+  s.kind = ST_GSLICE;
+  s.cfg = maxima ? 1 : 0;
+  s.n = (int)gtasks.size();
+  s.n2 = (int)st.size();
+  s.descs = P.push(descs);
+  s.tasks = P.push(gtasks);
+  s.offs = P.push(st);
+  s.bytes = (size_t)bytes;
+  s.level = level;
+  P.steps.push_back(s);
 }
 
 // K blocks (of 32) of one exact accumulation chunk of the sliced GEMM, and
@@ -891,14 +976,13 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   const int S = h->slices;
   const size_t es = h->esize;
   const int cplx = h->dtype == PSELINV_C128 ? 1 : 0;
-  std::vector<SnTask> gt;
-  std::vector<int64_t> gofs, mofs;
-  std::vector<SliceDesc> sl1, sl2, mx1;
+  std::vector<SliceDesc> gd, sl2;  // gd: G by rows / columns, Lhat, Uhat^T of every supernode
+  std::vector<GTileTask> gt;
+  std::vector<int> dense;          // the panels' slice sets in gd
   std::vector<OzDesc> main, dg;
   std::vector<CopySeg> zero, mirror;
   const bool sym = h->opts.symmetric != 0;
   OzBuilder ob(h, (size_t)gbase_scalars * es);
-  auto take = [&](size_t bytes) { return ob.take(bytes); };
   // row and column maxima of every G and panel of the level (the sweep's
   // maxima region, zeroed at its start)
   int64_t nmax = 0;
@@ -911,9 +995,6 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   max_cursor += align256((size_t)nmax * 8 + 8);
   h->scratch_high = std::max(h->scratch_high, max_cursor);
   int64_t moff = 0;
-  auto slice_desc = [&](const double* src, int ld, int mode, int R, int Kd) {
-    return ob.slice(src, ld, mode, R, Kd);
-  };
   auto push_product = [&](std::vector<OzDesc>& out, const SliceDesc& a, const SliceDesc& b,
                           char* C, int ldc, int M, int N) {
     ob.product(out, a, b, C, ldc, M, N, -1.0);
@@ -922,45 +1003,38 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
     for (int64_t K : grp) {
       const int s = (int)H.sn_width[K], c = (int)(H.rows_ptr[K + 1] - H.rows_ptr[K]);
       if (c == 0) continue;
-      char* G = take((size_t)c * c * es);
-      const int64_t g0 = (G - h->scratch) / (int64_t)es;
       const int64_t m0 = moff;
       moff += 2 * c + 3 * s;
-      for (int tq = 0; tq < ceil_div(c, 32); tq++)
-        for (int tp = 0; tp < ceil_div(c, 32); tp++) {
-          gt.push_back({(int)b, (int)K, tp, tq});
-          gofs.push_back(g0);
-          mofs.push_back(m0);
-        }
       const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
       const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
       // symmetric A: G is symmetric and Uhat = Lhat^T, so step 5's product is
       // the transpose of step 3's (a copy) and step 4 uses Lhat
-      SliceDesc gr = slice_desc((const double*)G, c, SLICE_ROWS, c, c);
-      gr.maxbits = maxbase + m0;  // row maxima of G (from the gather for real data)
-      SliceDesc lh = slice_desc((const double*)(h->nf + lo), c, SLICE_COLS, s, c);
+      SliceDesc gr = ob.slice(nullptr, c, SLICE_ROWS, c, c);  // G by rows (from the gather)
+      gr.maxbits = maxbase + m0;
+      SliceDesc lh = ob.slice(h->nf + lo, c, SLICE_COLS, s, c);
       lh.maxbits = maxbase + m0 + 2 * c;
       SliceDesc gc = gr, uh = lh;
       if (!sym) {
-        gc = slice_desc((const double*)G, c, SLICE_COLS, c, c);
-        gc.maxbits = maxbase + m0 + c;  // column maxima of G
-        uh = slice_desc((const double*)(h->nf + uo), c, SLICE_COLS, s, c);
+        gc = ob.slice(nullptr, c, SLICE_COLS, c, c);  // G by columns
+        gc.maxbits = maxbase + m0 + c;
+        uh = ob.slice(h->nf + uo, c, SLICE_COLS, s, c);
         uh.maxbits = maxbase + m0 + 2 * c + s;
       }
-      SliceDesc ak = slice_desc((const double*)(h->ainv + lo), c, SLICE_COLS, s, c);
+      SliceDesc ak = ob.slice(h->ainv + lo, c, SLICE_COLS, s, c);
       ak.maxbits = maxbase + m0 + 2 * c + 2 * s;
-      sl1.push_back(gr);
-      sl1.push_back(lh);
+      const int ir = (int)gd.size();
+      gd.push_back(gr);
+      const int ic = sym ? -1 : (int)gd.size();
+      if (!sym) gd.push_back(gc);
+      dense.push_back((int)gd.size());
+      gd.push_back(lh);
       if (!sym) {
-        sl1.push_back(gc);
-        sl1.push_back(uh);
+        dense.push_back((int)gd.size());
+        gd.push_back(uh);
       }
-      if (cplx) {
-        mx1.push_back(gr);
-        if (!sym) mx1.push_back(gc);
-      }
-      mx1.push_back(lh);
-      if (!sym) mx1.push_back(uh);
+      for (int tq = 0; tq < ceil_div(c, 64); tq++)
+        for (int tp = 0; tp < ceil_div(c, 64); tp++)
+          gt.push_back({(int)b, (int)K, tp, tq, ir, ic});
       sl2.push_back(ak);
       // step 3: Ainv(C,K) = -G Lhat;  step 5: Ainv(K,C)^T = -G^T Uhat^T
       push_product(main, gr, lh, h->ainv + lo, c, c, s);
@@ -971,22 +1045,13 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
       zero.push_back({nullptr, h->ainv + lo, (int64_t)2 * c * s * (cplx ? 2 : 1)});
     }
   if (gt.empty()) return;
-  Step g;
-  g.kind = ST_GATHER;
-  g.n = (int)gt.size();
-  g.tasks = P.push(gt);
-  g.offs = P.push(gofs);
-  if (!cplx) {
-    g.offs2 = P.push(mofs);
-    g.ptr2 = maxbase;
-  }
-  g.level = lev;
-  P.steps.push_back(g);
   const int prec = PSELINV_PREC_OZAKI_FP16;
   const int ks_main = tuned_value(h, prec, lev, 1, choose_ozaki_ksplit(main));
   const int ks_diag = tuned_value(h, prec, lev, 2, choose_ozaki_ksplit(dg));
-  add_slice_step(P, mx1, lev, true);
-  add_slice_step(P, sl1, lev, false);
+  // G's maxima, then its slices in both layouts straight from the ancestors'
+  // blocks (with the panels' maxima and slices in the same launches)
+  add_gslice_step(P, gd, gt, dense, lev, true, es);
+  add_gslice_step(P, gd, gt, dense, lev, false, es);
   // outputs of products split along K (requested, or forced by the exact
   // chunk limit) are accumulated: zero them first
   if (set_ozaki_ksplit(main, ks_main, false)) add_zero_step(P, zero, lev);
@@ -1063,7 +1128,7 @@ double level_product_flops(const pselinv_ctx* h, int lev) {
   double lf = 0;
   for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
     const double c = (double)cK(H, H.level_sn[i]), w = (double)H.sn_width[H.level_sn[i]];
-    lf += 4.0 * c * c * w;
+    lf += 4.0 * c * (double)cU(H, H.level_sn[i]) * w;
   }
   return lf * (double)h->nbatch * (h->dtype == DT_F64 ? 1.0 : 4.0);
 }
@@ -1095,6 +1160,8 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   // the first levels, and the deep levels' in a second one behind it; the
   // first normalisation that needs either waits for it.
   const int nlev = (int)H.level_ptr.size() - 1;
+  // a partitioned sweep covers a subset of the supernodes
+  auto in_set = [&](int64_t K) { return h->subset.empty() || h->subset[(size_t)K] != 0; };
   int lev_a = -1, lev_b = -1;
   {
     auto level_tasks = [&](int l) {
@@ -1121,6 +1188,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       for (int l = 0; l < nlev; l++)
         for (int64_t i = H.level_ptr[l]; i < H.level_ptr[l + 1]; i++) {
           const int64_t K = H.level_sn[i];
+          if (!in_set(K)) continue;
           (l <= lev_a ? ta : l <= lev_b ? tb : tc).push_back({b, K, wbase[b * H.ns + K]});
         }
     add_tri_step(P, H, ta, -1, 1, false);  // one launch: the first normalisation waits for it
@@ -1139,7 +1207,8 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
     for (int64_t b = 0; b < nb; b++)
       for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++) {
         const int64_t K = H.level_sn[i];
-        const int64_t s = H.sn_width[K], c = cK(H, K), w0 = wbase[b * H.ns + K];
+        if (!in_set(K)) continue;
+        const int64_t s = H.sn_width[K], c = cK(H, K), cu = cU(H, K), w0 = wbase[b * H.ns + K];
         const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
         char* Linv = h->scratch + (size_t)w0 * es;
         char* Uinv = Linv + (size_t)s * s * es;
@@ -1147,14 +1216,13 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
         // D_K = Uinv Linv (upper x lower), Lhat = L Linv, Uhat^T = U^T Uinv^T (lower B)
         norm.push_back(make_desc(Uinv, Linv, h->ainv + so, s, s, s, s, s, s, 0, 0, 1.0, 0.0, 0, 1,
                                  GEMM_TRI_UPPER_A | GEMM_TRI_LOWER_B));
-        if (c > 0) {
-          const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
+        const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
+        if (c > 0)
           norm.push_back(make_desc(h->lu + lo, Linv, h->nf + lo, c, s, s, c, s, c, 0, 0, 1.0, 0.0,
                                    0, 1, GEMM_TRI_LOWER_B));
-          if (!h->opts.symmetric)  // symmetric A: Uhat = Lhat^T, not needed
-            norm.push_back(make_desc(h->lu + uo, Uinv, h->nf + uo, c, s, s, c, s, c, 0, 1, 1.0, 0.0,
-                                     0, 1, GEMM_TRI_LOWER_B));
-        }
+        if (cu > 0 && !h->opts.symmetric)  // symmetric A: Uhat = Lhat^T, not needed
+          norm.push_back(make_desc(h->lu + uo, Uinv, h->nf + uo, cu, s, s, cu, s, cu, 0, 1, 1.0,
+                                   0.0, 0, 1, GEMM_TRI_LOWER_B));
       }
     const size_t first = P.steps.size();
     // levels of few wide supernodes (near the roots): split K so that the
@@ -1207,11 +1275,13 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
     // groups: the whole level, or one supernode at a time
     std::vector<std::vector<int64_t>> groups;
     if (schedule == PSELINV_SCHED_LEVEL) {
-      groups.emplace_back(H.level_sn.begin() + H.level_ptr[lev],
-                          H.level_sn.begin() + H.level_ptr[lev + 1]);
+      groups.emplace_back();
+      for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++)
+        if (in_set(H.level_sn[i])) groups.back().push_back(H.level_sn[i]);
+      if (groups.back().empty()) groups.pop_back();
     } else {
       for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++)
-        groups.push_back({H.level_sn[i]});
+        if (in_set(H.level_sn[i])) groups.push_back({H.level_sn[i]});
     }
     const int slot_main = precision == PSELINV_PREC_OZAKI_FP16 ? 4 : 1;
     const int slot_diag = precision == PSELINV_PREC_OZAKI_FP16 ? 5 : 2;
@@ -1220,37 +1290,64 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
         add_ozaki_level(h, P, grp, nb, gbase, (int)lev, max_cursor);
         continue;
       }
-      if (schedule == PSELINV_SCHED_LEVEL && add_small_level(h, P, grp, nb, (int)lev)) continue;
+      if (schedule == PSELINV_SCHED_LEVEL && !H.general && add_small_level(h, P, grp, nb, (int)lev))
+        continue;
       std::vector<SnTask> gt;
       std::vector<int64_t> gofs;
       std::vector<GemmDesc> main, dg;
-      std::vector<CopySeg> mirror;
+      std::vector<CopySeg> mirror, zsegs;
       int64_t goff = gbase;
       for (int64_t b = 0; b < nb; b++)
         for (int64_t K : grp) {
-          const int64_t s = H.sn_width[K], c = cK(H, K);
-          if (c == 0) continue;
+          const int64_t s = H.sn_width[K], c = cK(H, K), cu = cU(H, K);
+          if (c == 0 || cu == 0) {
+            // nothing after D_K; with one structure empty (a general
+            // pattern) the other panel of Ainv is zero (steps 3 and 5 sum
+            // over the empty one)
+            if (c + cu > 0) {
+              const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
+              zsegs.push_back({nullptr, h->ainv + so + (size_t)s * s * es,
+                               (c + cu) * s * (int64_t)(es / 8)});
+            }
+            continue;
+          }
           const int64_t g0 = goff;
-          goff += c * c;
+          goff += c * cu;
           h->scratch_high = std::max(h->scratch_high, (size_t)goff * es);
+          const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
+          const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
+          char* G = h->scratch + (size_t)g0 * es;
+          const int ksplit = std::max(1, (int)std::min<int64_t>(cu / 256, 64));
+          if (H.general) {
+            // G = Ainv(R_U, R_L) (cu x c).  Step 3: Ainv(R_U, K) = -G Lhat into
+            // the U^T panel; step 5: Ainv(K, R_L)^T = -G^T Uhat^T into the L
+            // panel; step 4: Ainv_KK += -Uhat Ainv(R_U, K)
+            for (int tq = 0; tq < ceil_div(c, 32); tq++)
+              for (int tp = 0; tp < ceil_div(cu, 32); tp++) {
+                gt.push_back({(int)b, (int)K, tp, tq});
+                gofs.push_back(g0);
+              }
+            main.push_back(make_desc(G, h->nf + lo, h->ainv + uo, cu, s, c, cu, c, cu, 0, 0, -1.0, 0.0));
+            main.push_back(make_desc(G, h->nf + uo, h->ainv + lo, c, s, cu, cu, cu, c, 1, 0, -1.0, 0.0));
+            dg.push_back(make_desc(h->nf + uo, h->ainv + uo, h->ainv + so, s, s, cu, cu, cu, s, 1, 0,
+                                   -1.0, 1.0, 1, ksplit));
+            continue;
+          }
           for (int tq = 0; tq < ceil_div(c, 32); tq++)
             for (int tp = 0; tp < ceil_div(c, 32); tp++) {
               gt.push_back({(int)b, (int)K, tp, tq});
               gofs.push_back(g0);
             }
-          const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
-          const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
-          char* G = h->scratch + (size_t)g0 * es;
           main.push_back(make_desc(G, h->nf + lo, h->ainv + lo, c, s, c, c, c, c, 0, 0, -1.0, 0.0));
           // symmetric A: step 5 is the transpose of step 3 and Uhat = Lhat^T
           if (sym)
             mirror.push_back({h->ainv + lo, h->ainv + uo, c * s});
           else
             main.push_back(make_desc(G, h->nf + uo, h->ainv + uo, c, s, c, c, c, c, 1, 0, -1.0, 0.0));
-          const int ksplit = std::max(1, (int)std::min<int64_t>(c / 256, 64));
           dg.push_back(make_desc(h->nf + (sym ? lo : uo), h->ainv + lo, h->ainv + so, s, s, c, c, c,
                                  s, 1, 0, -1.0, 1.0, 1, ksplit));
         }
+      add_zero_step(P, zsegs, (int)lev);
       if (gt.empty()) continue;
       Step g;
       g.kind = ST_GATHER;
@@ -1298,14 +1395,22 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       launch_lu_panel(h->dtype, h->S, h->lu, (const SnTask*)(a + s.tasks), s.n, st);
       break;
     case ST_GATHER:
-      launch_gather(h->dtype, h->S, h->ainv, h->scratch, (const int64_t*)(a + s.offs),
-                    (const SnTask*)(a + s.tasks), s.n, st,
-                    s.ptr2 ? (const int64_t*)(a + s.offs2) : nullptr,
-                    (unsigned long long*)s.ptr2);
+      if (h->H.general)
+        launch_gather_general(h->dtype, h->S, h->ainv, h->scratch, (const int64_t*)(a + s.offs),
+                              (const SnTask*)(a + s.tasks), s.n, st);
+      else
+        launch_gather(h->dtype, h->S, h->ainv, h->scratch, (const int64_t*)(a + s.offs),
+                      (const SnTask*)(a + s.tasks), s.n, st,
+                      s.ptr2 ? (const int64_t*)(a + s.offs2) : nullptr,
+                      (unsigned long long*)s.ptr2);
       break;
     case ST_SCATTER_SUB:
-      launch_scatter_sub(h->dtype, h->S, h->lu, h->scratch, (const int64_t*)(a + s.offs),
-                         (const SnTask*)(a + s.tasks), s.n, st);
+      if (h->H.general)
+        launch_scatter_sub_general(h->dtype, h->S, h->lu, h->scratch, (const int64_t*)(a + s.offs),
+                                   (const SnTask*)(a + s.tasks), s.n, st);
+      else
+        launch_scatter_sub(h->dtype, h->S, h->lu, h->scratch, (const int64_t*)(a + s.offs),
+                           (const SnTask*)(a + s.tasks), s.n, st);
       break;
     case ST_COPY:
       launch_copy(h->dtype, (const CopySeg*)(a + s.tasks), s.n, s.grid, st);
@@ -1330,6 +1435,11 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
     case ST_SMALL_LEVEL:
       launch_small_level(h->dtype, h->S, h->ainv, h->nf, (const SnTask*)(a + s.tasks), s.n,
                          (size_t)s.cfg, h->opts.symmetric != 0, st);
+      break;
+    case ST_GSLICE:
+      launch_gslice(h->dtype, h->S, h->ainv, (const SliceDesc*)(a + s.descs),
+                    (const GTileTask*)(a + s.tasks), s.n, (const SliceTask*)(a + s.offs), s.n2,
+                    s.cfg == 1, st);
       break;
   }
 }
@@ -1430,6 +1540,29 @@ void free_numeric(pselinv_ctx* h) {
   h->factored = h->inverted = false;
 }
 
+// Common tail of the analyses: widest supernode, the input pattern (for
+// the consumers), and the device copy of the structure.
+int finish_analyze(pselinv_ctx* h, int64_t n, const int64_t* colptr, const int64_t* rowind,
+                   pselinv_t* out) {
+  for (int64_t k = 0; k < h->H.ns; k++) h->max_width = std::max<int>(h->max_width, (int)h->H.sn_width[k]);
+  h->colptr_h.assign(colptr, colptr + n + 1);
+  h->rowind_h.assign(rowind, rowind + colptr[n]);
+  if (!h->opts.host_only) {
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+      (void)cudaGetLastError();
+      delete h;
+      return PSELINV_ERR_CUDA;
+    }
+    const int rc = upload_structure(h);
+    if (rc != PSELINV_OK) {
+      pselinv_free(h);
+      return rc;
+    }
+  }
+  *out = h;
+  return PSELINV_OK;
+}
+
 int read_device_error(pselinv_ctx* h, cudaStream_t st) {
   int herr[2] = {0, 0};
   CK(cudaMemcpyAsync(herr, h->derr, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1515,28 +1648,75 @@ int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind, con
     }
     perm = nd.data();
   }
-  int rc = analyze_host(n, colptr, rowind, perm, h->opts.max_supernode, h->opts.relax_pct, h->H);
+  const int rc = analyze_host(n, colptr, rowind, perm, h->opts.max_supernode, h->opts.relax_pct,
+                              h->H);
   if (rc != PSELINV_OK) {
     delete h;
     return rc;
   }
-  for (int64_t k = 0; k < h->H.ns; k++) h->max_width = std::max<int>(h->max_width, (int)h->H.sn_width[k]);
-  h->colptr_h.assign(colptr, colptr + n + 1);
-  h->rowind_h.assign(rowind, rowind + colptr[n]);
-  if (!h->opts.host_only) {
-    if (cudaGetDevice(&h->device) != cudaSuccess) {
-      (void)cudaGetLastError();
-      delete h;
-      return PSELINV_ERR_CUDA;
-    }
-    rc = upload_structure(h);
-    if (rc != PSELINV_OK) {
-      pselinv_free(h);
-      return rc;
-    }
+  return finish_analyze(h, n, colptr, rowind, out);
+}
+
+int pselinv_analyze_general(int64_t n, const int64_t* colptr, const int64_t* rowind,
+                            const int64_t* rperm, const int64_t* cperm, const pselinv_opts* opts,
+                            pselinv_t* out) {
+  if (!out) return PSELINV_ERR_ARG;
+  *out = nullptr;
+  pselinv_ctx* h = new (std::nothrow) pselinv_ctx();
+  if (!h) return PSELINV_ERR_OOM;
+  if (opts) h->opts = *opts; else pselinv_default_opts(&h->opts);
+  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 256 || h->opts.symmetric) {
+    delete h;
+    return PSELINV_ERR_ARG;
   }
-  *out = h;
-  return PSELINV_OK;
+  const int rc = analyze_general_host(n, colptr, rowind, rperm, cperm, h->opts.max_supernode,
+                                      h->opts.relax_pct, h->H);
+  if (rc != PSELINV_OK) {
+    delete h;
+    return rc;
+  }
+  return finish_analyze(h, n, colptr, rowind, out);
+}
+
+int pselinv_group(const pselinv_t* members, int64_t count, const pselinv_opts* opts,
+                  pselinv_t* out) {
+  if (!out) return PSELINV_ERR_ARG;
+  *out = nullptr;
+  if (!members || count < 1) return PSELINV_ERR_ARG;
+  int64_t N = 0, NNZ = 0;
+  for (int64_t m = 0; m < count; m++) {
+    if (!members[m]) return PSELINV_ERR_ARG;
+    if (members[m]->H.general) return PSELINV_ERR_UNSUPPORTED;
+    N += members[m]->H.n;
+    NNZ += (int64_t)members[m]->rowind_h.size();
+  }
+  std::vector<int64_t> colptr, rowind, perm;
+  try {
+    colptr.reserve((size_t)N + 1);
+    rowind.reserve((size_t)NNZ);
+    perm.reserve((size_t)N);
+  } catch (const std::bad_alloc&) {
+    return PSELINV_ERR_OOM;
+  }
+  // direct sum A_1 (+) A_2 (+) ...: member m's rows and columns shifted by
+  // the sizes before it, its ordering likewise (block diagonal, so the
+  // elimination forest is the union of the members' trees)
+  colptr.push_back(0);
+  int64_t roff = 0, zoff = 0;
+  for (int64_t m = 0; m < count; m++) {
+    const pselinv_ctx* g = members[m];
+    const int64_t n = g->H.n;
+    for (int64_t j = 0; j < n; j++) colptr.push_back(zoff + g->colptr_h[(size_t)j + 1]);
+    for (int64_t r : g->rowind_h) rowind.push_back(r + roff);
+    for (int64_t j = 0; j < n; j++) perm.push_back(g->H.perm[(size_t)j] + roff);
+    roff += n;
+    zoff += (int64_t)g->rowind_h.size();
+  }
+  pselinv_opts o = opts ? *opts : members[0]->opts;
+  if (!opts) o.host_only = 0;
+  for (int64_t m = 0; m < count && !opts; m++)
+    if (!members[m]->opts.host_only) o.host_only = 0;
+  return pselinv_analyze(N, colptr.data(), rowind.data(), perm.data(), &o, out);
 }
 
 int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, void* stream) {
@@ -1583,6 +1763,7 @@ int pselinv_selinv(pselinv_t h, int precision, void* stream) {
   if (!h || !h->factored) return PSELINV_ERR_ARG;
   if (precision < 0) precision = h->opts.precision;
   if (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16) return PSELINV_ERR_ARG;
+  if (h->H.general && precision != PSELINV_PREC_FP64) return PSELINV_ERR_UNSUPPORTED;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
@@ -1596,6 +1777,126 @@ int pselinv_selinv(pselinv_t h, int precision, void* stream) {
   if (rc != PSELINV_OK) return rc;
   h->inverted = true;
   return PSELINV_OK;
+}
+
+int pselinv_partition(pselinv_t h, int32_t nranks, int32_t* owner) {
+  if (!h || nranks < 1 || !owner) return PSELINV_ERR_ARG;
+  const HostSym& H = h->H;
+  if (H.general) return PSELINV_ERR_UNSUPPORTED;
+  const int64_t ns = H.ns;
+  // flops of every supernode and of the subtree below it (children first)
+  std::vector<double> f(ns), F(ns, 0.0);
+  std::vector<std::vector<int64_t>> children(ns);
+  for (int64_t k = 0; k < ns; k++) {
+    const double s = (double)H.sn_width[k], c = (double)cK(H, k);
+    f[k] = 4 * c * c * s + 4 * c * s * s + 4.0 / 3.0 * s * s * s;
+    if (H.sn_parent[k] >= 0) children[H.sn_parent[k]].push_back(k);
+  }
+  for (int64_t k = 0; k < ns; k++) {  // parents have larger indices
+    F[k] += f[k];
+    if (H.sn_parent[k] >= 0) F[H.sn_parent[k]] += F[k];
+  }
+  // split the heaviest subtree of the frontier into its children until the
+  // frontier has about eight subtrees per rank or the heaviest one is
+  // small against the share of a rank; the split roots form the top part
+  std::vector<int64_t> frontier;
+  for (int64_t k = 0; k < ns; k++) {
+    owner[k] = -1;
+    if (H.sn_parent[k] < 0) frontier.push_back(k);
+  }
+  double total = 0;
+  for (int64_t r : frontier) total += F[r];
+  if (nranks > 1)
+    for (;;) {
+      size_t best = frontier.size();
+      for (size_t i = 0; i < frontier.size(); i++)
+        if (!children[frontier[i]].empty() &&
+            (best == frontier.size() || F[frontier[i]] > F[frontier[best]]))
+          best = i;
+      if (best == frontier.size()) break;
+      const int64_t r = frontier[best];
+      if ((int64_t)frontier.size() >= 8 * (int64_t)nranks && F[r] <= total / (4.0 * nranks)) break;
+      frontier.erase(frontier.begin() + (std::ptrdiff_t)best);
+      for (int64_t c : children[r]) frontier.push_back(c);
+    }
+  // longest processing time first: heaviest subtree to the least loaded rank
+  std::sort(frontier.begin(), frontier.end(), [&](int64_t a, int64_t b) { return F[a] > F[b]; });
+  std::vector<double> load((size_t)nranks, 0.0);
+  std::vector<int32_t> root_rank(ns, -1);
+  for (int64_t r : frontier) {
+    const int32_t q = (int32_t)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[(size_t)q] += F[r];
+    root_rank[r] = q;
+  }
+  // every supernode below a frontier root belongs to that root's rank
+  for (int64_t k = ns - 1; k >= 0; k--) {
+    if (root_rank[k] >= 0) owner[k] = root_rank[k];
+    else if (H.sn_parent[k] >= 0 && owner[H.sn_parent[k]] >= 0) owner[k] = owner[H.sn_parent[k]];
+  }
+  return PSELINV_OK;
+}
+
+int pselinv_set_subset(pselinv_t h, const int32_t* owner, int32_t rank) {
+  if (!h) return PSELINV_ERR_ARG;
+  if (owner && h->H.general) return PSELINV_ERR_UNSUPPORTED;
+  if (owner) {
+    h->subset.assign((size_t)h->H.ns, 0);
+    for (int64_t k = 0; k < h->H.ns; k++) h->subset[(size_t)k] = owner[k] == rank ? 1 : 0;
+  } else {
+    h->subset.clear();
+  }
+  for (auto& pp : h->selinv_plan)
+    for (auto& p : pp) p.release();
+  return PSELINV_OK;
+}
+
+// G_K = Ainv(R_K, R_K) of instance `batch` between `buf` (device, c x c
+// column-major) and the handle's storage: export gathers it, import writes
+// it back into the ancestors' blocks it comes from.
+static int block_transfer(pselinv_t h, int64_t K, int64_t batch, void* buf, bool import,
+                          cudaStream_t st) {
+  if (!h || !h->factored || K < 0 || K >= h->H.ns || batch < 0 || batch >= h->nbatch || !buf)
+    return PSELINV_ERR_ARG;
+  if (h->H.general) return PSELINV_ERR_UNSUPPORTED;
+  if (!is_device_ptr(buf)) return PSELINV_ERR_ARG;
+  const int64_t c = cK(h->H, K);
+  if (c == 0) return PSELINV_OK;
+  CK(cudaSetDevice(h->device));
+  std::vector<SnTask> tasks;
+  for (int tq = 0; tq < ceil_div(c, 32); tq++)
+    for (int tp = 0; tp < ceil_div(c, 32); tp++) tasks.push_back({(int)batch, (int)K, tp, tq});
+  const size_t tb = align256(tasks.size() * sizeof(SnTask)), ob = align256(tasks.size() * 8);
+  if (tb + ob > h->blk_buf_bytes) {
+    CK(cudaStreamSynchronize(st));
+    if (h->blk_buf) cudaFree(h->blk_buf);
+    h->blk_buf = nullptr;
+    h->blk_buf_bytes = 0;
+    CK(cudaMalloc(&h->blk_buf, tb + ob));
+    h->blk_buf_bytes = tb + ob;
+  }
+  char* d = (char*)h->blk_buf;
+  CK(cudaMemcpyAsync(d, tasks.data(), tasks.size() * sizeof(SnTask), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d + tb, 0, tasks.size() * 8, st));
+  if (import)
+    launch_scatter_set(h->dtype, h->S, h->ainv, buf, (const int64_t*)(d + tb),
+                       (const SnTask*)d, (int)tasks.size(), st);
+  else
+    launch_gather(h->dtype, h->S, h->ainv, buf, (const int64_t*)(d + tb), (const SnTask*)d,
+                  (int)tasks.size(), st);
+  CK(cudaGetLastError());
+  // the host task list must outlive the copy
+  CK(cudaStreamSynchronize(st));
+  return PSELINV_OK;
+}
+
+int pselinv_export_block(pselinv_t h, int64_t K, int64_t batch, void* out, void* stream) {
+  return block_transfer(h, K, batch, out, false, (cudaStream_t)stream);
+}
+
+int pselinv_import_block(pselinv_t h, int64_t K, int64_t batch, const void* in, void* stream) {
+  const int rc = block_transfer(h, K, batch, const_cast<void*>(in), true, (cudaStream_t)stream);
+  if (rc == PSELINV_OK && h) h->inverted = true;
+  return rc;
 }
 
 int pselinv_set_schedule(pselinv_t h, int schedule) {
@@ -1659,6 +1960,11 @@ int pselinv_get_structure(pselinv_t h, pselinv_structure* o) {
   o->flops_selinv = H.flops_selinv;
   o->flops_selinv_exact = H.flops_selinv_exact;
   o->flops_factor = H.flops_factor;
+  o->general = H.general ? 1 : 0;
+  o->rperm = H.general ? H.rperm.data() : H.perm.data();
+  o->urows_ptr = H.general ? H.urows_ptr.data() : H.rows_ptr.data();
+  o->urows = H.general ? H.urows.data() : H.rows.data();
+  o->out_map = H.general ? H.inv_map.data() : H.value_map.data();
   return PSELINV_OK;
 }
 
@@ -1733,7 +2039,8 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
                                 PSELINV_STEP_GATHER,  PSELINV_STEP_SCATTER_SUB, PSELINV_STEP_COPY,
                                 PSELINV_STEP_MEMSET,  PSELINV_STEP_SCATTER_VALUES,
                                 PSELINV_STEP_SLICE,   PSELINV_STEP_OZAKI_GEMM, PSELINV_STEP_MEMSET,
-                                PSELINV_STEP_DIAG_LU, PSELINV_STEP_SMALL_LEVEL};
+                                PSELINV_STEP_DIAG_LU, PSELINV_STEP_SMALL_LEVEL,
+                                PSELINV_STEP_GATHER_SLICE};
     out[i].kind = kinds[s.kind];
     out[i].level = s.level;
     out[i].tasks = s.n;
@@ -1818,6 +2125,7 @@ extern "C" {
 int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, void* stream) {
   if (!h || !h->factored || (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16))
     return PSELINV_ERR_ARG;
+  if (h->H.general && precision != PSELINV_PREC_FP64) return PSELINV_ERR_UNSUPPORTED;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
@@ -1877,6 +2185,9 @@ int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, vo
         const Step& s = P.steps[i];
         if (s.level >= 0) lev_acc[s.level] += stats[i].ms;
         if (s.slot < 0) continue;
+        // phase B keeps its large levels split at their default K split,
+        // which need not be a candidate: only phase A times K splits
+        if (mode_tag == 1 && s.kind == ST_OZGEMM) continue;
         acc[std::make_tuple(s.level, s.slot, (int)s.kind, s.param)] += stats[i].ms;
       }
       for (const auto& kv : acc) {
@@ -2069,6 +2380,12 @@ int pselinv_trace(pselinv_t h, const void* weights, const void* B, void* out, vo
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = (int64_t)h->colptr_h.size() - 1, nnz = h->H.nnz;
+  if (!h->tslot && h->H.general) {
+    // Tr[B A^{-1}] = sum_p B[p] (A^{-1})_{col(p), row(p)}: exactly the
+    // selected entry returned for each input entry (Eq. sel_entries)
+    CK(cudaMalloc(&h->tslot, (size_t)std::max<int64_t>(nnz, 1) * 8));
+    CK(cudaMemcpy(h->tslot, h->H.inv_map.data(), (size_t)nnz * 8, cudaMemcpyHostToDevice));
+  }
   if (!h->tslot) {
     // transposed entry of every input entry (the pattern is structurally
     // symmetric), then its storage slot
@@ -2250,6 +2567,7 @@ void pselinv_free(pselinv_t h) {
     cudaFree(h->dsym);
     cudaFree(h->derr);
     cudaFree(h->tslot);
+    if (h->blk_buf) cudaFree(h->blk_buf);
   }
   delete h;
 }

@@ -74,6 +74,25 @@ struct SymDev {
   int32_t check;    // 1: bounds-check map reads
   int64_t relidx_size;
   int* err;         // [0] status, [1] info
+  // slot of the selected entry returned for each input entry (extraction,
+  // weighted sums): value_map for structurally symmetric handles
+  const int64_t* out_map;
+  // general patterns (general = 1; null for structurally symmetric
+  // handles): sn_c, rows_ptr, rows_blk and blk_* describe R_L(K) (the L
+  // panel's rows), sn_cu, urows_ptr, urows_blk and ublk_* R_U(K) (the U^T
+  // panel's rows); a block of R_L(K) maps the positions of R_U(K) from
+  // blk_q0 on (relidx at blk_rel - blk_q0) and a block of R_U(K) those of
+  // R_L(K) from ublk_q0 on; lrows / urows hold R_L and R_U themselves.
+  int32_t general;
+  const int32_t* sn_cu;
+  const int64_t* urows_ptr;
+  const int32_t* lrows;
+  const int32_t* urows;
+  const int32_t* urows_blk;
+  const int32_t* blk_q0;
+  const int32_t* ublk_sn;
+  const int64_t* ublk_rel;
+  const int32_t* ublk_q0;
 };
 
 enum DevErr { DEV_OK = 0, DEV_ZERO_PIVOT = 1, DEV_CHECK = 2, DEV_TIMEOUT = 3 };
@@ -186,6 +205,19 @@ struct OzDesc {
 struct OzTask {
   int d, tm, tn, ks;
 };
+// One 64 x 64 tile (tp, tq) of G_K = Ainv(R_K, R_K) of instance `inst`,
+// sliced straight from the ancestors' blocks in `store`: dr / dc index the
+// SliceDescs of G by rows and by columns (R = Kd = c_K; their src is unused;
+// dc < 0: by rows only, for a symmetric G)
+struct GTileTask {
+  int inst, K, tp, tq, dr, dc;
+};
+// maxima = true: the tiles' row and column maxima into the descs' maxbits
+// (and the maxima of the ordinary slice tasks stasks[0..nst)); false: their
+// slices (exponents from the maxima)
+void launch_gslice(int dtype, const SymDev& S, const void* store, const SliceDesc* descs,
+                   const GTileTask* gtasks, int ngt, const SliceTask* stasks, int nst, bool maxima,
+                   cudaStream_t st);
 cudaError_t prepare_ozaki_kernels();
 // maxima = true: accumulate row maxima into desc.maxbits; false: write the slices
 void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bool maxima,
@@ -272,6 +304,18 @@ void launch_small_level(int dtype, const SymDev& S, void* store, const void* nf,
 void launch_gather(int dtype, const SymDev& S, const void* store, void* out,
                    const int64_t* gofs, const SnTask* tasks, int ntasks, cudaStream_t st,
                    const int64_t* mofs = nullptr, unsigned long long* maxbase = nullptr);
+// General patterns: G_K = Ainv(R_U(K), R_L(K)) (c_U x c_L, column-major)
+// into out + gofs[task], tasks {inst, K, tile over R_U, tile over R_L}
+// (32 x 32 tiles); and store(R_L(K), R_U(K)) -= Sc_K (c_L x c_U) from
+// src + sofs[task], tasks {inst, K, tile over R_L, tile over R_U}.
+void launch_gather_general(int dtype, const SymDev& S, const void* store, void* out,
+                           const int64_t* gofs, const SnTask* tasks, int ntasks, cudaStream_t st);
+void launch_scatter_sub_general(int dtype, const SymDev& S, void* store, const void* src,
+                                const int64_t* sofs, const SnTask* tasks, int ntasks,
+                                cudaStream_t st);
+// store(R_K, R_K) = src + sofs[task] (the import of a gathered G_K); tasks as for gather
+void launch_scatter_set(int dtype, const SymDev& S, void* store, const void* src,
+                        const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st);
 // store(R_K, R_K) -= Sc_K (atomic) from src + sofs[task]; tasks as for gather
 void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src,
                         const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st);

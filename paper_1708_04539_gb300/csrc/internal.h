@@ -35,11 +35,31 @@ struct HostSym {
   std::vector<int32_t> relidx;
   std::vector<int64_t> value_map;  // storage slot of each input entry
   int64_t storage = 0;             // scalars per instance
+  // general patterns (analyze_general_host): rows / rows_ptr hold R_L(K)
+  // (the L panel's rows) and urows / urows_ptr R_U(K) (the U^T panel's
+  // rows, the columns of U right of K), which need not agree.  Row ordering
+  // rperm (new -> old; perm above is the column ordering).  Blocks of R_L(K)
+  // (blk_*) map the positions of R_U(K) from blk_q0 on (relidx at blk_rel)
+  // to the local index in J or the position in R_U(J); blocks of R_U(K)
+  // (ublk_*) map the positions of R_L(K) into J / R_L(J).  inv_map: slot of
+  // the selected entry (A^{-1})_{col,row} returned for each input entry.
+  bool general = false;
+  std::vector<int64_t> rperm, irperm;
+  std::vector<int64_t> urows_ptr, urows;
+  std::vector<int32_t> blk_q0;
+  std::vector<int32_t> usn_blk, ublk_sn, ublk_pb, ublk_pe, ublk_q0, urows_blk;
+  std::vector<int64_t> ublk_rel;
+  std::vector<int64_t> inv_map;
   double flops_selinv = 0, flops_selinv_exact = 0, flops_factor = 0;
 };
 
 // Host analysis; returns a PSELINV_* status.  No CUDA calls.
 int analyze_host(int64_t n, const int64_t* colptr, const int64_t* rowind, const int64_t* perm,
                  int64_t max_sn, int64_t relax_pct, HostSym& out);
+// The same for a general pattern with row ordering rperm and column
+// ordering cperm (static pivoting, P A Q with P != Q^T).
+int analyze_general_host(int64_t n, const int64_t* colptr, const int64_t* rowind,
+                         const int64_t* rperm, const int64_t* cperm, int64_t max_sn,
+                         int64_t relax_pct, HostSym& out);
 
 }  // namespace pselinv

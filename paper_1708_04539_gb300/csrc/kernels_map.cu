@@ -107,8 +107,150 @@ gather_kernel(SymDev S, const T* __restrict__ store, T* out, const int64_t* __re
   }
 }
 
-// store(R_K, R_K) -= Sc (atomic: siblings of one level update shared ancestors)
+// ---------------------------------------------------------------------------
+// general patterns (C_L != C_U)
+// ---------------------------------------------------------------------------
+// Slot of Ainv(x, y) for x = R_U(K)[p] in supernode I (block bp of R_U(K))
+// and y = R_L(K)[q] in supernode J (block bq of R_L(K)), on the pattern of
+// (L+U)^T: the diagonal block of J (I == J), the U^T panel of J (rows
+// R_U(J), I > J) or the L panel of I (rows R_L(I), I < J).  ok = false when
+// a checked read falls outside the maps or the storage.
+__device__ __forceinline__ int64_t gen_slot(const SymDev& S, int64_t rbL, int64_t rbU, int p,
+                                            int q, bool& ok) {
+  const int bq = S.rows_blk[rbL + q], bp = S.urows_blk[rbU + p];
+  const int J = S.blk_sn[bq], I = S.ublk_sn[bp];
+  int64_t ri;
+  if (I >= J) {
+    ri = S.blk_rel[bq] - S.blk_q0[bq] + p;  // x in J (local) or its position in R_U(J)
+  } else {
+    ri = S.ublk_rel[bp] - S.ublk_q0[bp] + q;  // position of y in R_L(I)
+  }
+  if (S.check && (ri < 0 || ri >= S.relidx_size)) {
+    ok = false;
+    return 0;
+  }
+  const int64_t r = S.relidx[ri];
+  int64_t slot;
+  if (I == J) {
+    slot = S.sn_off[J] + r + (int64_t)(S.lrows[rbL + q] - S.sn_first[J]) * S.sn_width[J];
+  } else if (I > J) {
+    const int sJ = S.sn_width[J];
+    slot = S.sn_off[J] + (int64_t)sJ * sJ + (int64_t)S.sn_c[J] * sJ + r +
+           (int64_t)(S.lrows[rbL + q] - S.sn_first[J]) * S.sn_cu[J];
+  } else {
+    const int sI = S.sn_width[I];
+    slot = S.sn_off[I] + (int64_t)sI * sI + r +
+           (int64_t)(S.urows[rbU + p] - S.sn_first[I]) * S.sn_c[I];
+  }
+  if (S.check && (slot < 0 || slot >= S.storage)) ok = false;
+  return slot;
+}
+
+// One 32 x 32 tile of G_K = Ainv(R_U(K), R_L(K)) per task: entries with I >= J
+// are read down the columns of J's blocks (lanes along p), the others along
+// the columns of I's L panel (lanes along q), transposed through shared memory.
 template <typename T>
+__global__ void __launch_bounds__(kThreads)
+gather_general_kernel(SymDev S, const T* __restrict__ store, T* out,
+                      const int64_t* __restrict__ gofs, const SnTask* __restrict__ tasks,
+                      int ntasks) {
+  __shared__ T tile[kTile][kTile + 1];
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SnTask task = tasks[t];
+    const int K = task.K;
+    const int cl = S.sn_c[K], cu = S.sn_cu[K];
+    const int64_t rbL = S.rows_ptr[K], rbU = S.urows_ptr[K];
+    const T* src = store + (int64_t)task.inst * S.storage;
+    T* G = out + gofs[t];
+    const int p0 = task.a * kTile, q0 = task.b * kTile;
+    for (int r = ly; r < kTile; r += kThreads / 32) {
+      const int p = p0 + lx, q = q0 + r;
+      if (p < cu && q < cl &&
+          S.ublk_sn[S.urows_blk[rbU + p]] >= S.blk_sn[S.rows_blk[rbL + q]]) {
+        bool ok = true;
+        const int64_t slot = gen_slot(S, rbL, rbU, p, q, ok);
+        if (!ok) set_error(S.err, DEV_CHECK, K);
+        tile[r][lx] = ok ? src[slot] : sc_zero(T());
+      }
+    }
+    for (int r = ly; r < kTile; r += kThreads / 32) {
+      const int p = p0 + r, q = q0 + lx;
+      if (p < cu && q < cl &&
+          S.ublk_sn[S.urows_blk[rbU + p]] < S.blk_sn[S.rows_blk[rbL + q]]) {
+        bool ok = true;
+        const int64_t slot = gen_slot(S, rbL, rbU, p, q, ok);
+        if (!ok) set_error(S.err, DEV_CHECK, K);
+        tile[lx][r] = ok ? src[slot] : sc_zero(T());
+      }
+    }
+    __syncthreads();
+    for (int r = ly; r < kTile; r += kThreads / 32) {
+      const int p = p0 + lx, q = q0 + r;
+      if (p < cu && q < cl) G[p + (int64_t)q * cu] = tile[r][lx];
+    }
+    __syncthreads();
+  }
+}
+
+// store(R_L(K), R_U(K)) -= Sc (c_L x c_U, column-major; atomic: supernodes
+// of one level may update the same ancestors).  Entry (i, m), i = R_L[p] in
+// supernode I, m = R_U[q] in J, goes to the diagonal block (I == J), the L
+// panel of J (I > J: position of i in R_L(J) from the map of R_U(K)'s block)
+// or the U^T panel of I (I < J: position of m in R_U(I)).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+scatter_sub_general_kernel(SymDev S, T* store, const T* __restrict__ src,
+                           const int64_t* __restrict__ sofs, const SnTask* __restrict__ tasks,
+                           int ntasks) {
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SnTask task = tasks[t];
+    const int K = task.K;
+    const int cl = S.sn_c[K], cu = S.sn_cu[K];
+    const int64_t rbL = S.rows_ptr[K], rbU = S.urows_ptr[K];
+    T* dst = store + (int64_t)task.inst * S.storage;
+    const T* Sc = src + sofs[t];
+    const int p0 = task.a * kTile, q0 = task.b * kTile;
+    for (int r = ly; r < kTile; r += kThreads / 32) {
+      const int p = p0 + lx, q = q0 + r;
+      if (p >= cl || q >= cu) continue;
+      const int bp = S.rows_blk[rbL + p], bq = S.urows_blk[rbU + q];
+      const int I = S.blk_sn[bp], J = S.ublk_sn[bq];
+      const int i = S.lrows[rbL + p], m = S.urows[rbU + q];
+      int64_t slot;
+      bool ok = true;
+      if (I == J) {
+        const int sI = S.sn_width[I], f = S.sn_first[I];
+        slot = S.sn_off[I] + (i - f) + (int64_t)(m - f) * sI;
+      } else if (I > J) {
+        const int64_t ri = S.ublk_rel[bq] - S.ublk_q0[bq] + p;
+        if (S.check && (ri < 0 || ri >= S.relidx_size)) ok = false;
+        const int sJ = S.sn_width[J];
+        slot = ok ? S.sn_off[J] + (int64_t)sJ * sJ + S.relidx[ri] +
+                        (int64_t)(m - S.sn_first[J]) * S.sn_c[J]
+                  : 0;
+      } else {
+        const int64_t ri = S.blk_rel[bp] - S.blk_q0[bp] + q;
+        if (S.check && (ri < 0 || ri >= S.relidx_size)) ok = false;
+        const int sI = S.sn_width[I];
+        slot = ok ? S.sn_off[I] + (int64_t)sI * sI + (int64_t)S.sn_c[I] * sI + S.relidx[ri] +
+                        (int64_t)(i - S.sn_first[I]) * S.sn_cu[I]
+                  : 0;
+      }
+      if (S.check && (slot < 0 || slot >= S.storage)) ok = false;
+      if (!ok) {
+        set_error(S.err, DEV_CHECK, K);
+        continue;
+      }
+      atomic_add_s(dst + slot, scale_s(Sc[p + (int64_t)q * cl], -1.0));
+    }
+  }
+}
+
+// store(R_K, R_K) -= Sc (atomic: siblings of one level update shared
+// ancestors); ASSIGN: store(R_K, R_K) = Sc (the import of a gathered block)
+template <typename T, bool ASSIGN = false>
 __global__ void __launch_bounds__(kThreads)
 scatter_sub_kernel(SymDev S, T* store, const T* __restrict__ src, const int64_t* __restrict__ sofs,
                    const SnTask* __restrict__ tasks, int ntasks) {
@@ -129,7 +271,10 @@ scatter_sub_kernel(SymDev S, T* store, const T* __restrict__ src, const int64_t*
         continue;
       }
       const T v = Sc[p + (int64_t)q * c];
-      atomic_add_s(dst + map_slot(S, rb, p, q), scale_s(v, -1.0));
+      if (ASSIGN)
+        dst[map_slot(S, rb, p, q)] = v;
+      else
+        atomic_add_s(dst + map_slot(S, rb, p, q), scale_s(v, -1.0));
     }
   }
 }
@@ -152,7 +297,7 @@ __global__ void __launch_bounds__(kThreads)
 extract_kernel(SymDev S, const T* __restrict__ store, T* out) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < S.nnz;
        p += (int64_t)gridDim.x * blockDim.x)
-    out[p] = store[S.value_map[p]];
+    out[p] = store[S.out_map[p]];
 }
 
 // Pole-expansion consumers (a weighted sum over the instances of a batch).
@@ -163,7 +308,7 @@ weighted_sum_kernel(SymDev S, const T* __restrict__ store, int nb, const T* __re
                     T* out) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < S.nnz;
        p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t slot = S.value_map[p];
+    const int64_t slot = S.out_map[p];
     T acc = sc_zero(T());
     for (int b = 0; b < nb; b++) acc = add_s(acc, mul_s(w[b], store[b * S.storage + slot]));
     out[p] = acc;
@@ -386,6 +531,43 @@ void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src
   else
     scatter_sub_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (cdouble*)store,
                                                            (const cdouble*)src, sofs, tasks, ntasks);
+}
+
+void launch_gather_general(int dtype, const SymDev& S, const void* store, void* out,
+                           const int64_t* gofs, const SnTask* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  if (dtype == DT_F64)
+    gather_general_kernel<double><<<grid, kThreads, 0, st>>>(S, (const double*)store,
+                                                             (double*)out, gofs, tasks, ntasks);
+  else
+    gather_general_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (const cdouble*)store,
+                                                              (cdouble*)out, gofs, tasks, ntasks);
+}
+
+void launch_scatter_sub_general(int dtype, const SymDev& S, void* store, const void* src,
+                                const int64_t* sofs, const SnTask* tasks, int ntasks,
+                                cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  if (dtype == DT_F64)
+    scatter_sub_general_kernel<double><<<grid, kThreads, 0, st>>>(
+        S, (double*)store, (const double*)src, sofs, tasks, ntasks);
+  else
+    scatter_sub_general_kernel<cdouble><<<grid, kThreads, 0, st>>>(
+        S, (cdouble*)store, (const cdouble*)src, sofs, tasks, ntasks);
+}
+
+void launch_scatter_set(int dtype, const SymDev& S, void* store, const void* src,
+                        const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  if (dtype == DT_F64)
+    scatter_sub_kernel<double, true><<<grid, kThreads, 0, st>>>(
+        S, (double*)store, (const double*)src, sofs, tasks, ntasks);
+  else
+    scatter_sub_kernel<cdouble, true><<<grid, kThreads, 0, st>>>(
+        S, (cdouble*)store, (const cdouble*)src, sofs, tasks, ntasks);
 }
 
 void launch_copy(int dtype, const CopySeg* segs, int nseg, int per_seg, cudaStream_t st) {

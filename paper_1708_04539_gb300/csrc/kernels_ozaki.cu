@@ -111,69 +111,274 @@ __device__ __forceinline__ void load8(const SliceDesc& d, int r, int k0, double 
   }
 }
 
-// Row maxima of |X| (bit patterns), accumulated with atomicMax into
-// d.maxbits (zeroed beforehand).
-__global__ void __launch_bounds__(kSliceThreads)
-slice_max_kernel(const SliceDesc* __restrict__ descs, const SliceTask* __restrict__ tasks, int ntasks) {
-  const int tid = threadIdx.x;
+// Row maxima of |X| (bit patterns) of one task, accumulated with atomicMax
+// into d.maxbits (zeroed beforehand).
+__device__ __forceinline__ void slice_max_task(const SliceDesc& d, const SliceTask& task, int tid) {
   const int ci = tid >> 3, rr = tid & 7;
   const int rl = (ci >> 2) * 8 + rr, kg = ci & 3;
-  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
-    const SliceTask task = tasks[t];
-    const SliceDesc d = descs[task.d];
-    const int r = task.rb * 64 + rl;
-    unsigned long long m = 0;
-    const int kb1 = min(d.K32, (task.kc + 1) * kSliceSpan);
-    for (int kb = task.kc * kSliceSpan; kb < kb1; kb++) {
-      double x[8];
-      load8(d, r, kb * 32 + kg * 8, x);
+  const int r = task.rb * 64 + rl;
+  unsigned long long m = 0;
+  const int kb1 = min(d.K32, (task.kc + 1) * kSliceSpan);
+  for (int kb = task.kc * kSliceSpan; kb < kb1; kb++) {
+    double x[8];
+    load8(d, r, kb * 32 + kg * 8, x);
 #pragma unroll
-      for (int j = 0; j < 8; j++) m = max(m, abs_bits(x[j]));
+    for (int j = 0; j < 8; j++) m = max(m, abs_bits(x[j]));
+  }
+  // the 4 lanes sharing a row are tid ^ 8, ^ 16 (same rr, kg = 0..3 inside a warp)
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 8));
+  m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
+  if (kg == 0 && r < d.R && m) atomicMax(d.maxbits + r, m);
+}
+
+// The S balanced base-128 digits of 8 values x of one row with exponent e,
+// written as the 16 bytes [16 tid, 16 tid + 16) of the 4 KB tile of every
+// slice at `dst` (slices `slice_stride` halves apart).
+__device__ __forceinline__ void write_digits(const double (&x)[8], int e, int S, __half* dst,
+                                             int64_t slice_stride) {
+  const int sh0 = 7 * S - e;
+  long long q[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) q[j] = fixed_point(x[j], sh0);
+  // balanced base-128 digits from the least significant slice upwards
+  for (int s = S - 1; s >= 0; s--) {
+    __align__(16) __half h[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      long long a = q[j];
+      if (s > 0) {
+        a = ((q[j] + 64) & 127) - 64;
+        q[j] = (q[j] - a) >> 7;
+      }
+      h[j] = __int2half_rn((int)a);
     }
-    // the 4 lanes sharing a row are tid ^ 8, ^ 16 (same rr, kg = 0..3 inside a warp)
-    m = max(m, __shfl_xor_sync(0xffffffffu, m, 8));
-    m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
-    if (kg == 0 && r < d.R && m) atomicMax(d.maxbits + r, m);
+    *reinterpret_cast<uint4*>(dst + s * slice_stride) = *reinterpret_cast<uint4*>(h);
   }
 }
 
-// Slices (see the work item above); exponents come from d.maxbits.
-__global__ void __launch_bounds__(kSliceThreads)
-slice_kernel(const SliceDesc* __restrict__ descs, const SliceTask* __restrict__ tasks, int ntasks) {
-  const int tid = threadIdx.x;
+// Slices of one task (see the work item above); exponents from d.maxbits.
+__device__ __forceinline__ void slice_task(const SliceDesc& d, const SliceTask& task, int tid) {
   const int ci = tid >> 3, rr = tid & 7;
   const int rl = (ci >> 2) * 8 + rr, kg = ci & 3;
+  const int r = task.rb * 64 + rl;
+  const int e = r < d.R ? exp_of_max(d.maxbits[r]) : 0;
+  if (task.kc == 0 && kg == 0 && r < d.R) d.exps[r] = e;
+  const int64_t slice_stride = (int64_t)d.R64 * d.K32 * (kTileBytes / 2);  // halves
+  const int kb1 = min(d.K32, (task.kc + 1) * kSliceSpan);
+  for (int kb = task.kc * kSliceSpan; kb < kb1; kb++) {
+    double x[8];
+    load8(d, r, kb * 32 + kg * 8, x);
+    write_digits(x, e, d.S,
+                 d.out + ((int64_t)task.rb * d.K32 + kb) * (kTileBytes / 2) + tid * 8,
+                 slice_stride);
+  }
+}
+
+__global__ void __launch_bounds__(kSliceThreads)
+slice_max_kernel(const SliceDesc* __restrict__ descs, const SliceTask* __restrict__ tasks, int ntasks) {
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const SliceTask task = tasks[t];
-    const SliceDesc d = descs[task.d];
-    const int r = task.rb * 64 + rl;
-    const int e = r < d.R ? exp_of_max(d.maxbits[r]) : 0;
-    if (task.kc == 0 && kg == 0 && r < d.R) d.exps[r] = e;
-    const int sh0 = 7 * d.S - e;
-    const int64_t slice_stride = (int64_t)d.R64 * d.K32 * (kTileBytes / 2);  // halves
-    const int kb1 = min(d.K32, (task.kc + 1) * kSliceSpan);
-    for (int kb = task.kc * kSliceSpan; kb < kb1; kb++) {
-      double x[8];
-      load8(d, r, kb * 32 + kg * 8, x);
-      long long q[8];
-#pragma unroll
-      for (int j = 0; j < 8; j++) q[j] = fixed_point(x[j], sh0);
-      __half* dst = d.out + ((int64_t)task.rb * d.K32 + kb) * (kTileBytes / 2) + tid * 8;
-      // balanced base-128 digits from the least significant slice upwards
-      for (int s = d.S - 1; s >= 0; s--) {
-        __align__(16) __half h[8];
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-          long long a = q[j];
-          if (s > 0) {
-            a = ((q[j] + 64) & 127) - 64;
-            q[j] = (q[j] - a) >> 7;
-          }
-          h[j] = __int2half_rn((int)a);
-        }
-        *reinterpret_cast<uint4*>(dst + s * slice_stride) = *reinterpret_cast<uint4*>(h);
+    slice_max_task(descs[task.d], task, threadIdx.x);
+  }
+}
+
+__global__ void __launch_bounds__(kSliceThreads)
+slice_kernel(const SliceDesc* __restrict__ descs, const SliceTask* __restrict__ tasks, int ntasks) {
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SliceTask task = tasks[t];
+    slice_task(descs[task.d], task, threadIdx.x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// G = Ainv(R_K, R_K) sliced straight from the ancestors' blocks
+// ---------------------------------------------------------------------------
+// A task stages one 64 x 64 tile of G in shared memory, reading each entry
+// once through the block index map (Algorithm 1's gather of Ainv_CC): the
+// entries on or below the block diagonal down the columns of the diagonal
+// blocks and L panels of the ancestors (lanes along the rows), the ones
+// above it along the rows of their U^T panels (lanes along the columns).
+// Per column and per row of the tile, the storage column and the relative
+// index list are looked up once, so an entry costs one index load and one
+// value load.  The maxima pass then accumulates the tile's row and column
+// maxima; the slicing pass writes the tile's slices in both layouts that
+// steps 3 and 5 read (G by rows and G by columns), so G is never written in
+// FP64.  Tasks past the G tiles are ordinary slice tasks (the panels of the
+// same level).
+constexpr int kGT = 64;        // G tile side
+constexpr int kGTPad = kGT + 1;
+
+template <typename T>
+__device__ __forceinline__ unsigned long long abs_bits_max(T v);
+template <>
+__device__ __forceinline__ unsigned long long abs_bits_max<double>(double v) {
+  return abs_bits(v);
+}
+template <>
+__device__ __forceinline__ unsigned long long abs_bits_max<cdouble>(cdouble v) {
+  return max(abs_bits(v.x), abs_bits(v.y));
+}
+__device__ __forceinline__ double part_of(double v, int) { return v; }
+__device__ __forceinline__ double part_of(cdouble v, int part) { return part ? v.y : v.x; }
+
+template <typename T>
+constexpr size_t gslice_smem() {
+  // tile + per column (diag base, L base, relative base: int64; block: int)
+  // + per row (U^T base, relative base: int64; block: int)
+  return (size_t)kGT * kGTPad * sizeof(T) + (size_t)kGT * (5 * 8 + 2 * 4);
+}
+
+template <typename T, bool MAXIMA>
+__global__ void __launch_bounds__(kSliceThreads)
+gslice_kernel(SymDev S, const T* __restrict__ store, const SliceDesc* __restrict__ descs,
+              const GTileTask* __restrict__ gtasks, int ngt,
+              const SliceTask* __restrict__ stasks, int nst) {
+  extern __shared__ __align__(16) unsigned char gs_raw[];
+  T* tile = reinterpret_cast<T*>(gs_raw);  // tile[pl * kGTPad + ql]
+  int64_t* cdiag = reinterpret_cast<int64_t*>(gs_raw + (size_t)kGT * kGTPad * sizeof(T));
+  int64_t* cpan = cdiag + kGT;
+  int64_t* crel = cpan + kGT;
+  int64_t* rpan = crel + kGT;
+  int64_t* rrel = rpan + kGT;
+  int* cblk = reinterpret_cast<int*>(rrel + kGT);
+  int* rblk = cblk + kGT;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int t = blockIdx.x; t < ngt + nst; t += gridDim.x) {
+    if (t >= ngt) {
+      const SliceTask task = stasks[t - ngt];
+      if (MAXIMA)
+        slice_max_task(descs[task.d], task, tid);
+      else
+        slice_task(descs[task.d], task, tid);
+      continue;
+    }
+    const GTileTask task = gtasks[t];
+    const int K = task.K;
+    const int c = S.sn_c[K];
+    const int64_t rb = S.rows_ptr[K];
+    const int64_t io = (int64_t)task.inst * S.storage;
+    const int p0 = task.tp * kGT, q0 = task.tq * kGT;
+    // per-column and per-row storage bases of the tile
+    if (tid < kGT) {
+      const int q = q0 + tid;
+      if (q < c) {
+        const int bq = S.rows_blk[rb + q];
+        const int J = S.blk_sn[bq];
+        const int64_t base = S.blk_rel[bq] - S.blk_pb[bq];
+        const int rq = S.relidx[base + q];  // local column of R_K[q] in J
+        const int sJ = S.sn_width[J];
+        cdiag[tid] = io + S.sn_off[J] + (int64_t)rq * sJ;
+        cpan[tid] = io + S.sn_off[J] + (int64_t)sJ * sJ + (int64_t)rq * S.sn_c[J];
+        crel[tid] = base;
+        cblk[tid] = bq;
+      } else {
+        cblk[tid] = 0x7FFFFFFF;
+      }
+    } else if (tid < 2 * kGT) {
+      const int pl = tid - kGT, p = p0 + pl;
+      if (p < c) {
+        const int bp = S.rows_blk[rb + p];
+        const int I = S.blk_sn[bp];
+        const int64_t base = S.blk_rel[bp] - S.blk_pb[bp];
+        const int rp = S.relidx[base + p];  // local column of R_K[p] in I
+        const int sI = S.sn_width[I], cI = S.sn_c[I];
+        rpan[pl] = io + S.sn_off[I] + (int64_t)sI * sI + (int64_t)cI * sI + (int64_t)rp * cI;
+        rrel[pl] = base;
+        rblk[pl] = bp;
+      } else {
+        rblk[pl] = -1;
       }
     }
+    __syncthreads();
+    // entries on or below the block diagonal: lanes along p (down a column)
+#pragma unroll 4
+    for (int i = 0; i < kGT * kGT / kSliceThreads; i++) {
+      const int ql = warp + 8 * (i >> 1), pl = lane + 32 * (i & 1);
+      const int p = p0 + pl, q = q0 + ql;
+      T v = sc_zero(T());
+      const int bp = rblk[pl], bq = cblk[ql];
+      if (p < c && q < c) {
+        if (bp < bq) continue;  // the upper pass writes it
+        const int64_t ri = crel[ql] + p;
+        bool ok = true;
+        if (S.check) ok = ri >= 0 && ri < S.relidx_size;
+        const int64_t slot = ok ? (bp == bq ? cdiag[ql] : cpan[ql]) + S.relidx[ri] : 0;
+        if (S.check) ok = ok && slot >= io && slot < io + S.storage;
+        if (ok)
+          v = store[slot];
+        else
+          set_error(S.err, DEV_CHECK, K);
+      }
+      tile[pl * kGTPad + ql] = v;
+    }
+    // entries above it: lanes along q (down a column of a U^T panel)
+#pragma unroll 4
+    for (int i = 0; i < kGT * kGT / kSliceThreads; i++) {
+      const int pl = warp + 8 * (i >> 1), ql = lane + 32 * (i & 1);
+      const int p = p0 + pl, q = q0 + ql;
+      if (p >= c || q >= c || rblk[pl] >= cblk[ql]) continue;
+      const int64_t ri = rrel[pl] + q;
+      bool ok = true;
+      if (S.check) ok = ri >= 0 && ri < S.relidx_size;
+      const int64_t slot = ok ? rpan[pl] + S.relidx[ri] : 0;
+      if (S.check) ok = ok && slot >= io && slot < io + S.storage;
+      T v = sc_zero(T());
+      if (ok)
+        v = store[slot];
+      else
+        set_error(S.err, DEV_CHECK, K);
+      tile[pl * kGTPad + ql] = v;
+    }
+    __syncthreads();
+    const SliceDesc& dr = descs[task.dr];
+    if (MAXIMA) {
+      // row maxima (threads 0-63) and column maxima (threads 64-127)
+      if (tid < kGT) {
+        unsigned long long m = 0;
+        for (int ql = 0; ql < kGT; ql++) m = max(m, abs_bits_max(tile[tid * kGTPad + ql]));
+        if (p0 + tid < c && m) atomicMax(dr.maxbits + p0 + tid, m);
+      } else if (tid < 2 * kGT && task.dc >= 0) {
+        const int ql = tid - kGT;
+        unsigned long long m = 0;
+        for (int pl = 0; pl < kGT; pl++) m = max(m, abs_bits_max(tile[pl * kGTPad + ql]));
+        if (q0 + ql < c && m) atomicMax(descs[task.dc].maxbits + q0 + ql, m);
+      }
+    } else {
+      // work item of the slicing: row rl, 8 values of K group kg of a 32-wide K block
+      const int ci = tid >> 3, rr = tid & 7;
+      const int rl = (ci >> 2) * 8 + rr, kg = ci & 3;
+      const int k32c = (c + 31) / 32;  // K blocks of one part
+      constexpr int kParts = sizeof(T) == 16 ? 2 : 1;
+      for (int layout = 0; layout < 2; layout++) {
+        if (layout == 1 && task.dc < 0) break;
+        const SliceDesc& d = layout == 0 ? dr : descs[task.dc];
+        const int r0 = layout == 0 ? p0 : q0;   // rows of this layout's tile
+        const int kq0 = layout == 0 ? q0 : p0;  // its K offset
+        const int rblk64 = r0 / 64;
+        const int r = r0 + rl;
+        const int e = r < c ? exp_of_max(d.maxbits[r]) : 0;
+        if (kq0 == 0 && kg == 0 && r < c) d.exps[r] = e;
+        const int64_t slice_stride = (int64_t)d.R64 * d.K32 * (kTileBytes / 2);
+        for (int kbl = 0; kbl < kGT / 32; kbl++) {
+          const int kb = kq0 / 32 + kbl;
+          if (kb >= k32c) break;
+          for (int part = 0; part < kParts; part++) {
+            double x[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+              const int kl = kbl * 32 + kg * 8 + j;
+              const T v = layout == 0 ? tile[rl * kGTPad + kl] : tile[kl * kGTPad + rl];
+              x[j] = part_of(v, part);
+            }
+            const int kbp = kb + part * k32c;
+            write_digits(x, e, d.S,
+                         d.out + ((int64_t)rblk64 * d.K32 + kbp) * (kTileBytes / 2) + tid * 8,
+                         slice_stride);
+          }
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -552,6 +757,12 @@ __global__ void zero_kernel(const CopySeg* __restrict__ segs, int nseg) {
 
 cudaError_t prepare_ozaki_kernels() {
   cudaError_t e;
+  e = cudaFuncSetAttribute(gslice_kernel<cdouble, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)gslice_smem<cdouble>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gslice_kernel<cdouble, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)gslice_smem<cdouble>());
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(ozaki_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem<4>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(ozaki_gemm_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem<5>());
@@ -568,6 +779,31 @@ void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bo
     slice_max_kernel<<<grid, kSliceThreads, 0, st>>>(descs, tasks, ntasks);
   else
     slice_kernel<<<grid, kSliceThreads, 0, st>>>(descs, tasks, ntasks);
+}
+
+void launch_gslice(int dtype, const SymDev& S, const void* store, const SliceDesc* descs,
+                   const GTileTask* gtasks, int ngt, const SliceTask* stasks, int nst, bool maxima,
+                   cudaStream_t st) {
+  const int ntasks = ngt + nst;
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  if (dtype == DT_F64) {
+    const size_t sm = gslice_smem<double>();
+    if (maxima)
+      gslice_kernel<double, true><<<grid, kSliceThreads, sm, st>>>(
+          S, (const double*)store, descs, gtasks, ngt, stasks, nst);
+    else
+      gslice_kernel<double, false><<<grid, kSliceThreads, sm, st>>>(
+          S, (const double*)store, descs, gtasks, ngt, stasks, nst);
+  } else {
+    const size_t sm = gslice_smem<cdouble>();
+    if (maxima)
+      gslice_kernel<cdouble, true><<<grid, kSliceThreads, sm, st>>>(
+          S, (const cdouble*)store, descs, gtasks, ngt, stasks, nst);
+    else
+      gslice_kernel<cdouble, false><<<grid, kSliceThreads, sm, st>>>(
+          S, (const cdouble*)store, descs, gtasks, ngt, stasks, nst);
+  }
 }
 
 void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,

@@ -243,3 +243,32 @@ def test_plan_cache_round_trip_host_only():
     h.plan_set([], ps.PREC_OZAKI_FP16)
     assert h.plan_get(ps.PREC_OZAKI_FP16) == []
     assert h.plan_get(ps.PREC_FP64) == [(0, 1, 2)]
+
+
+def test_group_is_the_direct_sum_host_only():
+    """pselinv_group through the C ABI: the grouped handle's structure is that
+    of the direct sum of the members' patterns (orderings shifted), and the
+    members stay usable."""
+    a = gen.conv_diff_2d(7, 1, max_sn=16)
+    b = gen.random_struct_sym(40, 0.1, 2, max_sn=16)
+    c = gen.tridiagonal(9, 3, max_sn=16)
+    members = [ps.SelInv.from_problem(q, host_only=True, max_supernode=16) for q in (a, b, c)]
+    g = ps.SelInv.group(members, max_supernode=16, host_only=True)
+    n_off = np.cumsum([0, a.n, b.n])
+    z_off = np.cumsum([0, a.nnz, b.nnz])
+    cp = np.concatenate([[0]] + [q.colptr[1:] + z for q, z in zip((a, b, c), z_off)])
+    ri = np.concatenate([q.rowind + o for q, o in zip((a, b, c), n_off)])
+    pm = np.concatenate([q.perm + o for q, o in zip((a, b, c), n_off)])
+    d = ps.SelInv(int(n_off[-1] + c.n), cp, ri, pm, max_supernode=16, host_only=True)
+    sg, sd = g.structure(), d.structure()
+    for key in ("n", "nsuper", "nlevels", "storage_size", "nnz_a"):
+        assert sg[key] == sd[key], key
+    for key in ("perm", "sn_width", "sn_parent", "sn_depth", "rows_ptr", "rows", "value_map"):
+        assert np.array_equal(sg[key], sd[key]), key
+    assert members[1].structure()["n"] == b.n  # members untouched
+    lib = ps.load_library()
+    import ctypes
+    out = ctypes.c_void_p()
+    assert lib.pselinv_group(None, 0, None, ctypes.byref(out)) == -1
+    for h in members + [g, d]:
+        h.close()

@@ -174,3 +174,12 @@ def test_fp64_product_kernels_match_oracle(torch, name, make, cfg):
             assert err < tol, (rep, prec, err)
     h.sync()
     h.close()
+
+
+@pytest.mark.parametrize("name,maker", [CASES[3], COMPLEX_CASES[0]], ids=["dg", "stencil27_c"])
+def test_split_checked_maps_match_oracle(torch, name, maker):
+    """The gather of Ainv_CC with every index-map read bounds-checked
+    (check_level = 1): same result, no error reported (h.sync())."""
+    p = maker()
+    st, sn, pa, sn64 = run_split(torch, p, check_level=1)
+    compare_full(p, st, sn, 0, 20, tol=TOL_SPLIT)
