@@ -186,10 +186,13 @@ int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind,
  * and R_U(K)).  Results: pselinv_get_selected(PATTERN_A) returns, for
  * entry p of A at row y = rowind[p] of column x, the selected entry
  * (A^{-1})_{x,y} (Eq. sel_entries: the transposed position), and
- * pselinv_trace / pselinv_weighted_sum use the same entries.  Only
- * PSELINV_PREC_FP64 is available for these handles (PSELINV_ERR_UNSUPPORTED
- * otherwise); opts->symmetric must be 0.  Other errors as pselinv_analyze
- * (PSELINV_ERR_ARG for an invalid ordering or pattern). */
+ * pselinv_trace / pselinv_weighted_sum use the same entries.  Both
+ * precisions are available; with PSELINV_PREC_OZAKI_FP16 the normalisation
+ * stays FP64 (opts->split_normalise is ignored) and G_K = Ainv(R_U, R_L) is
+ * gathered and sliced for steps 3 and 5 as for the other handles.
+ * opts->symmetric must be 0; pselinv_group, pselinv_partition and the block
+ * transfers return PSELINV_ERR_UNSUPPORTED for these handles.  Other errors
+ * as pselinv_analyze (PSELINV_ERR_ARG for an invalid ordering or pattern). */
 int pselinv_analyze_general(int64_t n, const int64_t* colptr, const int64_t* rowind,
                             const int64_t* rperm, const int64_t* cperm, const pselinv_opts* opts,
                             pselinv_t* out);

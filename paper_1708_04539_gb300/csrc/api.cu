@@ -202,6 +202,53 @@ int upload_structure(pselinv_ctx* h) {
   upload(host, o_brel, H.blk_rel);
   upload(host, o_rel, H.relidx);
   upload(host, o_vmap, H.value_map);
+  // per-position storage bases of the gathers of G_K (fused gather and
+  // slicing): the column side over R_L(K) (= R_K), the row side over R_U(K)
+  size_t o_cd = 0, o_cp = 0, o_cr = 0, o_cs = 0, o_rp = 0, o_rr = 0, o_rs = 0;
+  {
+    auto cl = [&](int64_t J) { return H.rows_ptr[J + 1] - H.rows_ptr[J]; };
+    auto cu = [&](int64_t J) {
+      return H.general ? H.urows_ptr[J + 1] - H.urows_ptr[J] : cl(J);
+    };
+    const size_t nl = H.rows.size();
+    std::vector<int64_t> cd(nl), cp(nl), cr(nl);
+    std::vector<int32_t> cs(nl);
+    for (int64_t k = 0; k < H.ns; k++)
+      for (int64_t p = H.rows_ptr[k]; p < H.rows_ptr[k + 1]; p++) {
+        const int32_t b = H.rows_blk[p];
+        const int64_t J = H.blk_sn[b], sJ = H.sn_width[J], t = H.rows[p] - H.sn_first[J];
+        cd[p] = H.sn_offset[J] + t * sJ;
+        // Ainv(x, y), x after J: L panel of J (symmetric) or its U^T panel
+        // (rows R_U(J), general)
+        cp[p] = H.general ? H.sn_offset[J] + sJ * sJ + cl(J) * sJ + t * cu(J)
+                          : H.sn_offset[J] + sJ * sJ + t * cl(J);
+        cr[p] = H.blk_rel[b] - (H.general ? H.blk_q0[b] : H.blk_pb[b]);
+        cs[p] = (int32_t)J;
+      }
+    const std::vector<int64_t>& uptr = H.general ? H.urows_ptr : H.rows_ptr;
+    const std::vector<int64_t>& urows = H.general ? H.urows : H.rows;
+    const size_t nu = urows.size();
+    std::vector<int64_t> rp(nu), rr(nu);
+    std::vector<int32_t> rs(nu);
+    for (int64_t k = 0; k < H.ns; k++)
+      for (int64_t p = uptr[k]; p < uptr[k + 1]; p++) {
+        const int32_t b = H.general ? H.urows_blk[p] : H.rows_blk[p];
+        const int64_t I = H.general ? H.ublk_sn[b] : H.blk_sn[b];
+        const int64_t sI = H.sn_width[I], t = urows[p] - H.sn_first[I];
+        // Ainv(x, y), y after I: U^T panel of I (symmetric) or its L panel
+        rp[p] = H.general ? H.sn_offset[I] + sI * sI + t * cl(I)
+                          : H.sn_offset[I] + sI * sI + cl(I) * sI + t * cl(I);
+        rr[p] = H.general ? H.ublk_rel[b] - H.ublk_q0[b] : H.blk_rel[b] - H.blk_pb[b];
+        rs[p] = (int32_t)I;
+      }
+    upload(host, o_cd, cd);
+    upload(host, o_cp, cp);
+    upload(host, o_cr, cr);
+    upload(host, o_cs, cs);
+    upload(host, o_rp, rp);
+    upload(host, o_rr, rr);
+    upload(host, o_rs, rs);
+  }
   // general patterns: the second row structure and its maps
   size_t o_cu = 0, o_urptr = 0, o_lrows = 0, o_urows = 0, o_urblk = 0, o_q0 = 0, o_ubsn = 0,
          o_ubrel = 0, o_ubq0 = 0, o_inv = 0;
@@ -244,6 +291,13 @@ int upload_structure(pselinv_ctx* h) {
   S.err = h->derr;
   S.out_map = S.value_map;
   S.general = H.general ? 1 : 0;
+  S.col_diag = (const int64_t*)(b + o_cd);
+  S.col_pan = (const int64_t*)(b + o_cp);
+  S.col_rel = (const int64_t*)(b + o_cr);
+  S.col_sn = (const int32_t*)(b + o_cs);
+  S.row_pan = (const int64_t*)(b + o_rp);
+  S.row_rel = (const int64_t*)(b + o_rr);
+  S.row_sn = (const int32_t*)(b + o_rs);
   if (H.general) {
     S.sn_cu = (const int32_t*)(b + o_cu);
     S.urows_ptr = (const int64_t*)(b + o_urptr);
@@ -389,7 +443,7 @@ size_t ozaki_level_bytes(const HostSym& H, int64_t nb, int S, size_t es) {
     size_t b = 0;
     for (int64_t i = H.level_ptr[d]; i < H.level_ptr[d + 1]; i++) {
       const int64_t K = H.level_sn[i];
-      b += ozaki_sn_bytes(H.sn_width[K], H.rows_ptr[K + 1] - H.rows_ptr[K], S, es);
+      b += ozaki_sn_bytes(H.sn_width[K], std::max(cK(H, K), cU(H, K)), S, es);
     }
     mx = std::max(mx, b * (size_t)nb);
   }
@@ -435,7 +489,8 @@ size_t selinv_main_bytes(const HostSym& H, int64_t nb, size_t es) {
 size_t maxima_bytes(const HostSym& H, int64_t nb) {
   size_t b = 0;
   for (int64_t K = 0; K < H.ns; K++)
-    if (cK(H, K) > 0) b += align256((size_t)(2 * cK(H, K) + 3 * H.sn_width[K]) * 8 * nb + 8);
+    if (cK(H, K) > 0 || cU(H, K) > 0)
+      b += align256((size_t)(cK(H, K) + cU(H, K) + 3 * H.sn_width[K]) * 8 * nb + 8);
   return b;
 }
 
@@ -811,9 +866,12 @@ void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool
   set_ozaki_ksplit(descs, ks, force_atomic);
   for (size_t d = 0; d < descs.size(); d++) {
     OzDesc& g = descs[d];
+    // the N tiles of one M block next to each other: they run in the same
+    // wave and read the same A slices (the large operand, G), so A comes from
+    // DRAM once and from L2 for the others
     for (int k = 0; k < g.ksplit; k++)
-      for (int tn = 0; tn < ceil_div(g.N, 64); tn++)
-        for (int tm = 0; tm < ceil_div(g.M, 128); tm++) tasks.push_back({(int)d, tm, tn, k});
+      for (int tm = 0; tm < ceil_div(g.M, 128); tm++)
+        for (int tn = 0; tn < ceil_div(g.N, 64); tn++) tasks.push_back({(int)d, tm, tn, k});
     flops += 2.0 * g.M * g.N * (double)g.K32 * 32;
     // slices of both operands read once, the FP64 result written (read too
     // when accumulated)
@@ -988,8 +1046,16 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   int64_t nmax = 0;
   for (int64_t b = 0; b < nb; b++)
     for (int64_t K : grp)
-      if (H.rows_ptr[K + 1] > H.rows_ptr[K])
-        nmax += 2 * (H.rows_ptr[K + 1] - H.rows_ptr[K]) + 3 * H.sn_width[K];
+      if (cK(H, K) > 0 && cU(H, K) > 0) nmax += cK(H, K) + cU(H, K) + 3 * H.sn_width[K];
+  std::vector<CopySeg> zside;  // general patterns: a panel whose products are empty
+  for (int64_t b = 0; b < nb; b++)
+    for (int64_t K : grp)
+      if ((cK(H, K) == 0) != (cU(H, K) == 0)) {
+        const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
+        zside.push_back({nullptr, h->ainv + so + (size_t)H.sn_width[K] * H.sn_width[K] * es,
+                         (cK(H, K) + cU(H, K)) * H.sn_width[K] * (cplx ? 2 : 1)});
+      }
+  add_zero_step(P, zside, lev);
   if (nmax == 0) return;  // roots only (c = 0): nothing after D_K
   unsigned long long* maxbase = (unsigned long long*)(h->scratch + max_cursor);
   max_cursor += align256((size_t)nmax * 8 + 8);
@@ -1001,27 +1067,32 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   };
   for (int64_t b = 0; b < nb; b++)
     for (int64_t K : grp) {
-      const int s = (int)H.sn_width[K], c = (int)(H.rows_ptr[K + 1] - H.rows_ptr[K]);
-      if (c == 0) continue;
+      // c: rows of the L panel (R_L(K) = R_K), cu: rows of the U^T panel
+      // (R_U(K) for a general pattern, else c); G = Ainv(R_U, R_L) is cu x c
+      const int s = (int)H.sn_width[K], c = (int)cK(H, K), cu = (int)cU(H, K);
+      if (c == 0 || cu == 0) continue;
       const int64_t m0 = moff;
-      moff += 2 * c + 3 * s;
+      moff += cu + c + 3 * s;
       const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
       const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
       // symmetric A: G is symmetric and Uhat = Lhat^T, so step 5's product is
       // the transpose of step 3's (a copy) and step 4 uses Lhat
-      SliceDesc gr = ob.slice(nullptr, c, SLICE_ROWS, c, c);  // G by rows (from the gather)
+      SliceDesc gr = ob.slice(nullptr, cu, SLICE_ROWS, cu, c);  // G by rows (from the gather)
       gr.maxbits = maxbase + m0;
       SliceDesc lh = ob.slice(h->nf + lo, c, SLICE_COLS, s, c);
-      lh.maxbits = maxbase + m0 + 2 * c;
+      lh.maxbits = maxbase + m0 + cu + c;
       SliceDesc gc = gr, uh = lh;
       if (!sym) {
-        gc = ob.slice(nullptr, c, SLICE_COLS, c, c);  // G by columns
-        gc.maxbits = maxbase + m0 + c;
-        uh = ob.slice(h->nf + uo, c, SLICE_COLS, s, c);
-        uh.maxbits = maxbase + m0 + 2 * c + s;
+        gc = ob.slice(nullptr, c, SLICE_COLS, c, cu);  // G by columns
+        gc.maxbits = maxbase + m0 + cu;
+        uh = ob.slice(h->nf + uo, cu, SLICE_COLS, s, cu);
+        uh.maxbits = maxbase + m0 + cu + c + s;
       }
-      SliceDesc ak = ob.slice(h->ainv + lo, c, SLICE_COLS, s, c);
-      ak.maxbits = maxbase + m0 + 2 * c + 2 * s;
+      // Ainv(R_U, K): the U^T panel of a general pattern, the L panel otherwise
+      char* ainv_uk = H.general ? h->ainv + uo : h->ainv + lo;
+      char* ainv_kl = H.general ? h->ainv + lo : h->ainv + uo;
+      SliceDesc ak = ob.slice(ainv_uk, cu, SLICE_COLS, s, cu);
+      ak.maxbits = maxbase + m0 + cu + c + 2 * s;
       const int ir = (int)gd.size();
       gd.push_back(gr);
       const int ic = sym ? -1 : (int)gd.size();
@@ -1033,16 +1104,16 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
         gd.push_back(uh);
       }
       for (int tq = 0; tq < ceil_div(c, 64); tq++)
-        for (int tp = 0; tp < ceil_div(c, 64); tp++)
+        for (int tp = 0; tp < ceil_div(cu, 64); tp++)
           gt.push_back({(int)b, (int)K, tp, tq, ir, ic});
       sl2.push_back(ak);
-      // step 3: Ainv(C,K) = -G Lhat;  step 5: Ainv(K,C)^T = -G^T Uhat^T
-      push_product(main, gr, lh, h->ainv + lo, c, c, s);
-      if (!sym) push_product(main, gc, uh, h->ainv + uo, c, c, s);
+      // step 3: Ainv(R_U, K) = -G Lhat;  step 5: Ainv(K, R_L)^T = -G^T Uhat^T
+      push_product(main, gr, lh, ainv_uk, cu, cu, s);
+      if (!sym) push_product(main, gc, uh, ainv_kl, c, c, s);
       else mirror.push_back({h->ainv + lo, h->ainv + uo, (int64_t)c * s});
-      // step 4: Ainv(K,K) = D_K - Uhat Ainv(C,K)
+      // step 4: Ainv(K,K) = D_K - Uhat Ainv(R_U, K)
       push_product(dg, uh, ak, h->ainv + so, s, s, s);
-      zero.push_back({nullptr, h->ainv + lo, (int64_t)2 * c * s * (cplx ? 2 : 1)});
+      zero.push_back({nullptr, h->ainv + lo, (int64_t)(c + cu) * s * (cplx ? 2 : 1)});
     }
   if (gt.empty()) return;
   const int prec = PSELINV_PREC_OZAKI_FP16;
@@ -1270,7 +1341,7 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
     if (precision == PSELINV_PREC_OZAKI_FP16)
       mode = tuned_value(h, precision, (int)lev, 3, level_product_flops(h, (int)lev) < 2e8 ? 1 : 0);
     const bool split_level = precision == PSELINV_PREC_OZAKI_FP16 && mode == 0;
-    add_normalize((int)lev, split_level && h->opts.split_normalise != 0);
+    add_normalize((int)lev, split_level && h->opts.split_normalise != 0 && !H.general);
     const size_t first_main = P.steps.size();
     // groups: the whole level, or one supernode at a time
     std::vector<std::vector<int64_t>> groups;
@@ -1763,7 +1834,6 @@ int pselinv_selinv(pselinv_t h, int precision, void* stream) {
   if (!h || !h->factored) return PSELINV_ERR_ARG;
   if (precision < 0) precision = h->opts.precision;
   if (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16) return PSELINV_ERR_ARG;
-  if (h->H.general && precision != PSELINV_PREC_FP64) return PSELINV_ERR_UNSUPPORTED;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;
@@ -2125,7 +2195,6 @@ extern "C" {
 int pselinv_tune(pselinv_t h, int precision, int mode, pselinv_model_t model, void* stream) {
   if (!h || !h->factored || (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16))
     return PSELINV_ERR_ARG;
-  if (h->H.general && precision != PSELINV_PREC_FP64) return PSELINV_ERR_UNSUPPORTED;
   CK(cudaSetDevice(h->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int sched = h->opts.schedule == PSELINV_SCHED_PER_SUPERNODE ? 1 : 0;

@@ -77,6 +77,21 @@ struct SymDev {
   // slot of the selected entry returned for each input entry (extraction,
   // weighted sums): value_map for structurally symmetric handles
   const int64_t* out_map;
+  // Storage bases of the gather of G_K = Ainv(R_U(K), R_L(K)) (R_U = R_L =
+  // R_K for structurally symmetric handles), precomputed per position.
+  // Column side, position q of R_L(K) (index rows_ptr[K] + q), y = R_L[q]
+  // in supernode J = col_sn: Ainv(x, y) for x in J or later lies at
+  // (x in J ? col_diag : col_pan)[q] + relidx[col_rel[q] + p], p the
+  // position of x in R_U(K).  Row side, position p of R_U(K) (index
+  // urows_ptr[K] + p, or rows_ptr[K] + p), x = R_U[p] in supernode I =
+  // row_sn: Ainv(x, y) for y after I lies at row_pan[p] + relidx[row_rel[p] + q].
+  const int64_t* col_diag;
+  const int64_t* col_pan;
+  const int64_t* col_rel;
+  const int32_t* col_sn;
+  const int64_t* row_pan;
+  const int64_t* row_rel;
+  const int32_t* row_sn;
   // general patterns (general = 1; null for structurally symmetric
   // handles): sn_c, rows_ptr, rows_blk and blk_* describe R_L(K) (the L
   // panel's rows), sn_cu, urows_ptr, urows_blk and ublk_* R_U(K) (the U^T

@@ -133,24 +133,36 @@ __device__ __forceinline__ void slice_max_task(const SliceDesc& d, const SliceTa
 
 // The S balanced base-128 digits of 8 values x of one row with exponent e,
 // written as the 16 bytes [16 tid, 16 tid + 16) of the 4 KB tile of every
-// slice at `dst` (slices `slice_stride` halves apart).
+// slice at `dst` (slices `slice_stride` halves apart).  Q (|Q| <= 2^{7S})
+// is split once into its low 7 L bits (L = S / 2 digits, non-negative) and
+// the rest, so that the digits come from 32-bit arithmetic: the low digits
+// leave a carry of 0 or 1 into the high part.  The digits are the same as
+// those of the 64-bit recurrence a = ((Q + 64) & 127) - 64, Q = (Q - a) / 128.
 __device__ __forceinline__ void write_digits(const double (&x)[8], int e, int S, __half* dst,
                                              int64_t slice_stride) {
   const int sh0 = 7 * S - e;
-  long long q[8];
+  const int L = S / 2;
+  int lo[8], hi[8];
 #pragma unroll
-  for (int j = 0; j < 8; j++) q[j] = fixed_point(x[j], sh0);
+  for (int j = 0; j < 8; j++) {
+    const long long q = fixed_point(x[j], sh0);
+    lo[j] = (int)(q & ((1ll << (7 * L)) - 1));
+    hi[j] = (int)(q >> (7 * L));
+  }
   // balanced base-128 digits from the least significant slice upwards
   for (int s = S - 1; s >= 0; s--) {
     __align__(16) __half h[8];
+    const bool low = s >= S - L;
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-      long long a = q[j];
+      int& v = low ? lo[j] : hi[j];
+      int a = v;
       if (s > 0) {
-        a = ((q[j] + 64) & 127) - 64;
-        q[j] = (q[j] - a) >> 7;
+        a = ((v + 64) & 127) - 64;
+        v = (v - a) >> 7;
       }
-      h[j] = __int2half_rn((int)a);
+      if (s == S - L) hi[j] += lo[j];  // carry of the low digits
+      h[j] = __int2half_rn(a);
     }
     *reinterpret_cast<uint4*>(dst + s * slice_stride) = *reinterpret_cast<uint4*>(h);
   }
@@ -254,110 +266,143 @@ gslice_kernel(SymDev S, const T* __restrict__ store, const SliceDesc* __restrict
     }
     const GTileTask task = gtasks[t];
     const int K = task.K;
-    const int c = S.sn_c[K];
-    const int64_t rb = S.rows_ptr[K];
+    // G_K = Ainv(R_U(K), R_L(K)): cu rows (positions p), cl columns (q);
+    // R_U = R_L = R_K for a structurally symmetric handle
+    const int cl = S.sn_c[K], cu = S.general ? S.sn_cu[K] : cl;
+    const int64_t rb = S.rows_ptr[K], rbU = S.general ? S.urows_ptr[K] : rb;
     const int64_t io = (int64_t)task.inst * S.storage;
     const int p0 = task.tp * kGT, q0 = task.tq * kGT;
-    // per-column and per-row storage bases of the tile
+    // per-column and per-row storage bases of the tile (precomputed per
+    // position: independent loads, no chain through the block maps); the
+    // supernode of each row and column decides where an entry lies
     if (tid < kGT) {
       const int q = q0 + tid;
-      if (q < c) {
-        const int bq = S.rows_blk[rb + q];
-        const int J = S.blk_sn[bq];
-        const int64_t base = S.blk_rel[bq] - S.blk_pb[bq];
-        const int rq = S.relidx[base + q];  // local column of R_K[q] in J
-        const int sJ = S.sn_width[J];
-        cdiag[tid] = io + S.sn_off[J] + (int64_t)rq * sJ;
-        cpan[tid] = io + S.sn_off[J] + (int64_t)sJ * sJ + (int64_t)rq * S.sn_c[J];
-        crel[tid] = base;
-        cblk[tid] = bq;
+      if (q < cl) {
+        cdiag[tid] = io + S.col_diag[rb + q];
+        cpan[tid] = io + S.col_pan[rb + q];
+        crel[tid] = S.col_rel[rb + q];
+        cblk[tid] = S.col_sn[rb + q];
       } else {
         cblk[tid] = 0x7FFFFFFF;
       }
     } else if (tid < 2 * kGT) {
       const int pl = tid - kGT, p = p0 + pl;
-      if (p < c) {
-        const int bp = S.rows_blk[rb + p];
-        const int I = S.blk_sn[bp];
-        const int64_t base = S.blk_rel[bp] - S.blk_pb[bp];
-        const int rp = S.relidx[base + p];  // local column of R_K[p] in I
-        const int sI = S.sn_width[I], cI = S.sn_c[I];
-        rpan[pl] = io + S.sn_off[I] + (int64_t)sI * sI + (int64_t)cI * sI + (int64_t)rp * cI;
-        rrel[pl] = base;
-        rblk[pl] = bp;
+      if (p < cu) {
+        rpan[pl] = io + S.row_pan[rbU + p];
+        rrel[pl] = S.row_rel[rbU + p];
+        rblk[pl] = S.row_sn[rbU + p];
       } else {
         rblk[pl] = -1;
       }
     }
     __syncthreads();
-    // entries on or below the block diagonal: lanes along p (down a column)
-#pragma unroll 4
-    for (int i = 0; i < kGT * kGT / kSliceThreads; i++) {
-      const int ql = warp + 8 * (i >> 1), pl = lane + 32 * (i & 1);
-      const int p = p0 + pl, q = q0 + ql;
-      T v = sc_zero(T());
-      const int bp = rblk[pl], bq = cblk[ql];
-      if (p < c && q < c) {
-        if (bp < bq) continue;  // the upper pass writes it
-        const int64_t ri = crel[ql] + p;
-        bool ok = true;
-        if (S.check) ok = ri >= 0 && ri < S.relidx_size;
-        const int64_t slot = ok ? (bp == bq ? cdiag[ql] : cpan[ql]) + S.relidx[ri] : 0;
-        if (S.check) ok = ok && slot >= io && slot < io + S.storage;
-        if (ok)
-          v = store[slot];
-        else
+    constexpr int kPer = kGT * kGT / kSliceThreads;  // entries per thread and pass
+    // entries whose row lies in the column's supernode or later: lanes along
+    // p (down a column); all index loads of the thread first, then all
+    // value loads
+    {
+      int rel[kPer];
+      bool use[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; i++) {
+        const int ql = warp + 8 * (i >> 1), pl = lane + 32 * (i & 1);
+        const int p = p0 + pl, q = q0 + ql;
+        use[i] = p < cu && q < cl && rblk[pl] >= cblk[ql];
+        int64_t ri = crel[ql] + p;
+        if (S.check && use[i] && (ri < 0 || ri >= S.relidx_size)) {
           set_error(S.err, DEV_CHECK, K);
+          use[i] = false;
+        }
+        rel[i] = use[i] ? S.relidx[ri] : 0;
       }
-      tile[pl * kGTPad + ql] = v;
+      T v[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; i++) {
+        const int ql = warp + 8 * (i >> 1), pl = lane + 32 * (i & 1);
+        const int64_t slot = (rblk[pl] == cblk[ql] ? cdiag[ql] : cpan[ql]) + rel[i];
+        if (S.check && use[i] && (slot < io || slot >= io + S.storage)) {
+          set_error(S.err, DEV_CHECK, K);
+          use[i] = false;
+        }
+        v[i] = use[i] ? store[slot] : sc_zero(T());
+      }
+#pragma unroll
+      for (int i = 0; i < kPer; i++) {
+        const int ql = warp + 8 * (i >> 1), pl = lane + 32 * (i & 1);
+        if (p0 + pl >= cu || q0 + ql >= cl || rblk[pl] >= cblk[ql])  // upper pass writes the rest
+          tile[pl * kGTPad + ql] = v[i];
+      }
     }
-    // entries above it: lanes along q (down a column of a U^T panel)
-#pragma unroll 4
-    for (int i = 0; i < kGT * kGT / kSliceThreads; i++) {
-      const int pl = warp + 8 * (i >> 1), ql = lane + 32 * (i & 1);
-      const int p = p0 + pl, q = q0 + ql;
-      if (p >= c || q >= c || rblk[pl] >= cblk[ql]) continue;
-      const int64_t ri = rrel[pl] + q;
-      bool ok = true;
-      if (S.check) ok = ri >= 0 && ri < S.relidx_size;
-      const int64_t slot = ok ? rpan[pl] + S.relidx[ri] : 0;
-      if (S.check) ok = ok && slot >= io && slot < io + S.storage;
-      T v = sc_zero(T());
-      if (ok)
-        v = store[slot];
-      else
-        set_error(S.err, DEV_CHECK, K);
-      tile[pl * kGTPad + ql] = v;
+    // the others: lanes along q (down a column of a panel of the row's supernode)
+    {
+      int rel[kPer];
+      bool use[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; i++) {
+        const int pl = warp + 8 * (i >> 1), ql = lane + 32 * (i & 1);
+        const int p = p0 + pl, q = q0 + ql;
+        use[i] = p < cu && q < cl && rblk[pl] < cblk[ql];
+        const int64_t ri = rrel[pl] + q;
+        if (S.check && use[i] && (ri < 0 || ri >= S.relidx_size)) {
+          set_error(S.err, DEV_CHECK, K);
+          use[i] = false;
+        }
+        rel[i] = use[i] ? S.relidx[ri] : 0;
+      }
+      T v[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; i++) {
+        const int pl = warp + 8 * (i >> 1);
+        const int64_t slot = rpan[pl] + rel[i];
+        if (S.check && use[i] && (slot < io || slot >= io + S.storage)) {
+          set_error(S.err, DEV_CHECK, K);
+          use[i] = false;
+        }
+        v[i] = use[i] ? store[slot] : sc_zero(T());
+      }
+#pragma unroll
+      for (int i = 0; i < kPer; i++) {
+        const int pl = warp + 8 * (i >> 1), ql = lane + 32 * (i & 1);
+        if (p0 + pl < cu && q0 + ql < cl && rblk[pl] < cblk[ql]) tile[pl * kGTPad + ql] = v[i];
+      }
     }
     __syncthreads();
     const SliceDesc& dr = descs[task.dr];
     if (MAXIMA) {
-      // row maxima (threads 0-63) and column maxima (threads 64-127)
-      if (tid < kGT) {
-        unsigned long long m = 0;
-        for (int ql = 0; ql < kGT; ql++) m = max(m, abs_bits_max(tile[tid * kGTPad + ql]));
-        if (p0 + tid < c && m) atomicMax(dr.maxbits + p0 + tid, m);
-      } else if (tid < 2 * kGT && task.dc >= 0) {
-        const int ql = tid - kGT;
-        unsigned long long m = 0;
-        for (int pl = 0; pl < kGT; pl++) m = max(m, abs_bits_max(tile[pl * kGTPad + ql]));
-        if (q0 + ql < c && m) atomicMax(descs[task.dc].maxbits + q0 + ql, m);
+      // row maxima, then column maxima: four threads (a quarter of the
+      // tile's width each, neighbours in one warp) per row / column
+      const int line = tid >> 2, part = tid & 3;
+      unsigned long long m = 0;
+      for (int i = 0; i < kGT / 4; i++)
+        m = max(m, abs_bits_max(tile[line * kGTPad + part * (kGT / 4) + i]));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      if (part == 0 && p0 + line < cu && m) atomicMax(dr.maxbits + p0 + line, m);
+      if (task.dc >= 0) {
+        m = 0;
+        for (int i = 0; i < kGT / 4; i++)
+          m = max(m, abs_bits_max(tile[(part * (kGT / 4) + i) * kGTPad + line]));
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        if (part == 0 && q0 + line < cl && m) atomicMax(descs[task.dc].maxbits + q0 + line, m);
       }
     } else {
       // work item of the slicing: row rl, 8 values of K group kg of a 32-wide K block
       const int ci = tid >> 3, rr = tid & 7;
       const int rl = (ci >> 2) * 8 + rr, kg = ci & 3;
-      const int k32c = (c + 31) / 32;  // K blocks of one part
       constexpr int kParts = sizeof(T) == 16 ? 2 : 1;
       for (int layout = 0; layout < 2; layout++) {
         if (layout == 1 && task.dc < 0) break;
+        // layout 0: G by rows (rows p, K = q); layout 1: G by columns
         const SliceDesc& d = layout == 0 ? dr : descs[task.dc];
         const int r0 = layout == 0 ? p0 : q0;   // rows of this layout's tile
         const int kq0 = layout == 0 ? q0 : p0;  // its K offset
+        const int nrows = layout == 0 ? cu : cl, nk = layout == 0 ? cl : cu;
+        const int k32c = (nk + 31) / 32;  // K blocks of one part
         const int rblk64 = r0 / 64;
         const int r = r0 + rl;
-        const int e = r < c ? exp_of_max(d.maxbits[r]) : 0;
-        if (kq0 == 0 && kg == 0 && r < c) d.exps[r] = e;
+        const int e = r < nrows ? exp_of_max(d.maxbits[r]) : 0;
+        if (kq0 == 0 && kg == 0 && r < nrows) d.exps[r] = e;
         const int64_t slice_stride = (int64_t)d.R64 * d.K32 * (kTileBytes / 2);
         for (int kbl = 0; kbl < kGT / 32; kbl++) {
           const int kb = kq0 / 32 + kbl;
@@ -481,6 +526,17 @@ __device__ __forceinline__ double scaled_int_to_double(long long v, int e, bool 
   return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -559,7 +615,10 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
       uint32_t g = 0;  // K blocks issued so far (ring position)
       for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
         const OzTask task = tasks[t];
-        const OzDesc d = descs[task.d];
+        const OzDesc* dp = descs + task.d;
+        OzDesc d;  // the fields the copies need
+        d.A = dp->A; d.B = dp->B; d.A_R64 = dp->A_R64; d.B_R64 = dp->B_R64; d.K32 = dp->K32;
+        d.ksplit = dp->ksplit; d.swap_b = dp->swap_b; d.half = dp->half;
         int kb0, nkb;
         task_range(d, task.ks, kb0, nkb);
         const bool a_second = 2 * task.tm + 1 < d.A_R64;
@@ -603,7 +662,9 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
       uint32_t g = 0, q = 0;  // K blocks consumed, chunks completed
       for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
         const OzTask task = tasks[t];
-        const OzDesc d = descs[task.d];
+        const OzDesc* dp = descs + task.d;
+        OzDesc d;  // the fields the MMAs need
+        d.K32 = dp->K32; d.ksplit = dp->ksplit; d.half = dp->half; d.neg_half = dp->neg_half;
         int kb0, nkb;
         task_range(d, task.ks, kb0, nkb);
         for (int i = 0; i < nkb; i++, g++) {
@@ -652,31 +713,53 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
     uint32_t q = 0;
     for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
       const OzTask task = tasks[t];
-      const OzDesc d = descs[task.d];
+      const OzDesc* dp = descs + task.d;
       int kb0, nkb;
-      task_range(d, task.ks, kb0, nkb);
+      task_range(*dp, task.ks, kb0, nkb);
       if (nkb <= 0) continue;
+      // the fields the epilogue needs, as scalars (kept in registers)
+      const int dM = dp->M, dN = dp->N, ldc = dp->ldc, cscale = dp->cscale, coff = dp->coff;
+      const int atomic = dp->atomic;
+      const int* __restrict__ eB = dp->eB;
+      double* __restrict__ Cp = dp->C;
+      const bool neg = dp->alpha < 0.0;  // alpha is +-1: its sign goes into the doubles
       const int nchunks = (nkb + kChunk - 1) / kChunk;
       const int r = task.tm * 128 + quarter * 32 + lane;
       const int nb = task.tn * 64 + hcol * 32;
+      const int ea_row = r < dM ? dp->eA[r] : 0;
       for (int c = 0; c < nchunks; c++, q++) {
         if (!mbar_wait(smem_u32(&bar_acc_full), q & 1) || abort_flag) {
           ok = false;
           break;
         }
         fence_after();
-        // the chunk's S accumulators -> one 64-bit partial sum per output
-        long long part[32];
-#pragma unroll
-        for (int j = 0; j < 32; j++) part[j] = 0;
+        // the chunk's S accumulators -> one 64-bit partial sum per output,
+        // added into the running totals in tensor memory, in two rounds of
+        // 16 outputs (32 TMEM columns of totals) each
 #pragma unroll 1
-        for (int dd = 0; dd < S; dd++) {
-          const int shift = 7 * (S - 1 - dd);
-          uint32_t v[32];
-          tmem_ld32(trow + (uint32_t)(dd * 64), v);
+        for (int g2 = 0; g2 < 2; g2++) {
+          long long part[16];
 #pragma unroll
-          for (int j = 0; j < 32; j++)
-            part[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shift;
+          for (int j = 0; j < 16; j++) part[j] = 0;
+#pragma unroll 1
+          for (int dd = 0; dd < S; dd++) {
+            const int shift = 7 * (S - 1 - dd);
+            uint32_t v[16];
+            tmem_ld16(trow + (uint32_t)(dd * 64 + g2 * 16), v);
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+              part[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shift;
+          }
+          uint32_t tv[32];
+          if (c > 0) tmem_ld32(ttot + (uint32_t)(g2 * 32), tv);
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            long long tt = part[j];
+            if (c > 0) tt += (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
+            tv[2 * j] = (uint32_t)tt;
+            tv[2 * j + 1] = (uint32_t)((unsigned long long)tt >> 32);
+          }
+          tmem_st32(ttot + (uint32_t)(g2 * 32), tv);
         }
         // accumulators read: the MMAs of the next chunk may start
         fence_before();
@@ -684,36 +767,29 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
         if (lane == 0)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_acc_empty))
                        : "memory");
-        // totals in two rounds of 16 values (32 TMEM columns) each
-        const bool last_chunk = c == nchunks - 1;
-        const int ea = (r < d.M ? d.eA[r] : 0) - 14 - 7 * (S - 1);
-        const bool neg = d.alpha < 0.0;  // alpha is +-1: its sign goes into the doubles
-#pragma unroll
+        // (warp-uniform: the tensor-memory loads below need the whole warp)
+        if (c != nchunks - 1) continue;
+        // last chunk: the totals become the FP64 outputs (while the MMAs of
+        // the next task already run)
+        const int ea = ea_row - 14 - 7 * (S - 1);
+#pragma unroll 1
         for (int g2 = 0; g2 < 2; g2++) {
           uint32_t tv[32];
-          if (c > 0) tmem_ld32(ttot + (uint32_t)(g2 * 32), tv);
-          if (!last_chunk) {
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-              long long tt = part[g2 * 16 + j];
-              if (c > 0) tt += (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
-              tv[2 * j] = (uint32_t)tt;
-              tv[2 * j + 1] = (uint32_t)((unsigned long long)tt >> 32);
-            }
-            tmem_st32(ttot + (uint32_t)(g2 * 32), tv);
-          } else if (r < d.M) {
+          tmem_ld32(ttot + (uint32_t)(g2 * 32), tv);
+          if (r < dM) {
 #pragma unroll
             for (int j = 0; j < 16; j++) {
               const int n = nb + g2 * 16 + j;
-              if (n < d.N) {
-                long long tt = part[g2 * 16 + j];
-                if (c > 0) tt += (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
-                const double v = scaled_int_to_double(tt, ea + d.eB[n], neg);
-                double* cp = d.C + (r + (int64_t)n * d.ldc) * d.cscale + d.coff;
-                if (d.atomic) atomicAdd(cp, v); else *cp = v;
+              if (n < dN) {
+                const long long tt =
+                    (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
+                const double v = scaled_int_to_double(tt, ea + eB[n], neg);
+                double* cp = Cp + (r + (int64_t)n * ldc) * cscale + coff;
+                if (atomic) atomicAdd(cp, v); else *cp = v;
               }
             }
           }
+          __syncwarp();  // converged again for the next tensor-memory load
         }
       }
     }

@@ -118,36 +118,75 @@ def plan_ms(h, prec, reps=3):
     return best
 
 
-@pytest.mark.slow
-def test_model_tuning_gains_over_heuristic(torch):
-    """Train on the tuner's records of smaller matrices, then tune a held-out
-    one with the model alone."""
+def _learned_vs_exhaustive(torch, train, held_out, precisions):
+    """Train on the tuner's records of the `train` matrices, tune `held_out`
+    with the model alone; (heuristic, model, exhaustive) ms per precision
+    (best of three launch-by-launch sweeps)."""
     import paper_1708_04539_gb300 as ps
     recs = []
-    for size in (20, 24, 28):
-        q = gen.upwind_3d(size, 80 + size, max_sn=256)
+    for q in train:
         h = ps.SelInv.from_problem(q)
         h.factor(torch.from_numpy(q.values).cuda())
-        for prec in (ps.PREC_FP64, ps.PREC_OZAKI_FP16):
+        for prec in precisions:
             h.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE)
             recs += h.tune_records()
         h.close()
+    import time
     m = ps.CostModel(hidden=32, seed=5)
     m.train(recs, epochs=4000, lr=3e-3)
-    p = gen.upwind_3d(34, 99, max_sn=256)
-    h = ps.SelInv.from_problem(p)
-    h.factor(torch.from_numpy(p.values).cuda())
+    h = ps.SelInv.from_problem(held_out)
+    h.factor(torch.from_numpy(held_out.values).cuda())
     out = {}
-    for prec in (ps.PREC_FP64, ps.PREC_OZAKI_FP16):
+    for prec in precisions:
         h.tune(precision=prec, mode=ps.TUNE_RESET)
         heur = plan_ms(h, prec)
+        t0 = time.perf_counter()
         h.tune(precision=prec, mode=ps.TUNE_MODEL, model=m)
+        t_model = time.perf_counter() - t0
         model = plan_ms(h, prec)
+        t0 = time.perf_counter()
         h.tune(precision=prec, mode=ps.TUNE_EXHAUSTIVE)
+        t_exh = time.perf_counter() - t0
         exh = plan_ms(h, prec)
-        out[prec] = (heur, model, exh)
+        out[prec] = (heur, model, exh, t_model, t_exh)
         print(f"precision {prec}: heuristic {heur:.3f} ms, model {model:.3f} ms, "
-              f"exhaustive {exh:.3f} ms, regret {(model - exh) / exh:.3f}")
-        assert model <= heur * 1.03
+              f"exhaustive {exh:.3f} ms, regret {(model - exh) / exh:.3f}; tuning "
+              f"{t_model:.3f} s with the model, {t_exh:.3f} s exhaustive")
     h.close()
     m.close()
+    return out
+
+
+@pytest.mark.slow
+def test_model_tuning_gains_over_heuristic(torch):
+    """Upwind 3D: a model trained on 20^3..28^3 tunes a held-out 34^3 matrix.
+    What the network gains over the method without it: the exhaustive
+    tuner's plan quality (regret at most 5%) at a fraction of its cost (no
+    timing runs: at most a tenth of the exhaustive tuner's wall time), and it
+    never does worse than the built-in heuristic by more than 2% (the
+    launch-by-launch time the tuner itself measures; on this family the row
+    panel heuristic is within a few percent of the best plan)."""
+    import paper_1708_04539_gb300 as ps
+    out = _learned_vs_exhaustive(
+        torch, [gen.upwind_3d(size, 80 + size, max_sn=256) for size in (20, 24, 28)],
+        gen.upwind_3d(34, 99, max_sn=256), (ps.PREC_FP64, ps.PREC_OZAKI_FP16))
+    for prec in (ps.PREC_FP64, ps.PREC_OZAKI_FP16):
+        heur, model, exh, t_model, t_exh = out[prec]
+        assert model <= 1.02 * heur, (prec, heur, model)
+        assert (model - exh) / exh <= 0.05, (prec, model, exh)
+        assert t_model <= 0.1 * t_exh, (prec, t_model, t_exh)
+
+
+@pytest.mark.slow
+def test_model_tuning_on_dg_operator(torch):
+    """The DG element-block family (the workload the learned model serves in
+    the benchmark): trained on 5^3 and 6^3 elements, tuning 8^3 elements,
+    with the same bounds."""
+    import paper_1708_04539_gb300 as ps
+    out = _learned_vs_exhaustive(
+        torch, [gen.dg_blocks(me, 64, 900 + me, max_sn=256) for me in (5, 6)],
+        gen.dg_blocks(8, 64, 908, max_sn=256), (ps.PREC_OZAKI_FP16,))
+    heur, model, exh, t_model, t_exh = out[ps.PREC_OZAKI_FP16]
+    assert model <= 1.02 * heur, (heur, model)
+    assert (model - exh) / exh <= 0.05, (model, exh)
+    assert t_model <= 0.1 * t_exh, (t_model, t_exh)
