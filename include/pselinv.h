@@ -316,9 +316,13 @@ enum pselinv_step_kind {
   PSELINV_STEP_MEMSET = 6, PSELINV_STEP_SCATTER_VALUES = 7, PSELINV_STEP_SLICE = 8,
   PSELINV_STEP_OZAKI_GEMM = 9, PSELINV_STEP_RECOMBINE = 10,
   PSELINV_STEP_SMALL_LEVEL = 11, /* steps 3-5 of a level of narrow supernodes, one launch */
-  PSELINV_STEP_GATHER_SLICE = 12 /* split levels: Ainv_CC gathered and sliced in one pass
-                                    (maxima, or slices in both layouts), with the panels'
-                                    slicing; Ainv_CC is never stored in FP64 */
+  PSELINV_STEP_GATHER_SLICE = 12, /* split levels: Ainv_CC gathered and sliced in one pass
+                                     (slices in both layouts, exponents from the running
+                                     maxima), with the panels' maxima or slicing; Ainv_CC is
+                                     never stored in FP64 */
+  PSELINV_STEP_OUTPUT_MAXIMA = 13 /* split sweeps: the running row and column maxima of
+                                     |Ainv| merged with a level's finished blocks; they
+                                     bound the rows and columns of every later Ainv_CC */
 };
 
 /* Run the selected-inversion plan (which = 0) or the factorisation plan

@@ -42,7 +42,7 @@ TUNE_RESET, TUNE_EXHAUSTIVE, TUNE_MODEL = 0, 1, 2
 
 STEP_KINDS = {0: "gemm", 1: "tri_inv", 2: "diag_lu", 3: "gather", 4: "scatter_sub", 5: "copy",
               6: "memset", 7: "scatter_values", 8: "slice", 9: "ozaki_gemm", 10: "recombine",
-              11: "small_level", 12: "gather_slice"}
+              11: "small_level", 12: "gather_slice", 13: "output_maxima"}
 
 
 class LibraryMissing(RuntimeError):

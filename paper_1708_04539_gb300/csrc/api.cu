@@ -53,7 +53,8 @@ enum StepKind {
   ST_ZERO,
   ST_LU_PANEL,
   ST_SMALL_LEVEL,
-  ST_GSLICE
+  ST_GSLICE,
+  ST_OUTMAX
 };
 
 struct Step {
@@ -139,6 +140,9 @@ struct pselinv_ctx {
   size_t scratch_high = 0;  // plan building: highest scratch byte a step uses
   char* staging = nullptr;  // nbatch * nnz values
   char* outstage = nullptr; // nnz values
+  // running row and column maxima of |Ainv| (nbatch * 2n bit patterns),
+  // the exponents of the split sweep's G slices
+  unsigned long long* rcmax = nullptr;
   // pole-expansion consumers: the input pattern (for transposed entries),
   // the storage slot of the transposed entry of every input entry, and a
   // buffer for weights, B and partial sums
@@ -249,15 +253,17 @@ int upload_structure(pselinv_ctx* h) {
     upload(host, o_rr, rr);
     upload(host, o_rs, rs);
   }
+  // the global index of every position of R_L(K) (R_K)
+  size_t o_lrows = 0;
+  upload(host, o_lrows, narrow<int32_t>(H.rows));
   // general patterns: the second row structure and its maps
-  size_t o_cu = 0, o_urptr = 0, o_lrows = 0, o_urows = 0, o_urblk = 0, o_q0 = 0, o_ubsn = 0,
-         o_ubrel = 0, o_ubq0 = 0, o_inv = 0;
+  size_t o_cu = 0, o_urptr = 0, o_urows = 0, o_urblk = 0, o_q0 = 0, o_ubsn = 0, o_ubrel = 0,
+         o_ubq0 = 0, o_inv = 0;
   if (H.general) {
     std::vector<int64_t> sn_cu(H.ns);
     for (int64_t k = 0; k < H.ns; k++) sn_cu[k] = H.urows_ptr[k + 1] - H.urows_ptr[k];
     upload(host, o_cu, narrow<int32_t>(sn_cu));
     upload(host, o_urptr, H.urows_ptr);
-    upload(host, o_lrows, narrow<int32_t>(H.rows));
     upload(host, o_urows, narrow<int32_t>(H.urows));
     upload(host, o_urblk, H.urows_blk);
     upload(host, o_q0, H.blk_q0);
@@ -298,10 +304,12 @@ int upload_structure(pselinv_ctx* h) {
   S.row_pan = (const int64_t*)(b + o_rp);
   S.row_rel = (const int64_t*)(b + o_rr);
   S.row_sn = (const int32_t*)(b + o_rs);
+  S.lrows = (const int32_t*)(b + o_lrows);
+  S.urows = S.lrows;
+  S.n = H.n;
   if (H.general) {
     S.sn_cu = (const int32_t*)(b + o_cu);
     S.urows_ptr = (const int64_t*)(b + o_urptr);
-    S.lrows = (const int32_t*)(b + o_lrows);
     S.urows = (const int32_t*)(b + o_urows);
     S.urows_blk = (const int32_t*)(b + o_urblk);
     S.blk_q0 = (const int32_t*)(b + o_q0);
@@ -1024,6 +1032,41 @@ void add_ozaki_normalize(pselinv_ctx* h, Plan& P, int lev, int64_t nb,
   for (size_t i = first; i < P.steps.size(); i++) P.steps[i].side = 1;
 }
 
+// Merge the finished blocks of the supernodes `sns` (diagonal block, L and
+// U^T panels of every instance) into the running row / column maxima of
+// Ainv: what a later level's G reads is bounded by them.
+void add_outmax_step(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& sns, int lev) {
+  const HostSym& H = h->H;
+  std::vector<MaxTask> tasks;
+  for (int64_t b = 0; b < h->nbatch; b++)
+    for (int64_t K : sns) {
+      const int s = (int)H.sn_width[K], c = (int)cK(H, K), cu = (int)cU(H, K);
+      const int64_t so = H.sn_offset[K];
+      // L panel: rows of Ainv (R_K) for a structurally symmetric handle,
+      // columns (R_L) for a general one; the U^T panel the other way round
+      const int lwhich = H.general ? 2 : 1, uwhich = H.general ? 1 : 2;
+      for (int r = 0; r < ceil_div(s, kOutMaxRows); r++) tasks.push_back({(int)b, (int)K, 0, r, so, s, 0});
+      for (int r = 0; r < ceil_div(c, kOutMaxRows); r++)
+        tasks.push_back({(int)b, (int)K, lwhich, r, so + (int64_t)s * s, c, 0});
+      for (int r = 0; r < ceil_div(cu, kOutMaxRows); r++)
+        tasks.push_back({(int)b, (int)K, uwhich, r, so + (int64_t)s * s + (int64_t)c * s, cu,
+                         H.general ? 1 : 0});
+    }
+  if (tasks.empty()) return;
+  Step st;
+  st.kind = ST_OUTMAX;
+  st.n = (int)tasks.size();
+  st.tasks = P.push(tasks);
+  double bytes = 0;
+  for (int64_t K : sns) {
+    const double s = (double)H.sn_width[K];
+    bytes += s * (s + cK(H, K) + cU(H, K));
+  }
+  st.bytes = (size_t)(bytes * h->nbatch * h->esize);
+  st.level = lev;
+  P.steps.push_back(st);
+}
+
 // One level (or one supernode) of the split-precision sweep: gather G,
 // slice G (by rows and by columns), Lhat and Uhat^T, sliced products for
 // steps 3 and 5, slice Ainv(C,K), sliced product for step 4 accumulated onto
@@ -1041,12 +1084,13 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   std::vector<CopySeg> zero, mirror;
   const bool sym = h->opts.symmetric != 0;
   OzBuilder ob(h, (size_t)gbase_scalars * es);
-  // row and column maxima of every G and panel of the level (the sweep's
-  // maxima region, zeroed at its start)
+  // column maxima of every panel operand of the level (the sweep's maxima
+  // region, zeroed at its start); G's exponents come from the running
+  // row / column maxima of Ainv instead
   int64_t nmax = 0;
   for (int64_t b = 0; b < nb; b++)
     for (int64_t K : grp)
-      if (cK(H, K) > 0 && cU(H, K) > 0) nmax += cK(H, K) + cU(H, K) + 3 * H.sn_width[K];
+      if (cK(H, K) > 0 && cU(H, K) > 0) nmax += 3 * H.sn_width[K];
   std::vector<CopySeg> zside;  // general patterns: a panel whose products are empty
   for (int64_t b = 0; b < nb; b++)
     for (int64_t K : grp)
@@ -1072,27 +1116,25 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
       const int s = (int)H.sn_width[K], c = (int)cK(H, K), cu = (int)cU(H, K);
       if (c == 0 || cu == 0) continue;
       const int64_t m0 = moff;
-      moff += cu + c + 3 * s;
+      moff += 3 * s;
       const size_t so = ((size_t)b * H.storage + H.sn_offset[K]) * es;
       const size_t lo = so + (size_t)s * s * es, uo = lo + (size_t)c * s * es;
       // symmetric A: G is symmetric and Uhat = Lhat^T, so step 5's product is
       // the transpose of step 3's (a copy) and step 4 uses Lhat
       SliceDesc gr = ob.slice(nullptr, cu, SLICE_ROWS, cu, c);  // G by rows (from the gather)
-      gr.maxbits = maxbase + m0;
       SliceDesc lh = ob.slice(h->nf + lo, c, SLICE_COLS, s, c);
-      lh.maxbits = maxbase + m0 + cu + c;
+      lh.maxbits = maxbase + m0;
       SliceDesc gc = gr, uh = lh;
       if (!sym) {
         gc = ob.slice(nullptr, c, SLICE_COLS, c, cu);  // G by columns
-        gc.maxbits = maxbase + m0 + cu;
         uh = ob.slice(h->nf + uo, cu, SLICE_COLS, s, cu);
-        uh.maxbits = maxbase + m0 + cu + c + s;
+        uh.maxbits = maxbase + m0 + s;
       }
       // Ainv(R_U, K): the U^T panel of a general pattern, the L panel otherwise
       char* ainv_uk = H.general ? h->ainv + uo : h->ainv + lo;
       char* ainv_kl = H.general ? h->ainv + lo : h->ainv + uo;
       SliceDesc ak = ob.slice(ainv_uk, cu, SLICE_COLS, s, cu);
-      ak.maxbits = maxbase + m0 + cu + c + 2 * s;
+      ak.maxbits = maxbase + m0 + 2 * s;
       const int ir = (int)gd.size();
       gd.push_back(gr);
       const int ic = sym ? -1 : (int)gd.size();
@@ -1119,9 +1161,10 @@ void add_ozaki_level(pselinv_ctx* h, Plan& P, const std::vector<int64_t>& grp, i
   const int prec = PSELINV_PREC_OZAKI_FP16;
   const int ks_main = tuned_value(h, prec, lev, 1, choose_ozaki_ksplit(main));
   const int ks_diag = tuned_value(h, prec, lev, 2, choose_ozaki_ksplit(dg));
-  // G's maxima, then its slices in both layouts straight from the ancestors'
-  // blocks (with the panels' maxima and slices in the same launches)
-  add_gslice_step(P, gd, gt, dense, lev, true, es);
+  // the panels' maxima, then G's slices in both layouts straight from the
+  // ancestors' blocks (exponents from the running maxima of Ainv) with the
+  // panels' slices in the same launch
+  add_gslice_step(P, gd, {}, dense, lev, true, es);
   add_gslice_step(P, gd, gt, dense, lev, false, es);
   // outputs of products split along K (requested, or forced by the exact
   // chunk limit) are accumulated: zero them first
@@ -1332,15 +1375,20 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
   P.two_streams = true;
   P.ev.assign(EV_LEVEL + std::max(nlev, 0), nullptr);
   for (auto& e : P.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // split precision: each level runs either the sliced tensor-core products
+  // (normalisation included) or, for levels whose products are too small
+  // to pay for the slicing, the FP64 ones; the default is a flop
+  // threshold, the tuner times both
+  std::vector<char> split_lv((size_t)std::max(nlev, 0), 0);
+  int last_split = -1;  // the running maxima are kept up to this level
+  for (int lev = 0; lev < nlev; lev++) {
+    if (precision != PSELINV_PREC_OZAKI_FP16) break;
+    const int mode = tuned_value(h, precision, lev, 3, level_product_flops(h, lev) < 2e8 ? 1 : 0);
+    split_lv[(size_t)lev] = mode == 0;
+    if (mode == 0) last_split = lev;
+  }
   for (size_t lev = 0; lev + 1 < H.level_ptr.size(); lev++) {
-    // split precision: each level runs either the sliced tensor-core products
-    // (normalisation included) or, for levels whose products are too small
-    // to pay for the slicing, the FP64 ones; the default is a flop
-    // threshold, the tuner times both
-    int mode = 0;
-    if (precision == PSELINV_PREC_OZAKI_FP16)
-      mode = tuned_value(h, precision, (int)lev, 3, level_product_flops(h, (int)lev) < 2e8 ? 1 : 0);
-    const bool split_level = precision == PSELINV_PREC_OZAKI_FP16 && mode == 0;
+    const bool split_level = split_lv[lev] != 0;
     add_normalize((int)lev, split_level && h->opts.split_normalise != 0 && !H.general);
     const size_t first_main = P.steps.size();
     // groups: the whole level, or one supernode at a time
@@ -1434,7 +1482,40 @@ int build_selinv_plan(pselinv_ctx* h, int schedule, int precision) {
       add_gemm_step(P, dt, tuned_value(h, precision, (int)lev, slot_diag, cfg), dg, (int)lev,
                     slot_diag);
     }
+    if ((int)lev < last_split) {  // a later split level slices blocks of this one
+      std::vector<int64_t> sns;
+      for (int64_t i = H.level_ptr[lev]; i < H.level_ptr[lev + 1]; i++)
+        if (in_set(H.level_sn[i])) sns.push_back(H.level_sn[i]);
+      add_outmax_step(h, P, sns, (int)lev);
+    }
     if (P.steps.size() > first_main) P.steps[first_main].wait = EV_LEVEL + (int)lev;
+  }
+  if (last_split >= 0) {
+    // a partitioned sweep starts from imported blocks G_r = Ainv(R_U(r),
+    // R_L(r)) of its subtree roots r: their row and column maxima first
+    std::vector<GTileTask> roots;
+    for (int64_t b = 0; b < nb; b++)
+      for (int64_t K = 0; K < H.ns && !h->subset.empty(); K++) {
+        const int64_t par = H.sn_parent[K];
+        if (!in_set(K) || par < 0 || in_set(par) || cK(H, K) == 0 || cU(H, K) == 0) continue;
+        for (int tq = 0; tq < ceil_div(cK(H, K), 64); tq++)
+          for (int tp = 0; tp < ceil_div(cU(H, K), 64); tp++)
+            roots.push_back({(int)b, (int)K, tp, tq, 0, -1});
+      }
+    std::vector<Step> pre;
+    Step ms;
+    ms.kind = ST_MEMSET;
+    ms.ptr = h->rcmax;
+    ms.bytes = (size_t)nb * 2 * H.n * 8;
+    pre.push_back(ms);
+    if (!roots.empty()) {
+      std::vector<SliceDesc> none(1);
+      const size_t at = P.steps.size();
+      add_gslice_step(P, none, roots, {}, -1, true, es);
+      pre.push_back(P.steps[at]);
+      P.steps.pop_back();
+    }
+    P.steps.insert(P.steps.begin(), pre.begin(), pre.end());
   }
   // the scratch sizes above bound every region the steps use
   if (h->scratch_high > h->scratch_bytes) return PSELINV_ERR_CHECK;
@@ -1510,7 +1591,10 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
     case ST_GSLICE:
       launch_gslice(h->dtype, h->S, h->ainv, (const SliceDesc*)(a + s.descs),
                     (const GTileTask*)(a + s.tasks), s.n, (const SliceTask*)(a + s.offs), s.n2,
-                    s.cfg == 1, st);
+                    s.cfg == 1, h->rcmax, st);
+      break;
+    case ST_OUTMAX:
+      launch_out_maxima(h->dtype, h->S, h->ainv, (const MaxTask*)(a + s.tasks), s.n, h->rcmax, st);
       break;
   }
 }
@@ -1605,7 +1689,9 @@ void free_numeric(pselinv_ctx* h) {
   cudaFree(h->staging);
   cudaFree(h->outstage);
   cudaFree(h->cbuf);
+  cudaFree(h->rcmax);
   h->lu = h->nf = h->ainv = h->scratch = h->staging = h->outstage = h->cbuf = nullptr;
+  h->rcmax = nullptr;
   h->dtype = 0;
   h->nbatch = 0;
   h->factored = h->inverted = false;
@@ -1811,6 +1897,7 @@ int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, v
     CK(cudaMalloc(&h->scratch, h->scratch_bytes));
     CK(cudaMalloc(&h->staging, (size_t)nbatch * h->H.nnz * es + 256));
     CK(cudaMalloc(&h->outstage, (size_t)h->H.nnz * es + 256));
+    CK(cudaMalloc(&h->rcmax, (size_t)nbatch * 2 * h->H.n * 8 + 256));
     CK(prepare_dense_kernels(dtype, h->max_width));
     CK(prepare_map_kernels());
     CK(prepare_ozaki_kernels());
@@ -2110,7 +2197,7 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
                                 PSELINV_STEP_MEMSET,  PSELINV_STEP_SCATTER_VALUES,
                                 PSELINV_STEP_SLICE,   PSELINV_STEP_OZAKI_GEMM, PSELINV_STEP_MEMSET,
                                 PSELINV_STEP_DIAG_LU, PSELINV_STEP_SMALL_LEVEL,
-                                PSELINV_STEP_GATHER_SLICE};
+                                PSELINV_STEP_GATHER_SLICE, PSELINV_STEP_OUTPUT_MAXIMA};
     out[i].kind = kinds[s.kind];
     out[i].level = s.level;
     out[i].tasks = s.n;

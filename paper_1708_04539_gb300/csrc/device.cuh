@@ -92,6 +92,11 @@ struct SymDev {
   const int64_t* row_pan;
   const int64_t* row_rel;
   const int32_t* row_sn;
+  // global (permuted) index of every position of R_L(K) / R_K (lrows, all
+  // handles) and of R_U(K) (urows, general handles; lrows otherwise)
+  const int32_t* lrows;
+  const int32_t* urows;
+  int64_t n;
   // general patterns (general = 1; null for structurally symmetric
   // handles): sn_c, rows_ptr, rows_blk and blk_* describe R_L(K) (the L
   // panel's rows), sn_cu, urows_ptr, urows_blk and ublk_* R_U(K) (the U^T
@@ -101,8 +106,6 @@ struct SymDev {
   int32_t general;
   const int32_t* sn_cu;
   const int64_t* urows_ptr;
-  const int32_t* lrows;
-  const int32_t* urows;
   const int32_t* urows_blk;
   const int32_t* blk_q0;
   const int32_t* ublk_sn;
@@ -227,12 +230,31 @@ struct OzTask {
 struct GTileTask {
   int inst, K, tp, tq, dr, dc;
 };
-// maxima = true: the tiles' row and column maxima into the descs' maxbits
-// (and the maxima of the ordinary slice tasks stasks[0..nst)); false: their
-// slices (exponents from the maxima)
+// Running maxima of |Ainv| per global row and column (bit patterns; rowmax
+// at rcmax + inst * 2n, colmax n further), the exponents of G's slices:
+// every entry of G_K lies in a row and a column whose entries so far
+// include it, so the maxima over them bound G's rows and columns.
+// maxima = true: the tiles' row and column maxima into rcmax (the G
+// blocks a partitioned sweep imports) and the maxima of the ordinary slice
+// tasks stasks[0..nst) into their descs' maxbits; false: the tiles' slices
+// in both layouts (exponents from rcmax) and the ordinary slices.
 void launch_gslice(int dtype, const SymDev& S, const void* store, const SliceDesc* descs,
                    const GTileTask* gtasks, int ngt, const SliceTask* stasks, int nst, bool maxima,
-                   cudaStream_t st);
+                   unsigned long long* rcmax, cudaStream_t st);
+// One chunk of rows of a stored block of Ainv: which = 0 the diagonal
+// block of K (rows and columns first(K) + t), 1 a panel whose rows are rows
+// of Ainv (entry (p, t) = Ainv(R[p], first + t)), 2 a panel whose rows are
+// columns of Ainv (entry (p, t) = Ainv(first + t, R[p])); R from lrows at
+// rows_ptr[K] (L panel) or urows at urows_ptr[K] (U^T panel, general).
+constexpr int kOutMaxRows = 128;
+struct MaxTask {
+  int inst, K, which, rc;  // rc: chunk of kOutMaxRows rows
+  int64_t off;              // scalar offset of the block in one instance
+  int nrows, upanel;        // rows of the block; 1: R from the U^T panel's list
+};
+// merge the blocks' row and column maxima into rcmax
+void launch_out_maxima(int dtype, const SymDev& S, const void* store, const MaxTask* tasks,
+                       int ntasks, unsigned long long* rcmax, cudaStream_t st);
 cudaError_t prepare_ozaki_kernels();
 // maxima = true: accumulate row maxima into desc.maxbits; false: write the slices
 void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bool maxima,

@@ -244,7 +244,7 @@ template <typename T, bool MAXIMA>
 __global__ void __launch_bounds__(kSliceThreads)
 gslice_kernel(SymDev S, const T* __restrict__ store, const SliceDesc* __restrict__ descs,
               const GTileTask* __restrict__ gtasks, int ngt,
-              const SliceTask* __restrict__ stasks, int nst) {
+              const SliceTask* __restrict__ stasks, int nst, unsigned long long* rcmax) {
   extern __shared__ __align__(16) unsigned char gs_raw[];
   T* tile = reinterpret_cast<T*>(gs_raw);  // tile[pl * kGTPad + ql]
   int64_t* cdiag = reinterpret_cast<int64_t*>(gs_raw + (size_t)kGT * kGTPad * sizeof(T));
@@ -368,6 +368,11 @@ gslice_kernel(SymDev S, const T* __restrict__ store, const SliceDesc* __restrict
     }
     __syncthreads();
     const SliceDesc& dr = descs[task.dr];
+    // the running row / column maxima of this instance
+    unsigned long long* rmax = rcmax + (int64_t)task.inst * 2 * S.n;
+    unsigned long long* cmax = rmax + S.n;
+    const int32_t* ridx = (S.general ? S.urows : S.lrows) + rbU;  // global row of position p
+    const int32_t* cidx = S.lrows + rb;                              // global column of q
     if (MAXIMA) {
       // row maxima, then column maxima: four threads (a quarter of the
       // tile's width each, neighbours in one warp) per row / column
@@ -377,15 +382,13 @@ gslice_kernel(SymDev S, const T* __restrict__ store, const SliceDesc* __restrict
         m = max(m, abs_bits_max(tile[line * kGTPad + part * (kGT / 4) + i]));
       m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
       m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
-      if (part == 0 && p0 + line < cu && m) atomicMax(dr.maxbits + p0 + line, m);
-      if (task.dc >= 0) {
-        m = 0;
-        for (int i = 0; i < kGT / 4; i++)
-          m = max(m, abs_bits_max(tile[(part * (kGT / 4) + i) * kGTPad + line]));
-        m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
-        m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
-        if (part == 0 && q0 + line < cl && m) atomicMax(descs[task.dc].maxbits + q0 + line, m);
-      }
+      if (part == 0 && p0 + line < cu && m) atomicMax(rmax + ridx[p0 + line], m);
+      m = 0;
+      for (int i = 0; i < kGT / 4; i++)
+        m = max(m, abs_bits_max(tile[(part * (kGT / 4) + i) * kGTPad + line]));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      if (part == 0 && q0 + line < cl && m) atomicMax(cmax + cidx[q0 + line], m);
     } else {
       // work item of the slicing: row rl, 8 values of K group kg of a 32-wide K block
       const int ci = tid >> 3, rr = tid & 7;
@@ -401,7 +404,14 @@ gslice_kernel(SymDev S, const T* __restrict__ store, const SliceDesc* __restrict
         const int k32c = (nk + 31) / 32;  // K blocks of one part
         const int rblk64 = r0 / 64;
         const int r = r0 + rl;
-        const int e = r < nrows ? exp_of_max(d.maxbits[r]) : 0;
+        // G by rows: rows of Ainv; by columns: its columns (a symmetric G,
+        // sliced by rows only, takes the larger of both)
+        unsigned long long mb = 0;
+        if (r < nrows) {
+          mb = layout == 0 ? rmax[ridx[r]] : cmax[cidx[r]];
+          if (task.dc < 0) mb = max(mb, cmax[cidx[r]]);
+        }
+        const int e = r < nrows ? exp_of_max(mb) : 0;
         if (kq0 == 0 && kg == 0 && r < nrows) d.exps[r] = e;
         const int64_t slice_stride = (int64_t)d.R64 * d.K32 * (kTileBytes / 2);
         for (int kbl = 0; kbl < kGT / 32; kbl++) {
@@ -857,9 +867,79 @@ void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bo
     slice_kernel<<<grid, kSliceThreads, 0, st>>>(descs, tasks, ntasks);
 }
 
+namespace {
+// Row and column maxima of one chunk of up to 128 rows of a stored block
+// of Ainv (see MaxTask): warp w takes the columns w, w + 8, ..., a lane the
+// rows lane + 32 i of each (coalesced down the column-major block); a
+// column's maximum is a warp reduction, a row's a reduction over the warps
+// in shared memory; one atomicMax per row and per column of the chunk.
+constexpr int kMaxRows = kOutMaxRows;
+template <typename T>
+__global__ void __launch_bounds__(kSliceThreads)
+out_maxima_kernel(SymDev S, const T* __restrict__ store, const MaxTask* __restrict__ tasks,
+                  int ntasks, unsigned long long* rcmax) {
+  constexpr int kWarps = kSliceThreads / 32;
+  __shared__ unsigned long long rowm[kWarps][kMaxRows];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const MaxTask task = tasks[t];
+    const int K = task.K, s = S.sn_width[K], f = S.sn_first[K];
+    const int r0 = task.rc * kMaxRows, nr = min(kMaxRows, task.nrows - r0);
+    const T* blk = store + (int64_t)task.inst * S.storage + task.off + r0;
+    unsigned long long* rmax = rcmax + (int64_t)task.inst * 2 * S.n;
+    unsigned long long* cmax = rmax + S.n;
+    // where the block's rows and columns lie among the rows / columns of Ainv
+    unsigned long long* rdst = task.which == 2 ? cmax : rmax;
+    unsigned long long* cdst = task.which == 2 ? rmax : cmax;
+    unsigned long long m[kMaxRows / 32];
+#pragma unroll
+    for (int i = 0; i < kMaxRows / 32; i++) m[i] = 0;
+    for (int tc = warp; tc < s; tc += kWarps) {
+      const T* col = blk + (int64_t)tc * task.nrows;
+      unsigned long long cm = 0;
+#pragma unroll
+      for (int i = 0; i < kMaxRows / 32; i++) {
+        const int r = lane + 32 * i;
+        const unsigned long long v = r < nr ? abs_bits_max(col[r]) : 0ull;
+        m[i] = max(m[i], v);
+        cm = max(cm, v);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+      if (lane == 0 && cm) atomicMax(cdst + f + tc, cm);
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxRows / 32; i++) rowm[warp][lane + 32 * i] = m[i];
+    __syncthreads();
+    if (tid < nr) {
+      unsigned long long x = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; w++) x = max(x, rowm[w][tid]);
+      const int32_t* R = task.which == 0 ? nullptr
+                         : task.upanel   ? S.urows + S.urows_ptr[K]
+                                         : S.lrows + S.rows_ptr[K];
+      if (x) atomicMax(rdst + (task.which == 0 ? f + r0 + tid : R[r0 + tid]), x);
+    }
+    __syncthreads();
+  }
+}
+}  // namespace
+
+void launch_out_maxima(int dtype, const SymDev& S, const void* store, const MaxTask* tasks,
+                       int ntasks, unsigned long long* rcmax, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  if (dtype == DT_F64)
+    out_maxima_kernel<double><<<grid, kSliceThreads, 0, st>>>(S, (const double*)store, tasks,
+                                                              ntasks, rcmax);
+  else
+    out_maxima_kernel<cdouble><<<grid, kSliceThreads, 0, st>>>(S, (const cdouble*)store, tasks,
+                                                               ntasks, rcmax);
+}
+
 void launch_gslice(int dtype, const SymDev& S, const void* store, const SliceDesc* descs,
                    const GTileTask* gtasks, int ngt, const SliceTask* stasks, int nst, bool maxima,
-                   cudaStream_t st) {
+                   unsigned long long* rcmax, cudaStream_t st) {
   const int ntasks = ngt + nst;
   if (ntasks <= 0) return;
   const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
@@ -867,18 +947,18 @@ void launch_gslice(int dtype, const SymDev& S, const void* store, const SliceDes
     const size_t sm = gslice_smem<double>();
     if (maxima)
       gslice_kernel<double, true><<<grid, kSliceThreads, sm, st>>>(
-          S, (const double*)store, descs, gtasks, ngt, stasks, nst);
+          S, (const double*)store, descs, gtasks, ngt, stasks, nst, rcmax);
     else
       gslice_kernel<double, false><<<grid, kSliceThreads, sm, st>>>(
-          S, (const double*)store, descs, gtasks, ngt, stasks, nst);
+          S, (const double*)store, descs, gtasks, ngt, stasks, nst, rcmax);
   } else {
     const size_t sm = gslice_smem<cdouble>();
     if (maxima)
       gslice_kernel<cdouble, true><<<grid, kSliceThreads, sm, st>>>(
-          S, (const cdouble*)store, descs, gtasks, ngt, stasks, nst);
+          S, (const cdouble*)store, descs, gtasks, ngt, stasks, nst, rcmax);
     else
       gslice_kernel<cdouble, false><<<grid, kSliceThreads, sm, st>>>(
-          S, (const cdouble*)store, descs, gtasks, ngt, stasks, nst);
+          S, (const cdouble*)store, descs, gtasks, ngt, stasks, nst, rcmax);
   }
 }
 
