@@ -84,6 +84,8 @@ def parse(argv=None):
                          "(profiling runs: timings under a profiler would mislead the tuner)")
     ap.add_argument("--dump-profile", default=None,
                     help="write the launch-by-launch profile (JSON) to this path")
+    ap.add_argument("--factor-precision", default="auto", choices=["auto", "fp64", "ozaki"],
+                    help="Schur products of the factorisation: auto = the sweep's precision")
     ap.add_argument("--split-normalise", action="store_true",
                     help="also slice the normalisation and D_K (by default they stay FP64)")
     ap.add_argument("--size", type=int, default=None,
@@ -428,13 +430,15 @@ def time_steps(h, prec, stream, steps, out_dev, warm=True):
     return e0.elapsed_time(e1) / steps
 
 
-def comparison(p, h, stream, out_dev, flops, big):
+def comparison(p, h, stream, out_dev, flops, big, refactor=None):
     """FP64 level-batched and FP64 per-supernode sweeps of the same matrix,
     and the error of the split-precision result against the FP64 one.
 
     big: the FP64 arms take about a minute each, so they run the built-in
     heuristic plan once (no tuning, no repeat; the plan is built before the
-    timed call)."""
+    timed call).  refactor: the values, when the handle's factors came from
+    split Schur products; the FP64 arms then run on an FP64 factorisation
+    (timed), and the error covers both split stages."""
     import torch
     import paper_1708_04539_gb300 as ps
     st = h.structure()
@@ -447,6 +451,17 @@ def comparison(p, h, stream, out_dev, flops, big):
         h.selinv(precision=ps.PREC_OZAKI_FP16, stream=stream)
         h.get_selected(split, layout=ps.LAYOUT_SUPERNODAL, stream=stream)
     torch.cuda.synchronize()
+    fp64_factor_ms = None
+    if refactor is not None:
+        h.set_factor_precision(ps.PREC_FP64)
+        with torch.cuda.stream(stream):
+            h.factor(refactor, stream=stream)  # builds the FP64 factorisation plan
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.factor(refactor, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_factor_ms = e0.elapsed_time(e1)
     h.tune(precision=ps.PREC_FP64, mode=ps.TUNE_RESET if big else ps.TUNE_EXHAUSTIVE,
            stream=stream)
     fp64_level_ms = time_steps(h, ps.PREC_FP64, stream, 1 if big else 3, out_dev, warm=not big)
@@ -454,6 +469,13 @@ def comparison(p, h, stream, out_dev, flops, big):
         h.get_selected(ref, layout=ps.LAYOUT_SUPERNODAL, stream=stream)
     torch.cuda.synchronize()
     err, normwise = selected_error_supernodal(st, split, ref)
+    split_sweep_err = None
+    if refactor is not None:  # the split sweep alone, on the FP64 factors
+        with torch.cuda.stream(stream):
+            h.selinv(precision=ps.PREC_OZAKI_FP16, stream=stream)
+            h.get_selected(split, layout=ps.LAYOUT_SUPERNODAL, stream=stream)
+        torch.cuda.synchronize()
+        split_sweep_err, _ = selected_error_supernodal(st, split, ref)
     del split
     h.set_schedule(ps.SCHED_PER_SUPERNODE)
     h.tune(precision=ps.PREC_FP64, mode=ps.TUNE_RESET, stream=stream)  # builds its plan
@@ -465,8 +487,14 @@ def comparison(p, h, stream, out_dev, flops, big):
            "fp64_per_supernode_ms": per_sn_ms,
            "fp64_per_supernode_gflops": flops / (per_sn_ms * 1e-3) / 1e9,
            "split_vs_fp64_selected_error": err, "split_vs_fp64_normwise_error": normwise,
+           "split_covers": "factorisation Schur products and sweep" if refactor is not None
+                           else "sweep",
            "error_metric": "max |x - r| / max(max_k |r_ik|, max_k |r_kj|) over every entry "
-                           "of the pattern of L+U; r = FP64 GPU result"}
+                           "of the pattern of L+U; r = FP64 GPU result (FP64 factorisation "
+                           "and FP64 sweep)"}
+    if refactor is not None:
+        out.update({"fp64_factor_ms": fp64_factor_ms,
+                    "split_sweep_on_fp64_factors_selected_error": split_sweep_err})
     if not big:
         # option: normalisation and D_K as sliced products too
         q = ps.SelInv.from_problem(p, relax_pct=20, split_normalise=True)
@@ -675,8 +703,10 @@ def run_ours(args):
     nbatch = p.nbatch
     sched = ps.SCHED_PER_SUPERNODE if args.schedule == "per_supernode" else ps.SCHED_LEVEL
     log(f"workload generated: n={p.n} nnz={p.nnz}")
+    fprec_name = args.precision if args.factor_precision == "auto" else args.factor_precision
+    fprec = ps.PREC_OZAKI_FP16 if fprec_name == "ozaki" else ps.PREC_FP64
     hkw = dict(relax_pct=20, schedule=sched, use_graph=not args.no_graph,
-               split_normalise=args.split_normalise)
+               split_normalise=args.split_normalise, factor_precision=fprec)
     if config == 4:
         members = [ps.SelInv.from_problem(q, host_only=True, relax_pct=20)
                    for q in p.meta["members"]]
@@ -843,6 +873,7 @@ def run_ours(args):
                    "flops_relaxed_structure": st["flops_selinv"] * (4.0 if cplx else 1.0),
                    "schedule": args.schedule, "cuda_graph": not args.no_graph,
                    "normalisation": "split" if args.split_normalise else "fp64",
+                   "factor_schur_products": fprec_name,
                    "tuning": tuning, "tuning_seconds": tune_s,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.0f MB of factors read per step)"
@@ -864,7 +895,8 @@ def run_ours(args):
     if learned_rec is not None:
         line["learned"] = learned_rec
     if not args.no_compare and args.precision == "ozaki" and rank == 0 and headline:
-        line["comparison"] = comparison(p, h, stream, out_dev[0], flops, big)
+        line["comparison"] = comparison(p, h, stream, out_dev[0], flops, big,
+                                        vals_dev if fprec == ps.PREC_OZAKI_FP16 else None)
         log("comparison done")
     h.close()
     if rank == 0 and world == 1 and not args.skip_cpu_baseline and headline:

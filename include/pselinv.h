@@ -96,7 +96,16 @@ typedef struct pselinv_opts {
   int32_t nd_leaf;       /* perm == NULL in pselinv_analyze: 0 (default) the natural order;
                             > 0 the nested-dissection ordering of pselinv_order_nd with
                             leaves of at most nd_leaf vertices (see the structure's perm) */
-  int32_t reserved[5];
+  int32_t factor_precision; /* PSELINV_PREC_FP64 (default) or PSELINV_PREC_OZAKI_FP16: the
+                            Schur-complement products L_{C,K} U_{K,C} of pselinv_factor as
+                            sliced FP16 tensor-core products (exact FP32 accumulation,
+                            FP64 result) on the levels whose products reach
+                            factor_split_mflops; the diagonal LU, the triangular solves
+                            and the scatter into the ancestors stay FP64 */
+  int32_t factor_split_mflops; /* factor_precision = OZAKI_FP16: smallest Schur-product work
+                            (MFLOP) of a level that goes split; 0 = default (200); < 0:
+                            every level */
+  int32_t reserved[3];
 } pselinv_opts;
 
 typedef struct pselinv_ctx* pselinv_t;
@@ -280,6 +289,13 @@ int pselinv_import_block(pselinv_t h, int64_t K, int64_t batch, const void* buf,
  * supernode, for comparison).  The plan of each schedule is built on its
  * first use and kept.  Host only. */
 int pselinv_set_schedule(pselinv_t h, int schedule);
+
+/* Precision of the Schur-complement products of later pselinv_factor calls
+ * (the handle's opts.factor_precision and opts.factor_split_mflops, see
+ * pselinv_opts): PSELINV_PREC_FP64 or PSELINV_PREC_OZAKI_FP16.  The
+ * factorisation plan is rebuilt on the next pselinv_factor; results already
+ * computed are kept.  Host only. */
+int pselinv_set_factor_precision(pselinv_t h, int precision, int32_t split_mflops);
 
 /* Copy results of instance `batch` (Algorithm 1 step 6 and Theorem 2 for
  * PSELINV_LAYOUT_PATTERN_A: out[p] = (A^{-1})_{rowind[p], j} for entry p of

@@ -30,7 +30,8 @@ _EXPORTS = [
     "pselinv_sync", "pselinv_last_info", "pselinv_error_string", "pselinv_free",
     "pselinv_block_inverse_noalloc", "pselinv_tune", "pselinv_tune_records",
     "pselinv_plan_get", "pselinv_plan_set", "pselinv_wait_selftest", "pselinv_measure_fp64_peak",
-    "pselinv_set_schedule", "pselinv_group", "pselinv_analyze_general",
+    "pselinv_set_schedule", "pselinv_set_factor_precision", "pselinv_group",
+    "pselinv_analyze_general",
     "pselinv_partition", "pselinv_set_subset", "pselinv_export_block", "pselinv_import_block",
     "pselinv_weighted_sum", "pselinv_trace",
     "pselinv_model_create", "pselinv_model_train", "pselinv_model_gradients",
@@ -66,7 +67,8 @@ class Opts(ctypes.Structure):
                 ("check_level", ctypes.c_int32),
                 ("host_only", ctypes.c_int32), ("split_normalise", ctypes.c_int32),
                 ("symmetric", ctypes.c_int32), ("nd_leaf", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("factor_precision", ctypes.c_int32), ("factor_split_mflops", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 _P64 = ctypes.POINTER(ctypes.c_int64)
@@ -167,6 +169,8 @@ def load_library():
     lib.pselinv_import_block.restype = ctypes.c_int
     lib.pselinv_set_schedule.argtypes = [P, ctypes.c_int]
     lib.pselinv_set_schedule.restype = ctypes.c_int
+    lib.pselinv_set_factor_precision.argtypes = [P, ctypes.c_int, ctypes.c_int32]
+    lib.pselinv_set_factor_precision.restype = ctypes.c_int
     RP = ctypes.POINTER(TuneRecord)
     lib.pselinv_tune.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P]
     lib.pselinv_tune.restype = ctypes.c_int
@@ -248,7 +252,8 @@ class SelInv:
     @staticmethod
     def _opts(lib, max_supernode=256, relax_pct=20, schedule=SCHED_LEVEL, use_graph=True,
               check_level=0, precision=PREC_FP64, slices=0, host_only=False,
-              split_normalise=False, symmetric=False, nd_leaf=0):
+              split_normalise=False, symmetric=False, nd_leaf=0, factor_precision=PREC_FP64,
+              factor_split_mflops=0):
         opts = Opts()
         lib.pselinv_default_opts(ctypes.byref(opts))
         opts.max_supernode = int(max_supernode)
@@ -262,6 +267,8 @@ class SelInv:
         opts.split_normalise = 1 if split_normalise else 0
         opts.symmetric = 1 if symmetric else 0
         opts.nd_leaf = int(nd_leaf)  # perm None: 0 natural order, > 0 nested dissection
+        opts.factor_precision = int(factor_precision)
+        opts.factor_split_mflops = int(factor_split_mflops)
         return opts
 
     def __init__(self, n, colptr, rowind, perm=None, **kw):
@@ -423,6 +430,13 @@ class SelInv:
     def set_schedule(self, schedule):
         """Schedule of later selinv/tune calls (SCHED_LEVEL or SCHED_PER_SUPERNODE)."""
         self._check(self._lib.pselinv_set_schedule(self._h, int(schedule)), "pselinv_set_schedule")
+
+    def set_factor_precision(self, precision, split_mflops=0):
+        """Precision of the Schur products of later factor calls (PREC_FP64 or
+        PREC_OZAKI_FP16; split_mflops < 0: every level split)."""
+        self._check(self._lib.pselinv_set_factor_precision(self._h, int(precision),
+                                                           int(split_mflops)),
+                    "pselinv_set_factor_precision")
 
     def tune(self, precision=PREC_FP64, mode=TUNE_EXHAUSTIVE, model=None, stream=None):
         """Autotune the launch shapes of the selected-inversion plan."""

@@ -506,16 +506,23 @@ size_t maxima_bytes(const HostSym& H, int64_t nb) {
 // split normalisation (side stream) has its own region after the sweep's,
 // the maxima theirs after that
 size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
-  int64_t fmax = 0;
+  // factorisation levels: W, the panels and the Schur product in FP64, then
+  // the slices of a split level's operands (counted for every level)
+  size_t fmax = 0;
+  const size_t parts = es / 8;
   for (size_t d = 0; d + 1 < H.hlevel_ptr.size(); d++) {
     int64_t f = 0;
+    size_t oz = 512;
     for (int64_t i = H.hlevel_ptr[d]; i < H.hlevel_ptr[d + 1]; i++) {
       const int64_t K = H.hlevel_sn[i], s = H.sn_width[K], c = cK(H, K), cu = cU(H, K);
       f += 2 * s * s + (c + cu) * s + c * cu;
+      if (c > 0 && cu > 0)
+        oz += parts * (slice_bytes(c, s, 6) + slice_bytes(cu, s, 6)) + exps_bytes(c) +
+              exps_bytes(cu) + 1024 + (size_t)(c + cu) * 8;
     }
-    fmax = std::max(fmax, f);
+    fmax = std::max(fmax, align256((size_t)(f * nb) * es) + oz * (size_t)nb + 512);
   }
-  return std::max((size_t)(fmax * nb) * es + 256,
+  return std::max(fmax + 256,
                   selinv_main_bytes(H, nb, es) + ozaki_norm_bytes(H, nb, 6, es) +
                       maxima_bytes(H, nb));
 }
@@ -622,10 +629,20 @@ void add_copy_step(Plan& P, const std::vector<CopySeg>& segs, int level, size_t 
 // panels: 61.9 vs 60.9 ms for the 40^3 factorisation)
 constexpr int kLuUpdateCfg = GEMM_32x32;
 
+// one Schur-complement product of the factorisation: Sc = TL TU^T (c x cu,
+// K = s), TL = L_{C,K} (c x s) and TU = U_{K,C}^T (cu x s), column major
+struct SchurProduct {
+  char *TL, *TU, *Sc;
+  int c, cu, s;
+};
+void add_ozaki_schur(pselinv_ctx* h, Plan& P, const std::vector<SchurProduct>& prods, int lev,
+                     size_t base);
+
 int build_factor_plan(pselinv_ctx* h) {
   const HostSym& H = h->H;
   Plan& P = h->factor_plan;
   P.release();
+  h->scratch_high = 0;
   const size_t es = h->esize;
   const int dt = h->dtype;
   const int64_t nb = h->nbatch;
@@ -642,6 +659,7 @@ int build_factor_plan(pselinv_ctx* h) {
     std::vector<TriBlock> tri;
     std::vector<int64_t> gofs;
     std::vector<GemmDesc> trsm, schur;
+    std::vector<SchurProduct> sprods;
     std::vector<CopySeg> segs;
     int64_t off = 0;  // scalars into scratch
     for (int64_t b = 0; b < nb; b++)
@@ -671,6 +689,7 @@ int build_factor_plan(pselinv_ctx* h) {
                                    GEMM_TRI_UPPER_B));
         if (c > 0 && cu > 0) {
           schur.push_back(make_desc(TL, TU, Sc, c, cu, s, c, cu, c, 0, 1, 1.0, 0.0));
+          sprods.push_back({TL, TU, Sc, (int)c, (int)cu, (int)s});
           for (int tq = 0; tq < ceil_div(cu, 32); tq++)
             for (int tp = 0; tp < ceil_div(c, 32); tp++) {
               gt.push_back({(int)b, (int)K, tp, tq});
@@ -714,9 +733,20 @@ int build_factor_plan(pselinv_ctx* h) {
     }
     add_tri_step(P, H, tri, (int)lev, 0);
     add_gemm_step(P, dt, GEMM_ROWS, trsm, (int)lev);
-    // row panels beat 64 x 64 tiles on these Schur products at every width
-    // (40^3 factorisation 61.9 -> 57.1 ms)
-    add_gemm_step(P, dt, GEMM_ROWS, schur, (int)lev);
+    // split precision: the Schur products of levels with enough work as
+    // sliced tensor-core products; otherwise FP64 row panels, which beat
+    // 64 x 64 tiles on these products at every width (40^3 factorisation
+    // 61.9 -> 57.1 ms)
+    double sflops = 0;
+    for (const SchurProduct& q : sprods) sflops += 2.0 * q.c * q.cu * q.s;
+    const double min_flops = h->opts.factor_split_mflops < 0    ? 0.0
+                             : h->opts.factor_split_mflops == 0 ? 2e8
+                                                                : 1e6 * h->opts.factor_split_mflops;
+    if (h->opts.factor_precision == PSELINV_PREC_OZAKI_FP16 && !sprods.empty() &&
+        sflops >= min_flops)
+      add_ozaki_schur(h, P, sprods, (int)lev, align256((size_t)off * es));
+    else
+      add_gemm_step(P, dt, GEMM_ROWS, schur, (int)lev);
     if (!gt.empty()) {
       Step sc;
       sc.kind = ST_SCATTER_SUB;
@@ -728,6 +758,7 @@ int build_factor_plan(pselinv_ctx* h) {
     }
     add_copy_step(P, segs, (int)lev, es);
   }
+  if (h->scratch_high > h->scratch_bytes) return PSELINV_ERR_CHECK;
   CK(cudaMalloc(&P.arena, P.host.size() + 256));
   CK(cudaMemcpy(P.arena, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
   P.built = true;
@@ -966,6 +997,41 @@ struct OzBuilder {
     out.push_back(d);
   }
 };
+
+// Schur products of one factorisation level as sliced products: row maxima
+// and slices of TL and TU (both by rows: A = TL, B = TU with K = s), then
+// the products into the FP64 Sc blocks the scatter subtracts.  Scratch from
+// `base` (bytes), after the level's FP64 region.
+void add_ozaki_schur(pselinv_ctx* h, Plan& P, const std::vector<SchurProduct>& prods, int lev,
+                     size_t base) {
+  OzBuilder ob(h, base);
+  int64_t nmax = 0;
+  for (const SchurProduct& q : prods) nmax += q.c + q.cu;
+  unsigned long long* maxbase = (unsigned long long*)ob.take((size_t)nmax * 8 + 8);
+  std::vector<SliceDesc> sl;
+  std::vector<OzDesc> out;
+  int64_t moff = 0;
+  for (const SchurProduct& q : prods) {
+    SliceDesc a = ob.slice(q.TL, q.c, SLICE_ROWS, q.c, q.s);
+    a.maxbits = maxbase + moff;
+    SliceDesc b = ob.slice(q.TU, q.cu, SLICE_ROWS, q.cu, q.s);
+    b.maxbits = maxbase + moff + q.c;
+    moff += q.c + q.cu;
+    sl.push_back(a);
+    sl.push_back(b);
+    ob.product(out, a, b, q.Sc, q.c, q.c, q.cu, 1.0);
+  }
+  Step ms;
+  ms.kind = ST_MEMSET;
+  ms.ptr = maxbase;
+  ms.bytes = (size_t)nmax * 8;
+  ms.level = lev;
+  P.steps.push_back(ms);
+  add_slice_step(P, sl, lev, true);
+  add_slice_step(P, sl, lev, false);
+  // K = s <= 256 is one exact chunk: no K split, no accumulation
+  add_ozgemm_step(P, out, h->slices, lev, false, 1, 0);
+}
 
 // Split-precision normalisation of one depth level (Algorithm 1 step 2 and
 // the diagonal block D_K = U_KK^{-1} L_KK^{-1} that starts Ainv_KK):
@@ -1762,6 +1828,8 @@ void pselinv_default_opts(pselinv_opts* o) {
   o->host_only = 0;
   o->split_normalise = 0;
   o->symmetric = 0;
+  o->factor_precision = PSELINV_PREC_FP64;
+  o->factor_split_mflops = 0;
 }
 
 const char* pselinv_error_string(int status) {
@@ -1786,7 +1854,9 @@ int pselinv_analyze(int64_t n, const int64_t* colptr, const int64_t* rowind, con
   pselinv_ctx* h = new (std::nothrow) pselinv_ctx();
   if (!h) return PSELINV_ERR_OOM;
   if (opts) h->opts = *opts; else pselinv_default_opts(&h->opts);
-  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 256 || h->opts.nd_leaf < 0) {
+  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 256 || h->opts.nd_leaf < 0 ||
+      (h->opts.factor_precision != PSELINV_PREC_FP64 &&
+       h->opts.factor_precision != PSELINV_PREC_OZAKI_FP16)) {
     delete h;
     return PSELINV_ERR_ARG;
   }
@@ -1822,7 +1892,9 @@ int pselinv_analyze_general(int64_t n, const int64_t* colptr, const int64_t* row
   pselinv_ctx* h = new (std::nothrow) pselinv_ctx();
   if (!h) return PSELINV_ERR_OOM;
   if (opts) h->opts = *opts; else pselinv_default_opts(&h->opts);
-  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 256 || h->opts.symmetric) {
+  if (h->opts.max_supernode < 1 || h->opts.max_supernode > 256 || h->opts.symmetric ||
+      (h->opts.factor_precision != PSELINV_PREC_FP64 &&
+       h->opts.factor_precision != PSELINV_PREC_OZAKI_FP16)) {
     delete h;
     return PSELINV_ERR_ARG;
   }
@@ -1902,7 +1974,9 @@ int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, v
     CK(prepare_map_kernels());
     CK(prepare_ozaki_kernels());
     h->slices = h->opts.slices <= 0 ? 6 : std::min(6, std::max(4, (int)h->opts.slices));
-    int rc = build_factor_plan(h);
+  }
+  if (!h->factor_plan.built) {
+    const int rc = build_factor_plan(h);
     if (rc != PSELINV_OK) return rc;
   }
   h->factored = h->inverted = false;
@@ -2054,6 +2128,15 @@ int pselinv_import_block(pselinv_t h, int64_t K, int64_t batch, const void* in, 
   const int rc = block_transfer(h, K, batch, const_cast<void*>(in), true, (cudaStream_t)stream);
   if (rc == PSELINV_OK && h) h->inverted = true;
   return rc;
+}
+
+int pselinv_set_factor_precision(pselinv_t h, int precision, int32_t split_mflops) {
+  if (!h || (precision != PSELINV_PREC_FP64 && precision != PSELINV_PREC_OZAKI_FP16))
+    return PSELINV_ERR_ARG;
+  h->opts.factor_precision = precision;
+  h->opts.factor_split_mflops = split_mflops;
+  h->factor_plan.release();
+  return PSELINV_OK;
 }
 
 int pselinv_set_schedule(pselinv_t h, int schedule) {

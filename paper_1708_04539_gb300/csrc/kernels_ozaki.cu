@@ -60,21 +60,36 @@ __device__ __forceinline__ int exp_of_max(unsigned long long bits) {
   const int E = (int)(bits >> 52);
   return E == 0 ? 0 : E - 1022;
 }
-// Q = rint(x 2^{sh0}) as a signed integer, from the bits of x (|Q| <= 2^{7S})
-__device__ __forceinline__ long long fixed_point(double x, int sh0) {
-  const long long b = __double_as_longlong(x);
+// |Q| = rint(|x| 2^{sh0}) (|Q| <= 2^{7S}, from the bits of x) split at bit
+// B: lo = |Q| mod 2^B and hi = |Q| >> B, returned as exact floats that
+// carry the sign of x (both below 2^23 in magnitude)
+__device__ __forceinline__ void fixed_point_split(double x, int sh0, int B, float& lo, float& hi) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7FF);
-  if (E == 0) return 0;
-  const long long M = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);  // x = +-M 2^{E-1075}
-  const int sh = E - 1075 + sh0;
-  long long q;
-  if (sh >= 0) {
-    q = M << (sh < 10 ? sh : 10);
-  } else {
-    const int r = -sh;
-    q = r >= 62 ? 0 : (M + (1ll << (r - 1))) >> r;
+  const int r = 1075 - E - sh0;  // |x| 2^{sh0} = M 2^{-r}
+  unsigned long long q = 0;
+  if (E != 0 && r < 54) {  // r >= 54: below one half
+    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int rr = r < 1 ? 1 : r;  // r > 7 for every |x| below 2^e
+    q = (M + (1ull << (rr - 1))) >> rr;
   }
-  return b < 0 ? -q : q;
+  const uint32_t ql = (uint32_t)q & ((1u << B) - 1u);
+  const uint32_t qh = (uint32_t)(q >> B);
+  // 2^23 + k has the bits 0x4B000000 | k (k < 2^23)
+  const float sg = (long long)b < 0 ? -1.0f : 1.0f;
+  lo = __fmaf_rn(__uint_as_float(0x4B000000u | ql), sg, -8388608.0f * sg);
+  hi = __fmaf_rn(__uint_as_float(0x4B000000u | qh), sg, -8388608.0f * sg);
+}
+
+// One balanced base-128 digit of an integer-valued float v (|v| < 2^22):
+// v = 128 t + a with t = rint(v / 128) (ties to even) and |a| <= 64; v
+// becomes t.  All three operations are exact.
+__device__ __forceinline__ float digit_step(float& v) {
+  constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: adding it rounds to an integer
+  const float t = __fsub_rn(__fmaf_rn(v, 0.0078125f, kRound), kRound);
+  const float a = __fmaf_rn(-128.0f, t, v);
+  v = t;
+  return a;
 }
 
 // Work item of the slicing kernels: thread t of a task covers row
@@ -133,39 +148,51 @@ __device__ __forceinline__ void slice_max_task(const SliceDesc& d, const SliceTa
 
 // The S balanced base-128 digits of 8 values x of one row with exponent e,
 // written as the 16 bytes [16 tid, 16 tid + 16) of the 4 KB tile of every
-// slice at `dst` (slices `slice_stride` halves apart).  Q (|Q| <= 2^{7S})
-// is split once into its low 7 L bits (L = S / 2 digits, non-negative) and
-// the rest, so that the digits come from 32-bit arithmetic: the low digits
-// leave a carry of 0 or 1 into the high part.  The digits are the same as
-// those of the 64-bit recurrence a = ((Q + 64) & 127) - 64, Q = (Q - a) / 128.
-__device__ __forceinline__ void write_digits(const double (&x)[8], int e, int S, __half* dst,
-                                             int64_t slice_stride) {
+// slice at `dst` (slices `slice_stride` halves apart).  Q = rint(x 2^{7S-e})
+// (|Q| <= 2^{7S}) is split once into its low 7 L bits (L = S / 2 digits)
+// and the rest, both exact floats, so that the digits come from FP32
+// arithmetic: the low digits leave a carry of -1, 0 or 1 into the high
+// part.  Digits below the top one lie in [-64, 64]; the top one is what
+// remains (|a| <= 129), and sum_s a_s 128^{S-1-s} = Q exactly.
+template <int S>
+__device__ __forceinline__ void write_digits_s(const double (&x)[8], int e, __half* dst,
+                                               int64_t slice_stride) {
+  constexpr int L = S / 2;
   const int sh0 = 7 * S - e;
-  const int L = S / 2;
-  int lo[8], hi[8];
+  float lo[8], hi[8];
 #pragma unroll
-  for (int j = 0; j < 8; j++) {
-    const long long q = fixed_point(x[j], sh0);
-    lo[j] = (int)(q & ((1ll << (7 * L)) - 1));
-    hi[j] = (int)(q >> (7 * L));
-  }
-  // balanced base-128 digits from the least significant slice upwards
+  for (int j = 0; j < 8; j++) fixed_point_split(x[j], sh0, 7 * L, lo[j], hi[j]);
+  // from the least significant slice upwards
+#pragma unroll
   for (int s = S - 1; s >= 0; s--) {
-    __align__(16) __half h[8];
-    const bool low = s >= S - L;
+    float a[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-      int& v = low ? lo[j] : hi[j];
-      int a = v;
-      if (s > 0) {
-        a = ((v + 64) & 127) - 64;
-        v = (v - a) >> 7;
+      if (s >= S - L) {
+        a[j] = digit_step(lo[j]);
+        if (s == S - L) hi[j] += lo[j];  // carry of the low digits (exact)
+      } else {
+        a[j] = s > 0 ? digit_step(hi[j]) : hi[j];
       }
-      if (s == S - L) hi[j] += lo[j];  // carry of the low digits
-      h[j] = __int2half_rn(a);
     }
-    *reinterpret_cast<uint4*>(dst + s * slice_stride) = *reinterpret_cast<uint4*>(h);
+    uint4 w;
+    __half2 h0 = __floats2half2_rn(a[0], a[1]), h1 = __floats2half2_rn(a[2], a[3]);
+    __half2 h2 = __floats2half2_rn(a[4], a[5]), h3 = __floats2half2_rn(a[6], a[7]);
+    w.x = *reinterpret_cast<uint32_t*>(&h0);
+    w.y = *reinterpret_cast<uint32_t*>(&h1);
+    w.z = *reinterpret_cast<uint32_t*>(&h2);
+    w.w = *reinterpret_cast<uint32_t*>(&h3);
+    *reinterpret_cast<uint4*>(dst + s * slice_stride) = w;
   }
+}
+__device__ __forceinline__ void write_digits(const double (&x)[8], int e, int S, __half* dst,
+                                             int64_t slice_stride) {
+  if (S == 6)
+    write_digits_s<6>(x, e, dst, slice_stride);
+  else if (S == 5)
+    write_digits_s<5>(x, e, dst, slice_stride);
+  else
+    write_digits_s<4>(x, e, dst, slice_stride);
 }
 
 // Slices of one task (see the work item above); exponents from d.maxbits.
@@ -664,7 +691,12 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
           }
         }
       }
-      if (!ok) abort_flag = 1;
+      if (!ok) {
+        abort_flag = 1;
+        // let the copies already issued land before the CTA exits (bounded)
+        for (uint32_t k = g > (uint32_t)kOzStages ? g - kOzStages : 0u; k < g; k++)
+          mbar_wait(smem_u32(&bar_full[k % kOzStages]), (k / kOzStages) & 1);
+      }
     }
   } else if (warp == kOzDrainWarps + 1) {
     // ---- MMA issue ----
@@ -712,7 +744,12 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
           }
         }
       }
-      if (!ok) abort_flag = 1;
+      if (!ok) {
+        abort_flag = 1;
+        // the MMAs already issued complete in order: wait (bounded) for the
+        // last commit before the accumulators are freed
+        if (g > 0) mbar_wait(smem_u32(&bar_free[(g - 1) % kOzStages]), ((g - 1) / kOzStages) & 1);
+      }
     }
   } else {
     // ---- drain and epilogue (warps 0-7) ----

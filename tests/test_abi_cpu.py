@@ -138,6 +138,25 @@ def test_error_strings_and_defaults():
     o = ps.binding.Opts()
     lib.pselinv_default_opts(ctypes.byref(o))
     assert o.max_supernode == 256 and o.relax_pct == 20 and o.use_graph == 1
+    assert o.factor_precision == ps.PREC_FP64 and o.factor_split_mflops == 0
+
+
+def test_factor_precision_option_is_checked():
+    """opts.factor_precision takes PREC_FP64 or PREC_OZAKI_FP16 only, at
+    analysis and through the setter (host-only handles: no CUDA call)."""
+    p = gen.tridiagonal(5, 1)
+    for bad in (2, -1):
+        with pytest.raises(ps.PselinvError) as e:
+            ps.SelInv.from_problem(p, host_only=True, factor_precision=bad)
+        assert e.value.code == -1
+        with pytest.raises(ps.PselinvError):
+            ps.SelInv.from_general_problem(p, host_only=True, factor_precision=bad)
+    h = ps.SelInv.from_problem(p, host_only=True, factor_precision=ps.PREC_OZAKI_FP16,
+                               factor_split_mflops=-1)
+    h.set_factor_precision(ps.PREC_FP64)
+    with pytest.raises(ps.PselinvError):
+        h.set_factor_precision(3)
+    h.close()
 
 
 def _compare_with_oracle(p, relax):
