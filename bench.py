@@ -37,6 +37,7 @@ METRIC = "selinv_fp64_equiv_gflops"
 UNIT = "GFLOP/s"
 HEADLINE_CONFIG = 5
 WORKLOADS = {
+    1: "2D 5-point convection-diffusion {m}^2 (n={n}), FP64, nested dissection, max supernode 64",
     2: "3D 7-point upwind convection-diffusion {m}^3 (n={n}), FP64, nested dissection, "
        "max supernode 256, relaxed supernodes (<=20% explicit zeros)",
     3: "3D 27-point complex operator A = H - zS + 0.2N on a {m}^3 grid (n={n}), complex128, "
@@ -47,9 +48,9 @@ WORKLOADS = {
        "upwind face blocks, FP64, nested dissection on the element grid, max supernode 256, "
        "relaxed supernodes (<=20% explicit zeros)",
 }
-DEFAULT_SIZE = {2: 40, 3: 60, 4: 32, 5: 16}
+DEFAULT_SIZE = {1: 31, 2: 40, 3: 60, 4: 32, 5: 16}
 # unknowns of the leading nested-dissection subdomain the CPU oracle is timed on
-SAMPLE_TARGET_N = {2: 4000, 3: 2000, 4: 4000, 5: 2048}
+SAMPLE_TARGET_N = {1: 961, 2: 4000, 3: 2000, 4: 4000, 5: 2048}
 # smaller matrices of the same family whose tuner records train the cost model
 TRAIN_SIZES = {2: (20, 24, 28), 5: (8, 10, 12)}
 SLICES = 6
@@ -91,9 +92,10 @@ def parse(argv=None):
     ap.add_argument("--size", type=int, default=None,
                     help="grid side (elements per side for the DG operator; default: the "
                          "configuration's own; smaller for profiling captures)")
-    ap.add_argument("--config", type=int, default=HEADLINE_CONFIG, choices=[2, 3, 4, 5],
-                    help="5: 16^3 x 64 DG operator (default); 2: 40^3 upwind; 3: 60^3 complex "
-                         "27-point; 4: 40 complex shifts of a 32^3 operator")
+    ap.add_argument("--config", type=int, default=HEADLINE_CONFIG, choices=[1, 2, 3, 4, 5],
+                    help="5: 16^3 x 64 DG operator (default); 1: 31^2 convection-diffusion; "
+                         "2: 40^3 upwind; 3: 60^3 complex 27-point; 4: 40 complex shifts of a "
+                         "32^3 operator and 64 uneven 2D grids in one sweep")
     return ap.parse_args(argv)
 
 
@@ -430,7 +432,7 @@ def time_steps(h, prec, stream, steps, out_dev, warm=True):
     return e0.elapsed_time(e1) / steps
 
 
-def comparison(p, h, stream, out_dev, flops, big, refactor=None):
+def comparison(p, h, stream, out_dev, flops, big, refactor=None, option_arm=True):
     """FP64 level-batched and FP64 per-supernode sweeps of the same matrix,
     and the error of the split-precision result against the FP64 one.
 
@@ -495,7 +497,7 @@ def comparison(p, h, stream, out_dev, flops, big, refactor=None):
     if refactor is not None:
         out.update({"fp64_factor_ms": fp64_factor_ms,
                     "split_sweep_on_fp64_factors_selected_error": split_sweep_err})
-    if not big:
+    if not big and option_arm:
         # option: normalisation and D_K as sliced products too
         q = ps.SelInv.from_problem(p, relax_pct=20, split_normalise=True)
         with torch.cuda.stream(stream):
@@ -687,11 +689,13 @@ def run_ours(args):
     config = args.config
     p = gen.make_config(config, size=args.size)
     nmat = 1
+    sample_p = p
     if config == 4:
         # the pole-expansion batch: every shift of the 3D operator and every
         # uneven 2D grid is a member of one group (pselinv_group), so one
         # sweep with one launch per kernel kind and level covers all of them
         fam, grids = p[0], p[1:]
+        sample_p = fam
         p = group_problem(fam, grids)
         nmat = fam.nbatch + len(grids)
     size = args.size or DEFAULT_SIZE[config]
@@ -894,13 +898,14 @@ def run_ours(args):
         line["roofline"] = None
     if learned_rec is not None:
         line["learned"] = learned_rec
-    if not args.no_compare and args.precision == "ozaki" and rank == 0 and headline:
+    if not args.no_compare and args.precision == "ozaki" and rank == 0:
         line["comparison"] = comparison(p, h, stream, out_dev[0], flops, big,
-                                        vals_dev if fprec == ps.PREC_OZAKI_FP16 else None)
+                                        vals_dev if fprec == ps.PREC_OZAKI_FP16 else None,
+                                        option_arm=config != 4)
         log("comparison done")
     h.close()
-    if rank == 0 and world == 1 and not args.skip_cpu_baseline and headline:
-        line["cpu_baseline"] = cpu_baseline(p, SAMPLE_TARGET_N[config])
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sample_p, SAMPLE_TARGET_N[config])
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
