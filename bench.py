@@ -87,6 +87,15 @@ def parse(argv=None):
                     help="write the launch-by-launch profile (JSON) to this path")
     ap.add_argument("--factor-precision", default="auto", choices=["auto", "fp64", "ozaki"],
                     help="Schur products of the factorisation: auto = the sweep's precision")
+    ap.add_argument("--slices", type=int, default=0, choices=[0, 4, 5, 6],
+                    help="FP16 slices per operand of the split products (0: the library's "
+                         "default, 6)")
+    ap.add_argument("--ozaki-a-tmem", action="store_true",
+                    help="sliced GEMM reads its A slices from tensor memory (default: from "
+                         "shared memory)")
+    ap.add_argument("--capture", action="store_true",
+                    help="profiler runs: one factorisation and one sweep (plan from --plan-in, "
+                         "or the untuned heuristic), nothing timed, no JSON line")
     ap.add_argument("--split-normalise", action="store_true",
                     help="also slice the normalisation and D_K (by default they stay FP64)")
     ap.add_argument("--size", type=int, default=None,
@@ -710,7 +719,8 @@ def run_ours(args):
     fprec_name = args.precision if args.factor_precision == "auto" else args.factor_precision
     fprec = ps.PREC_OZAKI_FP16 if fprec_name == "ozaki" else ps.PREC_FP64
     hkw = dict(relax_pct=20, schedule=sched, use_graph=not args.no_graph,
-               split_normalise=args.split_normalise, factor_precision=fprec)
+               split_normalise=args.split_normalise, factor_precision=fprec,
+               slices=args.slices, ozaki_a_tmem=args.ozaki_a_tmem)
     if config == 4:
         members = [ps.SelInv.from_problem(q, host_only=True, relax_pct=20)
                    for q in p.meta["members"]]
@@ -733,6 +743,18 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         h.factor(vals_dev, stream=stream)
     torch.cuda.synchronize()
+    if args.capture:  # one sweep for a profiler
+        prec = ps.PREC_OZAKI_FP16 if args.precision == "ozaki" else ps.PREC_FP64
+        if args.plan_in:
+            with open(args.plan_in) as f:
+                h.plan_set([tuple(t) for t in json.load(f)["triples"]], prec)
+        with torch.cuda.stream(stream):
+            h.selinv(precision=prec, stream=stream)
+            h.get_selected(out_dev[0], stream=stream)
+        torch.cuda.synchronize()
+        h.close()
+        log("capture run done")
+        return 0
     factor_ms = None
     if e2e_steps <= 0:
         with torch.cuda.stream(stream):

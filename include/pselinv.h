@@ -97,15 +97,22 @@ typedef struct pselinv_opts {
                             > 0 the nested-dissection ordering of pselinv_order_nd with
                             leaves of at most nd_leaf vertices (see the structure's perm) */
   int32_t factor_precision; /* PSELINV_PREC_FP64 (default) or PSELINV_PREC_OZAKI_FP16: the
-                            Schur-complement products L_{C,K} U_{K,C} of pselinv_factor as
-                            sliced FP16 tensor-core products (exact FP32 accumulation,
-                            FP64 result) on the levels whose products reach
-                            factor_split_mflops; the diagonal LU, the triangular solves
-                            and the scatter into the ancestors stay FP64 */
+                            panel solves L_{C,K} = A_{C,K} U_KK^{-1}, U_{K,C}^T =
+                            A_{K,C}^T L_KK^{-T} and the Schur-complement products
+                            L_{C,K} U_{K,C} of pselinv_factor as sliced FP16 tensor-core
+                            products (exact FP32 accumulation, FP64 result) on the levels
+                            whose Schur products reach factor_split_mflops; the diagonal
+                            LU, the triangular inverses and the scatter into the
+                            ancestors stay FP64 */
   int32_t factor_split_mflops; /* factor_precision = OZAKI_FP16: smallest Schur-product work
                             (MFLOP) of a level that goes split; 0 = default (200); < 0:
                             every level */
-  int32_t reserved[3];
+  int32_t ozaki_a_tmem;  /* sliced products: 0 (default) the MMAs read the A slices straight
+                            from shared memory (each A tile once per slice pair); 1 from
+                            tensor memory, copied there once per K half (tcgen05.cp; the
+                            64-bit totals then live in shared memory).  The same exact
+                            integer sums either way; 1 measured slower on GB300. */
+  int32_t reserved[2];
 } pselinv_opts;
 
 typedef struct pselinv_ctx* pselinv_t;

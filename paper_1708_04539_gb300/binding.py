@@ -68,7 +68,7 @@ class Opts(ctypes.Structure):
                 ("host_only", ctypes.c_int32), ("split_normalise", ctypes.c_int32),
                 ("symmetric", ctypes.c_int32), ("nd_leaf", ctypes.c_int32),
                 ("factor_precision", ctypes.c_int32), ("factor_split_mflops", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("ozaki_a_tmem", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 _P64 = ctypes.POINTER(ctypes.c_int64)
@@ -253,7 +253,7 @@ class SelInv:
     def _opts(lib, max_supernode=256, relax_pct=20, schedule=SCHED_LEVEL, use_graph=True,
               check_level=0, precision=PREC_FP64, slices=0, host_only=False,
               split_normalise=False, symmetric=False, nd_leaf=0, factor_precision=PREC_FP64,
-              factor_split_mflops=0):
+              factor_split_mflops=0, ozaki_a_tmem=False):
         opts = Opts()
         lib.pselinv_default_opts(ctypes.byref(opts))
         opts.max_supernode = int(max_supernode)
@@ -269,6 +269,7 @@ class SelInv:
         opts.nd_leaf = int(nd_leaf)  # perm None: 0 natural order, > 0 nested dissection
         opts.factor_precision = int(factor_precision)
         opts.factor_split_mflops = int(factor_split_mflops)
+        opts.ozaki_a_tmem = 1 if ozaki_a_tmem else 0
         return opts
 
     def __init__(self, n, colptr, rowind, perm=None, **kw):

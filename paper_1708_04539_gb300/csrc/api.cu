@@ -54,7 +54,8 @@ enum StepKind {
   ST_LU_PANEL,
   ST_SMALL_LEVEL,
   ST_GSLICE,
-  ST_OUTMAX
+  ST_OUTMAX,
+  ST_MIRROR
 };
 
 struct Step {
@@ -335,8 +336,10 @@ template <>
 void gemm_features<GemmDesc>(Step& st, const std::vector<GemmDesc>& descs, double);
 
 // GEMM step from a list of descriptors; tasks enumerate every tile and K chunk
+// lower_c: only the tasks of C on or below its diagonal (a symmetric
+// product whose upper triangle nobody reads)
 void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& descs, int level,
-                   int slot = -1) {
+                   int slot = -1, bool lower_c = false) {
   if (descs.empty()) return;
   if (cfg == GEMM_ROWS)
     for (const GemmDesc& g : descs)
@@ -360,6 +363,7 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
           if (kb >= ke) continue;
           const double kw = ke - kb;
           for (int tm = 0; tm < ceil_div(g.M, kRowsBlock); tm++) {
+            if (lower_c && (tm + 1) * kRowsBlock <= j0) continue;  // above the diagonal
             tasks.push_back({(int)d, tm, tn, nw + 16 * ks});
             work.push_back(kw * nw * std::min(kRowsBlock, g.M - tm * kRowsBlock));
           }
@@ -369,9 +373,11 @@ void add_gemm_step(Plan& P, int dtype, int cfg, const std::vector<GemmDesc>& des
       const int bm = gemm_tile_m(dtype, cfg), bn = gemm_tile_n(dtype, cfg);
       for (int ks = 0; ks < g.ksplit; ks++)
         for (int tn = 0; tn < ceil_div(g.N, bn); tn++)
-          for (int tm = 0; tm < ceil_div(g.M, bm); tm++) tasks.push_back({(int)d, tm, tn, ks});
+          for (int tm = 0; tm < ceil_div(g.M, bm); tm++)
+            if (!lower_c || (tm + 1) * bm > tn * bn) tasks.push_back({(int)d, tm, tn, ks});
     }
     double f = 2.0 * g.M * g.N * g.K;
+    if (lower_c) f = (double)g.M * (g.N + 1) * g.K;  // the lower triangle of a square C
     if (g.tri == GEMM_TRI_LOWER_B || g.tri == GEMM_TRI_UPPER_B) f = (double)g.M * g.N * (g.N + 1);
     if (g.tri == (GEMM_TRI_UPPER_A | GEMM_TRI_LOWER_B)) f = 2.0 * g.N * (double)g.N * g.N / 3.0;
     flops += f * (dtype == DT_F64 ? 1 : 4);
@@ -516,9 +522,10 @@ size_t scratch_need(const HostSym& H, int64_t nb, size_t es) {
     for (int64_t i = H.hlevel_ptr[d]; i < H.hlevel_ptr[d + 1]; i++) {
       const int64_t K = H.hlevel_sn[i], s = H.sn_width[K], c = cK(H, K), cu = cU(H, K);
       f += 2 * s * s + (c + cu) * s + c * cu;
-      if (c > 0 && cu > 0)
-        oz += parts * (slice_bytes(c, s, 6) + slice_bytes(cu, s, 6)) + exps_bytes(c) +
-              exps_bytes(cu) + 1024 + (size_t)(c + cu) * 8;
+      if (c > 0 && cu > 0)  // A_{C,K}, A_{K,C}^T, Uinv, Linv (the solves; then TL, TU)
+        oz += parts * (slice_bytes(c, s, 6) + slice_bytes(cu, s, 6) + 2 * slice_bytes(s, s, 6)) +
+              exps_bytes(c) + exps_bytes(cu) + 2 * exps_bytes(s) + 2048 +
+              (size_t)(c + cu + 2 * s) * 8;
     }
     fmax = std::max(fmax, align256((size_t)(f * nb) * es) + oz * (size_t)nb + 512);
   }
@@ -629,14 +636,19 @@ void add_copy_step(Plan& P, const std::vector<CopySeg>& segs, int level, size_t 
 // panels: 61.9 vs 60.9 ms for the 40^3 factorisation)
 constexpr int kLuUpdateCfg = GEMM_32x32;
 
-// one Schur-complement product of the factorisation: Sc = TL TU^T (c x cu,
-// K = s), TL = L_{C,K} (c x s) and TU = U_{K,C}^T (cu x s), column major
+// one supernode's products of the factorisation: the triangular solves
+// TL = AL Uinv (AL = A_{C,K}, c x s) and TU = AU Linv^T (AU = A_{K,C}^T,
+// cu x s), and the Schur complement Sc = TL TU^T (c x cu, K = s); column
+// major
 struct SchurProduct {
   char *TL, *TU, *Sc;
   int c, cu, s;
+  const char *AL, *AU, *Uinv, *Linv;
 };
+void add_ozaki_trsm(pselinv_ctx* h, Plan& P, const std::vector<SchurProduct>& prods, int lev,
+                    size_t base);
 void add_ozaki_schur(pselinv_ctx* h, Plan& P, const std::vector<SchurProduct>& prods, int lev,
-                     size_t base);
+                     size_t base, bool lower);
 
 int build_factor_plan(pselinv_ctx* h) {
   const HostSym& H = h->H;
@@ -654,6 +666,12 @@ int build_factor_plan(pselinv_ctx* h) {
   Step sv;
   sv.kind = ST_SCATTER_VALUES;
   P.steps.push_back(sv);
+  // symmetric values (A = A^T): U_{K,C}^T = A_{C,K} L_KK^{-T} and the Schur
+  // complement is symmetric, so the updates go to the lower triangle only
+  // (entries (x, y), x >= y: diagonal blocks and L panels; half the Schur
+  // work) and U^T panels are solved from the L panels; each diagonal block's
+  // upper triangle is mirrored from its lower one before its LU
+  const bool ldlt = h->opts.symmetric != 0 && !H.general;
   for (size_t lev = 0; lev + 1 < H.hlevel_ptr.size(); lev++) {
     std::vector<SnTask> diag, gt;
     std::vector<TriBlock> tri;
@@ -685,13 +703,13 @@ int build_factor_plan(pselinv_ctx* h) {
           trsm.push_back(make_desc(Lp, Uinv, TL, c, s, s, c, s, c, 0, 0, 1.0, 0.0, 0, 1,
                                    GEMM_TRI_UPPER_B));
         if (cu > 0)
-          trsm.push_back(make_desc(Up, Linv, TU, cu, s, s, cu, s, cu, 0, 1, 1.0, 0.0, 0, 1,
-                                   GEMM_TRI_UPPER_B));
+          trsm.push_back(make_desc(ldlt ? Lp : Up, Linv, TU, cu, s, s, cu, s, cu, 0, 1, 1.0, 0.0,
+                                   0, 1, GEMM_TRI_UPPER_B));
         if (c > 0 && cu > 0) {
           schur.push_back(make_desc(TL, TU, Sc, c, cu, s, c, cu, c, 0, 1, 1.0, 0.0));
-          sprods.push_back({TL, TU, Sc, (int)c, (int)cu, (int)s});
+          sprods.push_back({TL, TU, Sc, (int)c, (int)cu, (int)s, Lp, ldlt ? Lp : Up, Uinv, Linv});
           for (int tq = 0; tq < ceil_div(cu, 32); tq++)
-            for (int tp = 0; tp < ceil_div(c, 32); tp++) {
+            for (int tp = ldlt ? tq : 0; tp < ceil_div(c, 32); tp++) {
               gt.push_back({(int)b, (int)K, tp, tq});
               gofs.push_back(s0);
             }
@@ -703,6 +721,14 @@ int build_factor_plan(pselinv_ctx* h) {
     // batched over the level's supernodes
     int64_t smax = 0;
     for (const SnTask& t : diag) smax = std::max<int64_t>(smax, H.sn_width[t.K]);
+    if (ldlt && !diag.empty()) {
+      Step mr;
+      mr.kind = ST_MIRROR;
+      mr.n = (int)diag.size();
+      mr.tasks = P.push(diag);
+      mr.level = (int)lev;
+      P.steps.push_back(mr);
+    }
     for (int64_t j0 = 0; j0 < smax; j0 += 32) {
       std::vector<SnTask> piv, pan;
       std::vector<GemmDesc> upd;
@@ -731,25 +757,32 @@ int build_factor_plan(pselinv_ctx* h) {
       }
       add_gemm_step(P, dt, kLuUpdateCfg, upd, (int)lev);
     }
-    add_tri_step(P, H, tri, (int)lev, 0);
-    add_gemm_step(P, dt, GEMM_ROWS, trsm, (int)lev);
-    // split precision: the Schur products of levels with enough work as
-    // sliced tensor-core products; otherwise FP64 row panels, which beat
-    // 64 x 64 tiles on these products at every width (40^3 factorisation
-    // 61.9 -> 57.1 ms)
+    // split precision: the triangular solves and the Schur products of
+    // levels with enough Schur work as sliced tensor-core products (their
+    // operands sliced from the level's scratch after its FP64 region);
+    // otherwise FP64 row panels, which beat 64 x 64 tiles on these products
+    // at every width (40^3 factorisation 61.9 -> 57.1 ms)
     double sflops = 0;
     for (const SchurProduct& q : sprods) sflops += 2.0 * q.c * q.cu * q.s;
     const double min_flops = h->opts.factor_split_mflops < 0    ? 0.0
                              : h->opts.factor_split_mflops == 0 ? 2e8
                                                                 : 1e6 * h->opts.factor_split_mflops;
-    if (h->opts.factor_precision == PSELINV_PREC_OZAKI_FP16 && !sprods.empty() &&
-        sflops >= min_flops)
-      add_ozaki_schur(h, P, sprods, (int)lev, align256((size_t)off * es));
+    const bool split = h->opts.factor_precision == PSELINV_PREC_OZAKI_FP16 && !sprods.empty() &&
+                       sflops >= min_flops;
+    add_tri_step(P, H, tri, (int)lev, 0);
+    if (split && sprods.size() * 2 == trsm.size()) {
+      add_ozaki_trsm(h, P, sprods, (int)lev, align256((size_t)off * es));
+    } else {
+      add_gemm_step(P, dt, GEMM_ROWS, trsm, (int)lev);
+    }
+    if (split)
+      add_ozaki_schur(h, P, sprods, (int)lev, align256((size_t)off * es), ldlt);
     else
-      add_gemm_step(P, dt, GEMM_ROWS, schur, (int)lev);
+      add_gemm_step(P, dt, GEMM_ROWS, schur, (int)lev, -1, ldlt);
     if (!gt.empty()) {
       Step sc;
       sc.kind = ST_SCATTER_SUB;
+      sc.cfg = ldlt ? 1 : 0;
       sc.n = (int)gt.size();
       sc.tasks = P.push(gt);
       sc.offs = P.push(gofs);
@@ -898,7 +931,7 @@ bool set_ozaki_ksplit(std::vector<OzDesc>& descs, int ks, bool force_atomic) {
 }
 
 void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool force_atomic,
-                     int ks, int slot) {
+                     int ks, int slot, bool lower_c = false) {
   if (descs.empty()) return;
   std::vector<OzTask> tasks;
   double flops = 0, bytes = 0;
@@ -910,8 +943,9 @@ void add_ozgemm_step(Plan& P, std::vector<OzDesc>& descs, int S, int level, bool
     // DRAM once and from L2 for the others
     for (int k = 0; k < g.ksplit; k++)
       for (int tm = 0; tm < ceil_div(g.M, 128); tm++)
-        for (int tn = 0; tn < ceil_div(g.N, 64); tn++) tasks.push_back({(int)d, tm, tn, k});
-    flops += 2.0 * g.M * g.N * (double)g.K32 * 32;
+        for (int tn = 0; tn < ceil_div(g.N, 64); tn++)
+          if (!lower_c || (tm + 1) * 128 > tn * 64) tasks.push_back({(int)d, tm, tn, k});
+    flops += (lower_c ? 1.0 : 2.0) * g.M * g.N * (double)g.K32 * 32;
     // slices of both operands read once, the FP64 result written (read too
     // when accumulated)
     bytes += 2.0 * S * ((double)g.M + g.N) * g.K32 * 32 +
@@ -998,12 +1032,57 @@ struct OzBuilder {
   }
 };
 
+// Triangular solves of one factorisation level as sliced products (K = s):
+// TL = AL Uinv (B(n, k) = Uinv(k, n)) and TU = AU Linv^T (B(n, k) =
+// Linv(n, k)); Uinv and Linv hold exact zeros outside their triangles, so
+// the full products are the triangular ones.  For symmetric values AU is AL
+// and its slices serve both products.  Scratch from `base`.
+void add_ozaki_trsm(pselinv_ctx* h, Plan& P, const std::vector<SchurProduct>& prods, int lev,
+                    size_t base) {
+  OzBuilder ob(h, base);
+  int64_t nmax = 0;
+  for (const SchurProduct& q : prods) nmax += q.c + q.cu + 2 * q.s;
+  unsigned long long* maxbase = (unsigned long long*)ob.take((size_t)nmax * 8 + 8);
+  std::vector<SliceDesc> sl;
+  std::vector<OzDesc> out;
+  int64_t moff = 0;
+  for (const SchurProduct& q : prods) {
+    SliceDesc al = ob.slice(q.AL, q.c, SLICE_ROWS, q.c, q.s);
+    al.maxbits = maxbase + moff;
+    SliceDesc ub = ob.slice(q.Uinv, q.s, SLICE_COLS, q.s, q.s);
+    ub.maxbits = maxbase + moff + q.c;
+    SliceDesc lb = ob.slice(q.Linv, q.s, SLICE_ROWS, q.s, q.s);
+    lb.maxbits = maxbase + moff + q.c + q.s;
+    SliceDesc au = al;
+    if (q.AU != q.AL) {
+      au = ob.slice(q.AU, q.cu, SLICE_ROWS, q.cu, q.s);
+      au.maxbits = maxbase + moff + q.c + 2 * q.s;
+      sl.push_back(au);
+    }
+    moff += q.c + q.cu + 2 * q.s;
+    sl.push_back(al);
+    sl.push_back(ub);
+    sl.push_back(lb);
+    ob.product(out, al, ub, q.TL, q.c, q.c, q.s, 1.0);
+    ob.product(out, au, lb, q.TU, q.cu, q.cu, q.s, 1.0);
+  }
+  Step ms;
+  ms.kind = ST_MEMSET;
+  ms.ptr = maxbase;
+  ms.bytes = (size_t)nmax * 8;
+  ms.level = lev;
+  P.steps.push_back(ms);
+  add_slice_step(P, sl, lev, true);
+  add_slice_step(P, sl, lev, false);
+  add_ozgemm_step(P, out, h->slices, lev, false, 1, 0);
+}
+
 // Schur products of one factorisation level as sliced products: row maxima
 // and slices of TL and TU (both by rows: A = TL, B = TU with K = s), then
 // the products into the FP64 Sc blocks the scatter subtracts.  Scratch from
 // `base` (bytes), after the level's FP64 region.
 void add_ozaki_schur(pselinv_ctx* h, Plan& P, const std::vector<SchurProduct>& prods, int lev,
-                     size_t base) {
+                     size_t base, bool lower) {
   OzBuilder ob(h, base);
   int64_t nmax = 0;
   for (const SchurProduct& q : prods) nmax += q.c + q.cu;
@@ -1030,7 +1109,7 @@ void add_ozaki_schur(pselinv_ctx* h, Plan& P, const std::vector<SchurProduct>& p
   add_slice_step(P, sl, lev, true);
   add_slice_step(P, sl, lev, false);
   // K = s <= 256 is one exact chunk: no K split, no accumulation
-  add_ozgemm_step(P, out, h->slices, lev, false, 1, 0);
+  add_ozgemm_step(P, out, h->slices, lev, false, 1, 0, lower);
 }
 
 // Split-precision normalisation of one depth level (Algorithm 1 step 2 and
@@ -1628,7 +1707,7 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
                                    (const SnTask*)(a + s.tasks), s.n, st);
       else
         launch_scatter_sub(h->dtype, h->S, h->lu, h->scratch, (const int64_t*)(a + s.offs),
-                           (const SnTask*)(a + s.tasks), s.n, st);
+                           (const SnTask*)(a + s.tasks), s.n, s.cfg == 1, st);
       break;
     case ST_COPY:
       launch_copy(h->dtype, (const CopySeg*)(a + s.tasks), s.n, s.grid, st);
@@ -1645,7 +1724,7 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       break;
     case ST_OZGEMM:
       launch_ozaki_gemm(s.cfg, (const OzDesc*)(a + s.descs), (const OzTask*)(a + s.tasks), s.n,
-                        h->derr, s.side == 0, st);
+                        h->derr, s.side == 0, h->opts.ozaki_a_tmem != 0, st);
       break;
     case ST_ZERO:
       launch_zero((const CopySeg*)(a + s.tasks), s.n, s.grid, st);
@@ -1658,6 +1737,9 @@ void launch_step(pselinv_ctx* h, const Plan& P, const Step& s, cudaStream_t st) 
       launch_gslice(h->dtype, h->S, h->ainv, (const SliceDesc*)(a + s.descs),
                     (const GTileTask*)(a + s.tasks), s.n, (const SliceTask*)(a + s.offs), s.n2,
                     s.cfg == 1, h->rcmax, st);
+      break;
+    case ST_MIRROR:
+      launch_mirror_lower(h->dtype, h->S, h->lu, (const SnTask*)(a + s.tasks), s.n, st);
       break;
     case ST_OUTMAX:
       launch_out_maxima(h->dtype, h->S, h->ainv, (const MaxTask*)(a + s.tasks), s.n, h->rcmax, st);
@@ -2280,7 +2362,8 @@ int pselinv_profile(pselinv_t h, int which, void* stream, pselinv_step_stat* out
                                 PSELINV_STEP_MEMSET,  PSELINV_STEP_SCATTER_VALUES,
                                 PSELINV_STEP_SLICE,   PSELINV_STEP_OZAKI_GEMM, PSELINV_STEP_MEMSET,
                                 PSELINV_STEP_DIAG_LU, PSELINV_STEP_SMALL_LEVEL,
-                                PSELINV_STEP_GATHER_SLICE, PSELINV_STEP_OUTPUT_MAXIMA};
+                                PSELINV_STEP_GATHER_SLICE, PSELINV_STEP_OUTPUT_MAXIMA,
+                                PSELINV_STEP_COPY};
     out[i].kind = kinds[s.kind];
     out[i].level = s.level;
     out[i].tasks = s.n;

@@ -259,8 +259,10 @@ cudaError_t prepare_ozaki_kernels();
 // maxima = true: accumulate row maxima into desc.maxbits; false: write the slices
 void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bool maxima,
                   cudaStream_t st);
+// a_tmem: the MMAs read A from tensor memory (copied from the stage per K
+// half) instead of shared memory
 void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
-                       bool persistent, cudaStream_t st);
+                       bool persistent, bool a_tmem, cudaStream_t st);
 void launch_zero(const CopySeg* segs, int nseg, int per_seg, cudaStream_t st);
 // a kernel whose only wait never completes: it gives up after budget_ns and
 // records DEV_TIMEOUT in err[0]
@@ -354,8 +356,14 @@ void launch_scatter_sub_general(int dtype, const SymDev& S, void* store, const v
 void launch_scatter_set(int dtype, const SymDev& S, void* store, const void* src,
                         const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st);
 // store(R_K, R_K) -= Sc_K (atomic) from src + sofs[task]; tasks as for gather
+// lower: only the entries on or below the diagonal of each Sc (p >= q), for
+// the symmetric Schur complements of a symmetric A
 void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src,
-                        const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st);
+                        const int64_t* sofs, const SnTask* tasks, int ntasks, bool lower,
+                        cudaStream_t st);
+// upper triangle of each task's diagonal block := its lower one, transposed
+void launch_mirror_lower(int dtype, const SymDev& S, void* store, const SnTask* tasks, int ntasks,
+                         cudaStream_t st);
 // per_seg CTAs per segment (the plan sizes it by the longest segment)
 void launch_copy(int dtype, const CopySeg* segs, int nseg, int per_seg, cudaStream_t st);
 // out[p] = store[inst * storage + value_map[p]]

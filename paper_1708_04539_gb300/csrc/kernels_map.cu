@@ -249,8 +249,9 @@ scatter_sub_general_kernel(SymDev S, T* store, const T* __restrict__ src,
 }
 
 // store(R_K, R_K) -= Sc (atomic: siblings of one level update shared
-// ancestors); ASSIGN: store(R_K, R_K) = Sc (the import of a gathered block)
-template <typename T, bool ASSIGN = false>
+// ancestors); ASSIGN: store(R_K, R_K) = Sc (the import of a gathered block);
+// LOWER: the entries p >= q only (a symmetric Sc)
+template <typename T, bool ASSIGN = false, bool LOWER = false>
 __global__ void __launch_bounds__(kThreads)
 scatter_sub_kernel(SymDev S, T* store, const T* __restrict__ src, const int64_t* __restrict__ sofs,
                    const SnTask* __restrict__ tasks, int ntasks) {
@@ -265,7 +266,7 @@ scatter_sub_kernel(SymDev S, T* store, const T* __restrict__ src, const int64_t*
     const int p0 = task.a * kTile, q0 = task.b * kTile;
     for (int r = ly; r < kTile; r += kThreads / 32) {
       const int p = p0 + lx, q = q0 + r;
-      if (p >= c || q >= c) continue;
+      if (p >= c || q >= c || (LOWER && p < q)) continue;
       if (S.check && !map_in_range(S, rb, p, q)) {
         set_error(S.err, DEV_CHECK, K);
         continue;
@@ -276,6 +277,37 @@ scatter_sub_kernel(SymDev S, T* store, const T* __restrict__ src, const int64_t*
       else
         atomic_add_s(dst + map_slot(S, rb, p, q), scale_s(v, -1.0));
     }
+  }
+}
+
+// D(i, j) = D(j, i) for i < j of the diagonal block of each task's
+// supernode: 32 x 32 tiles of the upper triangle staged through shared
+// memory (coalesced on both sides)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+mirror_lower_kernel(SymDev S, T* store, const SnTask* __restrict__ tasks, int ntasks) {
+  __shared__ T tile[kTile][kTile + 1];
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const SnTask task = tasks[t];
+    const int s = S.sn_width[task.K];
+    T* D = store + (int64_t)task.inst * S.storage + S.sn_off[task.K];
+    const int nb = (s + kTile - 1) / kTile;
+    for (int bj = 0; bj < nb; bj++)
+      for (int bi = 0; bi <= bj; bi++) {
+        // source: rows bj*32.., columns bi*32.. (on or below the diagonal)
+        for (int r = ly; r < kTile; r += kThreads / 32) {
+          const int row = bj * kTile + lx, col = bi * kTile + r;
+          if (row < s && col < s) tile[r][lx] = D[row + (int64_t)col * s];
+        }
+        __syncthreads();
+        // destination: rows bi*32.., columns bj*32.., entries above the diagonal
+        for (int r = ly; r < kTile; r += kThreads / 32) {
+          const int row = bi * kTile + lx, col = bj * kTile + r;
+          if (row < s && col < s && row < col) D[row + (int64_t)col * s] = tile[lx][r];
+        }
+        __syncthreads();
+      }
   }
 }
 
@@ -522,15 +554,35 @@ void launch_gather(int dtype, const SymDev& S, const void* store, void* out, con
 }
 
 void launch_scatter_sub(int dtype, const SymDev& S, void* store, const void* src,
-                        const int64_t* sofs, const SnTask* tasks, int ntasks, cudaStream_t st) {
+                        const int64_t* sofs, const SnTask* tasks, int ntasks, bool lower,
+                        cudaStream_t st) {
+  if (ntasks <= 0) return;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  if (dtype == DT_F64) {
+    if (lower)
+      scatter_sub_kernel<double, false, true><<<grid, kThreads, 0, st>>>(
+          S, (double*)store, (const double*)src, sofs, tasks, ntasks);
+    else
+      scatter_sub_kernel<double><<<grid, kThreads, 0, st>>>(S, (double*)store,
+                                                            (const double*)src, sofs, tasks, ntasks);
+  } else {
+    if (lower)
+      scatter_sub_kernel<cdouble, false, true><<<grid, kThreads, 0, st>>>(
+          S, (cdouble*)store, (const cdouble*)src, sofs, tasks, ntasks);
+    else
+      scatter_sub_kernel<cdouble><<<grid, kThreads, 0, st>>>(
+          S, (cdouble*)store, (const cdouble*)src, sofs, tasks, ntasks);
+  }
+}
+
+void launch_mirror_lower(int dtype, const SymDev& S, void* store, const SnTask* tasks, int ntasks,
+                         cudaStream_t st) {
   if (ntasks <= 0) return;
   const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
   if (dtype == DT_F64)
-    scatter_sub_kernel<double><<<grid, kThreads, 0, st>>>(S, (double*)store, (const double*)src,
-                                                          sofs, tasks, ntasks);
+    mirror_lower_kernel<double><<<grid, kThreads, 0, st>>>(S, (double*)store, tasks, ntasks);
   else
-    scatter_sub_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (cdouble*)store,
-                                                           (const cdouble*)src, sofs, tasks, ntasks);
+    mirror_lower_kernel<cdouble><<<grid, kThreads, 0, st>>>(S, (cdouble*)store, tasks, ntasks);
 }
 
 void launch_gather_general(int dtype, const SymDev& S, const void* store, void* out,

@@ -268,7 +268,7 @@ constexpr size_t gslice_smem() {
 }
 
 template <typename T, bool MAXIMA>
-__global__ void __launch_bounds__(kSliceThreads)
+__global__ void __launch_bounds__(kSliceThreads, 4)
 gslice_kernel(SymDev S, const T* __restrict__ store, const SliceDesc* __restrict__ descs,
               const GTileTask* __restrict__ gtasks, int ngt,
               const SliceTask* __restrict__ stasks, int nst, unsigned long long* rcmax) {
@@ -323,74 +323,82 @@ gslice_kernel(SymDev S, const T* __restrict__ store, const SliceDesc* __restrict
       }
     }
     __syncthreads();
-    constexpr int kPer = kGT * kGT / kSliceThreads;  // entries per thread and pass
+    constexpr int kPer = kGT * kGT / kSliceThreads / 2;  // entries per thread and round
     // entries whose row lies in the column's supernode or later: lanes along
-    // p (down a column); all index loads of the thread first, then all
-    // value loads
-    {
+    // p (down a column); in two rounds, all index loads of a round first,
+    // then all its value loads
+#pragma unroll 1
+    for (int round = 0; round < 2; round++) {
       int rel[kPer];
       bool use[kPer];
 #pragma unroll
-      for (int i = 0; i < kPer; i++) {
+      for (int ii = 0; ii < kPer; ii++) {
+        const int i = round * kPer + ii;
         const int ql = warp + 8 * (i >> 1), pl = lane + 32 * (i & 1);
         const int p = p0 + pl, q = q0 + ql;
-        use[i] = p < cu && q < cl && rblk[pl] >= cblk[ql];
+        use[ii] = p < cu && q < cl && rblk[pl] >= cblk[ql];
         int64_t ri = crel[ql] + p;
-        if (S.check && use[i] && (ri < 0 || ri >= S.relidx_size)) {
+        if (S.check && use[ii] && (ri < 0 || ri >= S.relidx_size)) {
           set_error(S.err, DEV_CHECK, K);
-          use[i] = false;
+          use[ii] = false;
         }
-        rel[i] = use[i] ? S.relidx[ri] : 0;
+        rel[ii] = use[ii] ? S.relidx[ri] : 0;
       }
       T v[kPer];
 #pragma unroll
-      for (int i = 0; i < kPer; i++) {
+      for (int ii = 0; ii < kPer; ii++) {
+        const int i = round * kPer + ii;
         const int ql = warp + 8 * (i >> 1), pl = lane + 32 * (i & 1);
-        const int64_t slot = (rblk[pl] == cblk[ql] ? cdiag[ql] : cpan[ql]) + rel[i];
-        if (S.check && use[i] && (slot < io || slot >= io + S.storage)) {
+        const int64_t slot = (rblk[pl] == cblk[ql] ? cdiag[ql] : cpan[ql]) + rel[ii];
+        if (S.check && use[ii] && (slot < io || slot >= io + S.storage)) {
           set_error(S.err, DEV_CHECK, K);
-          use[i] = false;
+          use[ii] = false;
         }
-        v[i] = use[i] ? store[slot] : sc_zero(T());
+        v[ii] = use[ii] ? store[slot] : sc_zero(T());
       }
 #pragma unroll
-      for (int i = 0; i < kPer; i++) {
+      for (int ii = 0; ii < kPer; ii++) {
+        const int i = round * kPer + ii;
         const int ql = warp + 8 * (i >> 1), pl = lane + 32 * (i & 1);
         if (p0 + pl >= cu || q0 + ql >= cl || rblk[pl] >= cblk[ql])  // upper pass writes the rest
-          tile[pl * kGTPad + ql] = v[i];
+          tile[pl * kGTPad + ql] = v[ii];
       }
     }
     // the others: lanes along q (down a column of a panel of the row's supernode)
-    {
+#pragma unroll 1
+    for (int round = 0; round < 2; round++) {
       int rel[kPer];
       bool use[kPer];
 #pragma unroll
-      for (int i = 0; i < kPer; i++) {
+      for (int ii = 0; ii < kPer; ii++) {
+        const int i = round * kPer + ii;
         const int pl = warp + 8 * (i >> 1), ql = lane + 32 * (i & 1);
         const int p = p0 + pl, q = q0 + ql;
-        use[i] = p < cu && q < cl && rblk[pl] < cblk[ql];
+        use[ii] = p < cu && q < cl && rblk[pl] < cblk[ql];
         const int64_t ri = rrel[pl] + q;
-        if (S.check && use[i] && (ri < 0 || ri >= S.relidx_size)) {
+        if (S.check && use[ii] && (ri < 0 || ri >= S.relidx_size)) {
           set_error(S.err, DEV_CHECK, K);
-          use[i] = false;
+          use[ii] = false;
         }
-        rel[i] = use[i] ? S.relidx[ri] : 0;
+        rel[ii] = use[ii] ? S.relidx[ri] : 0;
       }
       T v[kPer];
 #pragma unroll
-      for (int i = 0; i < kPer; i++) {
+      for (int ii = 0; ii < kPer; ii++) {
+        const int i = round * kPer + ii;
         const int pl = warp + 8 * (i >> 1);
-        const int64_t slot = rpan[pl] + rel[i];
-        if (S.check && use[i] && (slot < io || slot >= io + S.storage)) {
+        const int64_t slot = rpan[pl] + rel[ii];
+        if (S.check && use[ii] && (slot < io || slot >= io + S.storage)) {
           set_error(S.err, DEV_CHECK, K);
-          use[i] = false;
+          use[ii] = false;
         }
-        v[i] = use[i] ? store[slot] : sc_zero(T());
+        v[ii] = use[ii] ? store[slot] : sc_zero(T());
       }
 #pragma unroll
-      for (int i = 0; i < kPer; i++) {
+      for (int ii = 0; ii < kPer; ii++) {
+        const int i = round * kPer + ii;
         const int pl = warp + 8 * (i >> 1), ql = lane + 32 * (i & 1);
-        if (p0 + pl < cu && q0 + ql < cl && rblk[pl] < cblk[ql]) tile[pl * kGTPad + ql] = v[i];
+        if (p0 + pl < cu && q0 + ql < cl && rblk[pl] < cblk[ql]) tile[pl * kGTPad + ql] = v[ii];
       }
     }
     __syncthreads();
@@ -486,6 +494,19 @@ __device__ __forceinline__ void mma_f16(uint32_t dt, uint64_t a, uint64_t b, uin
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// the same with A from tensor memory (128 lanes = rows, 8 columns = K 16)
+__device__ __forceinline__ void mma_f16_ta(uint32_t dt, uint32_t at, uint64_t b, uint32_t acc,
+                                           uint32_t idesc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dt),
+      "r"(at), "l"(b), "r"(idesc), "r"(acc));
+}
+// 128 rows x 256 bits (K 16 of FP16) from shared memory (canonical K-major
+// layout of the descriptor) into tensor memory: row i -> lane i
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
+  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -610,16 +631,22 @@ __device__ __forceinline__ void task_range(const OzDesc& d, int ks, int& kb0, in
   nkb = min(d.K32, kb0 + per) - kb0;
 }
 
-template <int S>
+// ATMEM: the A slices go from the stage into tensor memory (tcgen05.cp, K 16
+// at a time, two buffers of S x 8 columns after the accumulators) and the
+// MMAs read A there, so shared memory serves each A tile once per K half
+// instead of once per slice pair; the 64-bit totals then live in shared
+// memory (64 KB after the ring) instead of tensor memory.
+template <int S, bool ATMEM>
 __global__ void __launch_bounds__(kOzThreads, 1)
 ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ tasks, int ntasks,
                   int* err) {
   constexpr int kAB = S * 2 * kTileBytes;  // A part of a stage (128 rows)
   constexpr int kStage = S * 3 * kTileBytes;
   constexpr uint32_t kTmemCols = 512;
+  static_assert(!ATMEM || S * 64 + 2 * S * 8 <= (int)kTmemCols, "tensor memory budget");
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_full[kOzStages], bar_free[kOzStages], bar_acc_full,
-      bar_acc_empty;
+      bar_acc_empty, bar_afree[2];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -631,6 +658,8 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
     }
     mbar_init(smem_u32(&bar_acc_full), 1);
     mbar_init(smem_u32(&bar_acc_empty), kOzDrainWarps);  // one arrival per drain warp
+    mbar_init(smem_u32(&bar_afree[0]), 1);
+    mbar_init(smem_u32(&bar_afree[1]), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -702,6 +731,7 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
     // ---- MMA issue ----
     if (lane == 0) {
       uint32_t g = 0, q = 0;  // K blocks consumed, chunks completed
+      uint32_t h16 = 0;       // ATMEM: K halves issued (tensor-memory A buffer ring)
       for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
         const OzTask task = tasks[t];
         const OzDesc* dp = descs + task.d;
@@ -727,16 +757,50 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
           // stage-base descriptors; an offset within shared memory is added
           // to the address field (bits 0-13 hold address >> 4)
           const uint64_t a0 = smem_desc(st), b0 = smem_desc(st + kAB);
+          if (ATMEM) {
+            bool waited = true;
+#pragma unroll 1
+            for (int hk = 0; hk < 2; hk++, h16++) {
+              const uint32_t x = h16 & 1;
+              // the MMAs that read this buffer two halves ago are done
+              if (h16 >= 2 && !mbar_wait(smem_u32(&bar_afree[x]), ((h16 - 2) >> 1) & 1)) {
+                waited = false;
+                break;
+              }
+              const uint32_t ta = tmem + (uint32_t)(S * 64) + x * (uint32_t)(S * 8);
 #pragma unroll
-          for (int sa = 0; sa < S; sa++)
+              for (int sa = 0; sa < S; sa++)
+                tmem_cp_128x256b(ta + (uint32_t)(sa * 8),
+                                 a0 + (uint64_t)((sa * 2 * kTileBytes + hk * 256) >> 4));
 #pragma unroll
-            for (int tb = 0; tb < S - sa; tb++) {
-              const uint32_t dt = tmem + (uint32_t)((sa + tb) * 64);
-              const uint64_t ad = a0 + (uint64_t)((sa * 2 * kTileBytes) >> 4);
-              const uint64_t bd = b0 + (uint64_t)((tb * kTileBytes) >> 4);
-              mma_f16(dt, ad, bd, (sa == 0 && first) ? 0u : 1u, idesc);
-              mma_f16(dt, ad + (256 >> 4), bd + (256 >> 4), 1u, idesc);
+              for (int sa = 0; sa < S; sa++)
+#pragma unroll
+                for (int tb = 0; tb < S - sa; tb++)
+                  mma_f16_ta(tmem + (uint32_t)((sa + tb) * 64), ta + (uint32_t)(sa * 8),
+                             b0 + (uint64_t)((tb * kTileBytes + hk * 256) >> 4),
+                             (sa == 0 && first && hk == 0) ? 0u : 1u, idesc);
+              mma_commit(smem_u32(&bar_afree[x]));
             }
+            if (!waited) {
+              // the stage's commit still tracks what was issued, so that the
+              // exit below waits for it
+              mma_commit(smem_u32(&bar_free[stg]));
+              g++;
+              ok = false;
+              break;
+            }
+          } else {
+#pragma unroll
+            for (int sa = 0; sa < S; sa++)
+#pragma unroll
+              for (int tb = 0; tb < S - sa; tb++) {
+                const uint32_t dt = tmem + (uint32_t)((sa + tb) * 64);
+                const uint64_t ad = a0 + (uint64_t)((sa * 2 * kTileBytes) >> 4);
+                const uint64_t bd = b0 + (uint64_t)((tb * kTileBytes) >> 4);
+                mma_f16(dt, ad, bd, (sa == 0 && first) ? 0u : 1u, idesc);
+                mma_f16(dt, ad + (256 >> 4), bd + (256 >> 4), 1u, idesc);
+              }
+          }
           mma_commit(smem_u32(&bar_free[stg]));
           if (last) {
             mma_commit(smem_u32(&bar_acc_full));
@@ -757,6 +821,9 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(hcol * 32);
     // 64-bit totals after the accumulators: value j of the half at 2j (lo), 2j + 1 (hi)
     const uint32_t ttot = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(S * 64 + hcol * 64);
+    // ATMEM: the totals in shared memory after the ring, output j of lane l
+    // of warp w at [(w * 32 + j) * 32 + l] (lanes contiguous)
+    long long* stot = reinterpret_cast<long long*>(smem + kOzStages * kStage) + warp * 32 * 32 + lane;
     uint32_t q = 0;
     for (int t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
       const OzTask task = tasks[t];
@@ -797,16 +864,24 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
             for (int j = 0; j < 16; j++)
               part[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shift;
           }
-          uint32_t tv[32];
-          if (c > 0) tmem_ld32(ttot + (uint32_t)(g2 * 32), tv);
+          if (ATMEM) {
 #pragma unroll
-          for (int j = 0; j < 16; j++) {
-            long long tt = part[j];
-            if (c > 0) tt += (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
-            tv[2 * j] = (uint32_t)tt;
-            tv[2 * j + 1] = (uint32_t)((unsigned long long)tt >> 32);
+            for (int j = 0; j < 16; j++) {
+              long long* tp = stot + (g2 * 16 + j) * 32;
+              *tp = c > 0 ? *tp + part[j] : part[j];
+            }
+          } else {
+            uint32_t tv[32];
+            if (c > 0) tmem_ld32(ttot + (uint32_t)(g2 * 32), tv);
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+              long long tt = part[j];
+              if (c > 0) tt += (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
+              tv[2 * j] = (uint32_t)tt;
+              tv[2 * j + 1] = (uint32_t)((unsigned long long)tt >> 32);
+            }
+            tmem_st32(ttot + (uint32_t)(g2 * 32), tv);
           }
-          tmem_st32(ttot + (uint32_t)(g2 * 32), tv);
         }
         // accumulators read: the MMAs of the next chunk may start
         fence_before();
@@ -822,14 +897,15 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
 #pragma unroll 1
         for (int g2 = 0; g2 < 2; g2++) {
           uint32_t tv[32];
-          tmem_ld32(ttot + (uint32_t)(g2 * 32), tv);
+          if (!ATMEM) tmem_ld32(ttot + (uint32_t)(g2 * 32), tv);
           if (r < dM) {
 #pragma unroll
             for (int j = 0; j < 16; j++) {
               const int n = nb + g2 * 16 + j;
               if (n < dN) {
                 const long long tt =
-                    (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
+                    ATMEM ? stot[(g2 * 16 + j) * 32]
+                          : (long long)(((unsigned long long)tv[2 * j + 1] << 32) | tv[2 * j]);
                 const double v = scaled_int_to_double(tt, ea + eB[n], neg);
                 double* cp = Cp + (r + (int64_t)n * ldc) * cscale + coff;
                 if (atomic) atomicAdd(cp, v); else *cp = v;
@@ -849,9 +925,9 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-template <int S>
+template <int S, bool ATMEM>
 constexpr int gemm_smem() {
-  return kOzStages * S * 3 * kTileBytes;
+  return kOzStages * S * 3 * kTileBytes + (ATMEM ? kOzDrainWarps * 32 * 32 * 8 : 0);
 }
 
 // Failure-path check: wait on an mbarrier that nothing will complete, with a
@@ -886,12 +962,18 @@ cudaError_t prepare_ozaki_kernels() {
   e = cudaFuncSetAttribute(gslice_kernel<cdouble, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)gslice_smem<cdouble>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(ozaki_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem<4>());
+#define PSELINV_OZ_ATTR(S, AT)                                                               \
+  e = cudaFuncSetAttribute(ozaki_gemm_kernel<S, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           gemm_smem<S, AT>());                                                 \
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(ozaki_gemm_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem<5>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(ozaki_gemm_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              gemm_smem<6>());
+  PSELINV_OZ_ATTR(4, false)
+  PSELINV_OZ_ATTR(5, false)
+  PSELINV_OZ_ATTR(6, false)
+  PSELINV_OZ_ATTR(4, true)
+  PSELINV_OZ_ATTR(5, true)
+  PSELINV_OZ_ATTR(6, true)
+#undef PSELINV_OZ_ATTR
+  return cudaSuccess;
 }
 
 void launch_slice(const SliceDesc* descs, const SliceTask* tasks, int ntasks, bool maxima,
@@ -1000,17 +1082,29 @@ void launch_gslice(int dtype, const SymDev& S, const void* store, const SliceDes
 }
 
 void launch_ozaki_gemm(int S, const OzDesc* descs, const OzTask* tasks, int ntasks, int* err,
-                       bool persistent, cudaStream_t st) {
+                       bool persistent, bool a_tmem, cudaStream_t st) {
   if (ntasks <= 0) return;
   // one CTA fits an SM (shared memory and tensor memory): a persistent grid
   // on the sweep's stream; one task per CTA on the normalisation stream, so
   // that its CTAs leave SMs to the sweep between tasks
   const int grid = persistent && ntasks > 152 ? 152 : ntasks;
-  switch (S) {
-    case 4: ozaki_gemm_kernel<4><<<grid, kOzThreads, gemm_smem<4>(), st>>>(descs, tasks, ntasks, err); break;
-    case 5: ozaki_gemm_kernel<5><<<grid, kOzThreads, gemm_smem<5>(), st>>>(descs, tasks, ntasks, err); break;
-    default: ozaki_gemm_kernel<6><<<grid, kOzThreads, gemm_smem<6>(), st>>>(descs, tasks, ntasks, err); break;
+#define PSELINV_OZ_LAUNCH(SS, AT)                                                        \
+  ozaki_gemm_kernel<SS, AT><<<grid, kOzThreads, gemm_smem<SS, AT>(), st>>>(descs, tasks, \
+                                                                          ntasks, err)
+  if (a_tmem) {
+    switch (S) {
+      case 4: PSELINV_OZ_LAUNCH(4, true); break;
+      case 5: PSELINV_OZ_LAUNCH(5, true); break;
+      default: PSELINV_OZ_LAUNCH(6, true); break;
+    }
+  } else {
+    switch (S) {
+      case 4: PSELINV_OZ_LAUNCH(4, false); break;
+      case 5: PSELINV_OZ_LAUNCH(5, false); break;
+      default: PSELINV_OZ_LAUNCH(6, false); break;
+    }
   }
+#undef PSELINV_OZ_LAUNCH
 }
 
 void launch_wait_selftest(int* err, unsigned long long budget_ns, cudaStream_t st) {

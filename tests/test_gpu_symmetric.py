@@ -57,3 +57,32 @@ def test_symmetric_sweep_matches_oracle_and_general_sweep(torch, name, maker):
     compare_full(p, st, symsp, 0, 20, tol=TOL_SPLIT)
     st, symspn = run(torch, p, ps.PREC_OZAKI_FP16, True, all_split=True, split_normalise=True)
     compare_full(p, st, symspn, 0, 20, tol=TOL_SPLIT)
+
+
+@pytest.mark.parametrize("name,maker", CASES, ids=[c[0] for c in CASES])
+def test_symmetric_factorisation(torch, name, maker):
+    """For A = A^T the factorisation updates only the lower triangle (the
+    Schur complements are symmetric; U's panels are solved from L's, the
+    diagonal blocks mirrored before their LU): the factors equal the general
+    factorisation's, FP64 and with split Schur products, and the symmetric
+    plan runs half the Schur-product work."""
+    import paper_1708_04539_gb300 as ps
+    p = maker()
+    vals = torch.from_numpy(np.ascontiguousarray(p.values)).cuda()
+    g = ps.SelInv.from_problem(p)
+    g.factor(vals)
+    ref = g.get_selected(layout=ps.LAYOUT_FACTORS)
+    gflops = sum(s["flops"] for s in g.profile(1) if s["kind"] == "gemm")
+    g.close()
+    scale = np.abs(ref).max()
+    for fprec, tol in ((ps.PREC_FP64, 1e-12), (ps.PREC_OZAKI_FP16, 1e-10)):
+        h = ps.SelInv.from_problem(p, symmetric=True, factor_precision=fprec,
+                                   factor_split_mflops=-1)
+        h.factor(vals)
+        fac = h.get_selected(layout=ps.LAYOUT_FACTORS)
+        prof = h.profile(1)
+        h.close()
+        assert np.abs(fac - ref).max() <= tol * scale, (fprec, np.abs(fac - ref).max() / scale)
+        if fprec == ps.PREC_FP64:
+            sflops = sum(s["flops"] for s in prof if s["kind"] == "gemm")
+            assert sflops < 0.9 * gflops, (sflops, gflops)
