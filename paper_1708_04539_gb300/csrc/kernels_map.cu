@@ -250,12 +250,19 @@ scatter_sub_general_kernel(SymDev S, T* store, const T* __restrict__ src,
 
 // store(R_K, R_K) -= Sc (atomic: siblings of one level update shared
 // ancestors); ASSIGN: store(R_K, R_K) = Sc (the import of a gathered block);
-// LOWER: the entries p >= q only (a symmetric Sc)
+// LOWER: the entries p >= q only (a symmetric Sc).  Entry (p, q), x = R_K[p]
+// in supernode I, y = R_K[q] in J, lies in J's diagonal block or L panel
+// (I >= J: the column's storage base + the relative index of p) or in I's
+// U^T panel (I < J: the row's base + the relative index of q); the bases of
+// the tile's 32 rows and columns are staged in shared memory once, so an
+// entry costs one index load, one value load and one store or atomic.
 template <typename T, bool ASSIGN = false, bool LOWER = false>
 __global__ void __launch_bounds__(kThreads)
 scatter_sub_kernel(SymDev S, T* store, const T* __restrict__ src, const int64_t* __restrict__ sofs,
                    const SnTask* __restrict__ tasks, int ntasks) {
-  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  __shared__ int64_t cdiag[kTile], cpan[kTile], crel[kTile], rpan[kTile], rrel[kTile];
+  __shared__ int csn[kTile], rsn[kTile];
+  const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
   for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const SnTask task = tasks[t];
     const int K = task.K;
@@ -264,19 +271,45 @@ scatter_sub_kernel(SymDev S, T* store, const T* __restrict__ src, const int64_t*
     T* dst = store + (int64_t)task.inst * S.storage;
     const T* Sc = src + sofs[t];
     const int p0 = task.a * kTile, q0 = task.b * kTile;
+    if (tid < kTile) {
+      const int q = q0 + tid;
+      if (q < c) {
+        cdiag[tid] = S.col_diag[rb + q];
+        cpan[tid] = S.col_pan[rb + q];
+        crel[tid] = S.col_rel[rb + q];
+        csn[tid] = S.col_sn[rb + q];
+      }
+    } else if (tid < 2 * kTile) {
+      const int pl = tid - kTile, p = p0 + pl;
+      if (p < c) {
+        rpan[pl] = S.row_pan[rb + p];
+        rrel[pl] = S.row_rel[rb + p];
+        rsn[pl] = S.row_sn[rb + p];
+      }
+    }
+    __syncthreads();
     for (int r = ly; r < kTile; r += kThreads / 32) {
-      const int p = p0 + lx, q = q0 + r;
+      const int p = p0 + lx, q = q0 + r;  // lanes along p: Sc is column major
       if (p >= c || q >= c || (LOWER && p < q)) continue;
-      if (S.check && !map_in_range(S, rb, p, q)) {
+      const bool col_side = rsn[lx] >= csn[r];
+      const int64_t ri = col_side ? crel[r] + p : rrel[lx] + q;
+      if (S.check && (ri < 0 || ri >= S.relidx_size)) {
+        set_error(S.err, DEV_CHECK, K);
+        continue;
+      }
+      const int64_t slot =
+          (col_side ? (rsn[lx] == csn[r] ? cdiag[r] : cpan[r]) : rpan[lx]) + S.relidx[ri];
+      if (S.check && (slot < 0 || slot >= S.storage)) {
         set_error(S.err, DEV_CHECK, K);
         continue;
       }
       const T v = Sc[p + (int64_t)q * c];
       if (ASSIGN)
-        dst[map_slot(S, rb, p, q)] = v;
+        dst[slot] = v;
       else
-        atomic_add_s(dst + map_slot(S, rb, p, q), scale_s(v, -1.0));
+        atomic_add_s(dst + slot, scale_s(v, -1.0));
     }
+    __syncthreads();
   }
 }
 
