@@ -752,6 +752,10 @@ def run_ours(args):
             h.selinv(precision=prec, stream=stream)
             h.get_selected(out_dev[0], stream=stream)
         torch.cuda.synchronize()
+        if args.dump_profile:  # the plan's launches with their algorithmic work
+            with open(args.dump_profile, "w") as f:
+                json.dump({"config": config, "size": size,
+                           "steps": h.profile(0, stream=stream)}, f)
         h.close()
         log("capture run done")
         return 0

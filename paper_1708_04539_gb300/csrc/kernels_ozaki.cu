@@ -487,6 +487,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 // kind::f16, FP16 x FP16 -> FP32, both operands K-major, M = 128, N = 64
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 constexpr uint32_t kIdescNegA = kIdesc | (1u << 13);  // D += (-A) B
+// the same with N = 128: two B slices tb, tb + 1 (adjacent 4 KB tiles, so
+// one operand of 128 rows at the same 512-byte row-group stride) into the
+// adjacent accumulators of weights s + tb and s + tb + 1, A read once
+constexpr uint32_t kIdescN128 =
+    (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t kIdescN128NegA = kIdescN128 | (1u << 13);
 
 __device__ __forceinline__ void mma_f16(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc,
                                         uint32_t idesc) {
@@ -619,7 +625,13 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 //     after the last chunk, write the outputs while the MMAs of the next
 //     task already run.
 // ---------------------------------------------------------------------------
-constexpr int kOzStages = 2;
+// ring depth: three stages (216 KB for S = 6) hide the copy latency behind
+// the paired MMAs of a K block; the tensor-memory-A variant keeps two (its
+// totals take 64 KB of shared memory)
+template <int S, bool ATMEM>
+__host__ __device__ constexpr int oz_stages() {
+  return ATMEM || S * 3 * 4096 * 3 > 220 * 1024 ? 2 : 3;
+}
 constexpr int kOzDrainWarps = 8;
 constexpr int kOzThreads = (kOzDrainWarps + 2) * 32;
 
@@ -642,6 +654,7 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
                   int* err) {
   constexpr int kAB = S * 2 * kTileBytes;  // A part of a stage (128 rows)
   constexpr int kStage = S * 3 * kTileBytes;
+  constexpr int kOzStages = oz_stages<S, ATMEM>();
   constexpr uint32_t kTmemCols = 512;
   static_assert(!ATMEM || S * 64 + 2 * S * 8 <= (int)kTmemCols, "tensor memory budget");
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -753,7 +766,9 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
           }
           fence_after();
           const uint32_t st = smem_u32(smem + stg * kStage);
-          const uint32_t idesc = (d.neg_half && kb0 + i >= d.half) ? kIdescNegA : kIdesc;
+          const bool neg_a = d.neg_half && kb0 + i >= d.half;
+          const uint32_t idesc = neg_a ? kIdescNegA : kIdesc;
+          const uint32_t idesc2 = neg_a ? kIdescN128NegA : kIdescN128;
           // stage-base descriptors; an offset within shared memory is added
           // to the address field (bits 0-13 hold address >> 4)
           const uint64_t a0 = smem_desc(st), b0 = smem_desc(st + kAB);
@@ -775,10 +790,11 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
 #pragma unroll
               for (int sa = 0; sa < S; sa++)
 #pragma unroll
-                for (int tb = 0; tb < S - sa; tb++)
+                for (int tb = 0; tb < S - sa; tb += 2)
                   mma_f16_ta(tmem + (uint32_t)((sa + tb) * 64), ta + (uint32_t)(sa * 8),
                              b0 + (uint64_t)((tb * kTileBytes + hk * 256) >> 4),
-                             (sa == 0 && first && hk == 0) ? 0u : 1u, idesc);
+                             (sa == 0 && first && hk == 0) ? 0u : 1u,
+                             tb + 1 < S - sa ? idesc2 : idesc);
               mma_commit(smem_u32(&bar_afree[x]));
             }
             if (!waited) {
@@ -790,15 +806,21 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
               break;
             }
           } else {
+            // slice pairs (sa, tb) and (sa, tb + 1) in one N = 128 MMA: 9
+            // such and 3 of N = 64 per K 16 for S = 6 instead of 21 of N = 64
+            // (an N = 64 MMA is bound by reading its 6 KB of operands from
+            // shared memory: 48 cycles against 64 for N = 128's 8 KB and
+            // twice the products)
 #pragma unroll
             for (int sa = 0; sa < S; sa++)
 #pragma unroll
-              for (int tb = 0; tb < S - sa; tb++) {
+              for (int tb = 0; tb < S - sa; tb += 2) {
                 const uint32_t dt = tmem + (uint32_t)((sa + tb) * 64);
                 const uint64_t ad = a0 + (uint64_t)((sa * 2 * kTileBytes) >> 4);
                 const uint64_t bd = b0 + (uint64_t)((tb * kTileBytes) >> 4);
-                mma_f16(dt, ad, bd, (sa == 0 && first) ? 0u : 1u, idesc);
-                mma_f16(dt, ad + (256 >> 4), bd + (256 >> 4), 1u, idesc);
+                const uint32_t id = tb + 1 < S - sa ? idesc2 : idesc;
+                mma_f16(dt, ad, bd, (sa == 0 && first) ? 0u : 1u, id);
+                mma_f16(dt, ad + (256 >> 4), bd + (256 >> 4), 1u, id);
               }
           }
           mma_commit(smem_u32(&bar_free[stg]));
@@ -927,7 +949,7 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
 
 template <int S, bool ATMEM>
 constexpr int gemm_smem() {
-  return kOzStages * S * 3 * kTileBytes + (ATMEM ? kOzDrainWarps * 32 * 32 * 8 : 0);
+  return oz_stages<S, ATMEM>() * S * 3 * kTileBytes + (ATMEM ? kOzDrainWarps * 32 * 32 * 8 : 0);
 }
 
 // Failure-path check: wait on an mbarrier that nothing will complete, with a
