@@ -886,6 +886,15 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
             for (int j = 0; j < 16; j++)
               part[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << shift;
           }
+          if (g2 == 1) {
+            // every accumulator read: the MMAs of the next chunk may start
+            // while the totals (other columns) are updated
+            fence_before();
+            __syncwarp();
+            if (lane == 0)
+              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_acc_empty))
+                           : "memory");
+          }
           if (ATMEM) {
 #pragma unroll
             for (int j = 0; j < 16; j++) {
@@ -905,12 +914,9 @@ ozaki_gemm_kernel(const OzDesc* __restrict__ descs, const OzTask* __restrict__ t
             tmem_st32(ttot + (uint32_t)(g2 * 32), tv);
           }
         }
-        // accumulators read: the MMAs of the next chunk may start
+        // the totals are written before the epilogue reads them (same warp)
         fence_before();
         __syncwarp();
-        if (lane == 0)
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_acc_empty))
-                       : "memory");
         // (warp-uniform: the tensor-memory loads below need the whole warp)
         if (c != nchunks - 1) continue;
         // last chunk: the totals become the FP64 outputs (while the MMAs of
