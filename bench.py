@@ -314,7 +314,8 @@ def roofline_from_profile(prof, slices, fp64_peak):
                "peak_source": "measured bf16 dense peak (MEASURED_PEAKS.json) x 1.0 nominal "
                               "fp16/bf16 ratio",
                "tensor_flops_per_fp64_flop": pairs,
-               "traffic": traffic_from_profiles("ozaki_gemm")}
+               # captured with the default six slices
+               "traffic": traffic_from_profiles("ozaki_gemm") if slices == SLICES else None}
     else:
         achieved = k["bytes"] / sec / 1e9
         peak = float(peaks.get("hbm_gbs", 6778.7))
@@ -328,7 +329,7 @@ def roofline_from_profile(prof, slices, fp64_peak):
                  for n, v in kinds.items()}
 
 
-def path_roofline(st, cplx, nbatch, ms_step, fp64_peak, split):
+def path_roofline(st, cplx, nbatch, ms_step, fp64_peak, split, slices=SLICES):
     """Path-level roofline of one sweep from its level structure.
 
     Per supernode (width s, c = |R_K|, relaxed structure): products of steps
@@ -337,7 +338,8 @@ def path_roofline(st, cplx, nbatch, ms_step, fp64_peak, split):
     once, panels read and written).  FP64 roofline of level l:
     min(P_fp64, AI_l x HBM) over all its flops; split roofline: the sliced
     products at the tensor peak (21 slice products each) or HBM, whichever
-    is slower, plus F at the FP64 peak.  frac = roofline time / measured."""
+    is slower, plus F at the FP64 peak (S (S + 1) / 2 slice products for S
+    slices).  frac = roofline time / measured."""
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6778.7)) * 1e9
     tensor = float(peaks.get("bf16_tflops", 1925.5)) * 1e12
@@ -351,7 +353,7 @@ def path_roofline(st, cplx, nbatch, ms_step, fp64_peak, split):
     norm = (2 * c * width * width + 4.0 / 3.0 * width ** 3) * mult
     byts = (c * c + 2 * (2 * c * width + width * width)) * w * nbatch
     t64 = tsplit = 0.0
-    pairs = SLICES * (SLICES + 1) // 2
+    pairs = slices * (slices + 1) // 2
     for lev in range(int(st["nlevels"])):
         m = depth == lev
         f, b = float((prod[m] + norm[m]).sum()), float(byts[m].sum())
@@ -828,10 +830,11 @@ def run_ours(args):
 
     # launch-by-launch replay with CUDA events on the same stream
     prof = [] if args.no_profile else h.profile(0, stream=stream)
-    roofline, kinds = roofline_from_profile(prof, SLICES, fp64_peak)
+    nslices = args.slices or SLICES
+    roofline, kinds = roofline_from_profile(prof, nslices, fp64_peak)
     if roofline is not None:
         roofline["path"] = path_roofline(st, cplx, nbatch, ms_per_step / 1.0, fp64_peak,
-                                         prec == ps.PREC_OZAKI_FP16)
+                                         prec == ps.PREC_OZAKI_FP16, nslices)
     if args.dump_profile and rank == 0:
         with torch.cuda.stream(stream):
             fprof = [] if big else h.profile(1, stream=stream)
