@@ -251,7 +251,12 @@ int pselinv_group(const pselinv_t* members, int64_t count, const pselinv_opts* o
  * (Eq. LU, Section 3's prerequisite).  values: nbatch * nnz scalars of dtype,
  * instance b at values + b*nnz, in the CSC order given to pselinv_analyze;
  * host or device.  Runs on `stream` and waits for it to report a zero pivot
- * (PSELINV_ERR_ZERO_PIVOT; pselinv_last_info gives the permuted column). */
+ * (PSELINV_ERR_ZERO_PIVOT; pselinv_last_info gives the permuted column).
+ * The panel solves and Schur products are FP64, or sliced tensor-core
+ * products per opts.factor_precision (pselinv_set_factor_precision).  For a
+ * handle with opts.symmetric the Schur complements L_{C,K} U_{K,C} are
+ * symmetric: only their lower triangles are formed and scattered, U's panels
+ * are solved from L's, and the factors are the same L and U. */
 int pselinv_factor(pselinv_t h, int dtype, int64_t nbatch, const void* values, void* stream);
 
 /* Selected inversion of every factored instance (Algorithm 1 steps 2-5):
