@@ -291,3 +291,17 @@ def test_group_is_the_direct_sum_host_only():
     assert lib.pselinv_group(None, 0, None, ctypes.byref(out)) == -1
     for h in members + [g, d]:
         h.close()
+
+
+def test_empty_and_one_by_one_analysis():
+    """n = 0: an empty structure (no supernode, no level); n = 1: one
+    supernode of width 1 with an empty row structure at depth 0."""
+    h = ps.SelInv(0, np.array([0]), np.array([], dtype=np.int64), host_only=True)
+    st = h.structure()
+    assert st["nsuper"] == 0 and st["nlevels"] == 0 and st["storage_size"] == 0
+    h.close()
+    h = ps.SelInv(1, np.array([0, 1]), np.array([0]), host_only=True)
+    st = h.structure()
+    assert st["nsuper"] == 1 and st["nlevels"] == 1 and st["storage_size"] == 1
+    assert np.array_equal(st["rows_ptr"], [0, 0])
+    h.close()
