@@ -153,7 +153,8 @@ __device__ __forceinline__ void slice_max_task(const SliceDesc& d, const SliceTa
 // and the rest, both exact floats, so that the digits come from FP32
 // arithmetic: the low digits leave a carry of -1, 0 or 1 into the high
 // part.  Digits below the top one lie in [-64, 64]; the top one is what
-// remains (|a| <= 129), and sum_s a_s 128^{S-1-s} = Q exactly.
+// remains (|a| <= 128, as |Q| <= 2^{7S} and the lower digits sum to less
+// than half a top unit), and sum_s a_s 128^{S-1-s} = Q exactly.
 template <int S>
 __device__ __forceinline__ void write_digits_s(const double (&x)[8], int e, __half* dst,
                                                int64_t slice_stride) {
